@@ -1,0 +1,189 @@
+/*
+ * dog.h -- C ABI of the B300-native DS-PHD/MIB dynamic occupancy grid filter.
+ *
+ * The filter is the Dempster-Shafer approximation of the PHD/MIB filter of Nuss et al.,
+ * "A Random Finite Set Approach for Dynamic Occupancy Grid Maps with Real-Time
+ * Application" (Sect. VI), computed by the parallel recursion of Sect. VII (Alg. 1-7):
+ * particle prediction, sorting particles by grid cell, occupancy prediction and update,
+ * normalisation of persistent particles, initialisation of newborn particles, velocity
+ * moments and resampling.
+ *
+ * Conventions
+ *   - Every call returns DOG_OK (0) or a negative dog_status; nothing throws or aborts.
+ *   - The library owns no device memory: dog_create carves every array out of a device
+ *     workspace the caller allocates (size from dog_workspace_bytes) and keeps alive until
+ *     dog_destroy.  dog_destroy never frees it.
+ *   - All device work of a filter is issued on the CUDA stream given to dog_create, in
+ *     call order.  Calls marked "asynchronous" return before the GPU has finished.
+ *   - A handle is not thread-safe: calls on one filter must be serialised by the caller.
+ *   - Arrays are SoA; cell arrays have C = width * height entries in row-major order
+ *     (cell index = row * width + col, row = floor(y / cell_size), col = floor(x / cell_size),
+ *     grid origin at the corner (0, 0)).
+ *   - Errors detected on the device (an input that fails validation, a bounded wait that
+ *     ran out) are latched in the filter and returned by the next synchronising call
+ *     (dog_get_cells, dog_get_state, dog_get_debug, dog_sync), which clears them.  While an
+ *     error is latched, the results of the frames that follow are void.
+ */
+#ifndef DOG_H
+#define DOG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dog_status {
+  DOG_OK = 0,
+  DOG_ERR_INVALID_ARG = -1,         /* bad pointer, size or parameter                   */
+  DOG_ERR_WORKSPACE_TOO_SMALL = -2, /* workspace smaller than dog_workspace_bytes        */
+  DOG_ERR_CUDA = -3,                /* a CUDA runtime call failed                        */
+  DOG_ERR_TIMEOUT = -4,             /* a device-side bounded wait gave up; results void  */
+  DOG_ERR_INPUT = -5,               /* measurement grid / state outside its domain       */
+  DOG_ERR_BAD_STATE = -6,           /* call not valid in the filter's current state      */
+  DOG_ERR_UNSUPPORTED = -7          /* size beyond the supported maximum                 */
+} dog_status;
+
+/* dog_params.flags */
+#define DOG_NO_RESAMPLE 0x2u /* keep the normalised persistent particles (test mode)     */
+#define DOG_RECORD 0x4u      /* also keep newborn cells/flags and resample sources       */
+#define DOG_NO_GRAPH 0x8u    /* issue kernels one by one instead of a captured graph     */
+#define DOG_PROFILE 0x10u    /* time each kernel with CUDA events (dog_profile_read)      */
+
+/* memory kind of caller buffers */
+#define DOG_HOST 0
+#define DOG_DEVICE 1
+
+/* Filter parameters (Table I of the paper gives typical values).  All POD; validated by
+ * dog_workspace_bytes and dog_create.  Limits: 1 <= width, height; C = width*height <= 2^24;
+ * 1 <= num_particles < 2^25; num_birth < 2^25. */
+typedef struct dog_params {
+  int32_t width, height;   /* grid cells                                             */
+  float cell_size;         /* m                                                      */
+  uint32_t num_particles;  /* nu, persistent particles (constant, Sect. V-F)         */
+  uint32_t num_birth;      /* nu_b, newborn particles per frame (constant, Sect. VII) */
+  float p_S;               /* persistence probability, Eq. particle_persistence      */
+  float p_B;               /* birth probability, Eq. DS_resulting_masses1            */
+  float alpha_free;        /* free-mass discount alpha(T), Eq. DS_freespace_pred     */
+  float sigma_pos;         /* per-frame process noise SD of position (m), Eq. process */
+  float sigma_vel;         /* per-frame process noise SD of velocity (m/s)           */
+  float sigma_birth_vel;   /* SD of newborn velocities (m/s), Table I                 */
+  float sensor_x, sensor_y;/* radar position (m) for the radial-velocity likelihood  */
+  uint64_t seed;           /* Philox4x32-10 key                                       */
+  uint32_t flags;          /* DOG_* flags above                                       */
+} dog_params;
+
+/* Measurement grid (the paper's meas_cell_array, Sect. VII), SoA with C entries each.
+ * m_occ, m_free: observed occupancy BBA, each in [0,1], m_occ + m_free <= 1 (+1e-6).
+ * p_A, z_vr, sigma_vr: optional (all NULL for a lidar-only grid): association
+ * probability in [0,1] and the measured radial velocity with its SD (> 0 where p_A > 0)
+ * of the cell's spatial likelihood (Sect. VI-C). */
+typedef struct dog_meas_grid {
+  const float *m_occ, *m_free;
+  const float *p_A, *z_vr, *sigma_vr;
+} dog_meas_grid;
+
+/* Per-cell outputs of the last frame; any pointer may be NULL (not copied).
+ * m_occ, m_free: posterior BBA (Eq. DS_comb); rho_p, rho_b: persistent / newborn parts of
+ * m_occ (Eq. DS_resulting_masses1/2); p_occ: pignistic occupancy probability (Sect. VI-A);
+ * mean_vx, mean_vy, var_vx, var_vy, cov_vxy: velocity moments of the persistent
+ * particles (Eq. mean_x, var_x, covar_xy), 0 where rho_p = 0. */
+typedef struct dog_cells {
+  float *m_occ, *m_free, *rho_p, *rho_b, *p_occ;
+  float *mean_vx, *mean_vy, *var_vx, *var_vy, *cov_vxy;
+} dog_cells;
+
+/* Posterior state (checkpoint): particles x, y, vx, vy, w [num_particles] and the cells'
+ * free mass m_free [C]; the frame counter travels separately. */
+typedef struct dog_state {
+  float *x, *y, *vx, *vy, *w;
+  float *m_free;
+} dog_state;
+
+typedef struct dog_filter dog_filter; /* opaque */
+
+/* Bytes of device workspace dog_create needs for these parameters (host arithmetic only).
+ * Errors: DOG_ERR_INVALID_ARG (NULL or invalid parameters), DOG_ERR_UNSUPPORTED. */
+int dog_workspace_bytes(const dog_params *params, size_t *out_bytes);
+
+/* Create a filter in the caller's device workspace (256-byte aligned, at least
+ * dog_workspace_bytes long) on cuda_stream (a cudaStream_t; NULL = legacy default stream,
+ * which disables graph capture).  Initial state (frame 0): particles uniform over the grid
+ * with birth-distribution velocities and weight 0; all cells m_occ = m_free = 0.
+ * Asynchronous.  Errors: INVALID_ARG, UNSUPPORTED, WORKSPACE_TOO_SMALL, CUDA. */
+int dog_create(const dog_params *params, void *d_workspace, size_t workspace_bytes,
+               void *cuda_stream, dog_filter **out);
+
+/* Copy a measurement grid into the filter (Sect. VII: same dimensions as the map); it is
+ * used by every following dog_step until replaced.  mem_kind says where the caller's arrays
+ * live.  DOG_HOST: validated on the host (DOG_ERR_INPUT on violation, nothing copied) and
+ * the call returns after the copy; DOG_DEVICE: copied and validated on the filter's stream
+ * (asynchronous; a violation is latched and reported as DOG_ERR_INPUT). */
+int dog_set_measurement_grid(dog_filter *f, const dog_meas_grid *grid, int mem_kind);
+
+/* One recursion of the filter with time step dt (s): Alg. 1-7 of Sect. VII.
+ * Asynchronous.  Errors: INVALID_ARG (dt not finite or < 0), BAD_STATE (no measurement
+ * grid set yet), CUDA. */
+int dog_step(dog_filter *f, float dt);
+
+/* Copy the per-cell outputs of the last frame; synchronises the filter's stream.  Returns
+ * a latched device error if one occurred since the last synchronising call. */
+int dog_get_cells(dog_filter *f, const dog_cells *out, int mem_kind);
+
+/* Read / write the posterior state and frame counter (checkpoint / resume; Philox draws
+ * depend only on (seed, frame, index), so a resumed filter continues bit-exactly).
+ * dog_get_state synchronises; dog_set_state is ordered on the stream and returns after
+ * its copies completed. */
+int dog_get_state(dog_filter *f, const dog_state *out, int mem_kind, uint32_t *frame);
+int dog_set_state(dog_filter *f, const dog_state *in, int mem_kind, uint32_t frame);
+
+/* Wait for the filter's stream; return a latched device error, else DOG_OK. */
+int dog_sync(dog_filter *f);
+
+/* Intermediates of the last frame (for parity tests and diagnostics); synchronises.
+ * which / element type / count:
+ *   DOG_DBG_PRED_X..PRED_W   float [nu]  predicted particles, original order (Alg. 1)
+ *   DOG_DBG_KEY              u32   [nu]  cell index of each predicted particle
+ *   DOG_DBG_PERM             u32   [nu]  sorted position -> particle index (Alg. 2)
+ *   DOG_DBG_CELL_START/END   u32   [C]   half-open sorted range of each cell, 0/0 if empty
+ *   DOG_DBG_SUM_W, SUM_GW    u64   [C]   fixed-point (2^-40) sums of w and g*w per cell
+ *   DOG_DBG_M_OCC_PRED       float [C]   predicted occupied mass (Eq. DS_particle_sum_pred)
+ *   DOG_DBG_MU_A, MU_UA      float [C]   normalisation factors (Eq. DSnormalizationfactor(2))
+ *   DOG_DBG_W_NORM           float [nu]  normalised persistent weights, sorted order
+ *   DOG_DBG_BIRTH_X..BIRTH_W float [nu_b] newborn particles (Alg. 5)
+ *   DOG_DBG_BIRTH_CELL       u32   [nu_b] (DOG_RECORD only)
+ *   DOG_DBG_BIRTH_ASSOC      u32   [nu_b] 1 = associated set (DOG_RECORD only)
+ *   DOG_DBG_RESAMPLE_SRC     u32   [nu]  joint source index of each output (DOG_RECORD)
+ *   DOG_DBG_SCALARS          u64   [4]   frame, total weight, total birth mass, offset u
+ * Errors: INVALID_ARG (unknown which), BAD_STATE (needs DOG_RECORD). */
+enum {
+  DOG_DBG_PRED_X = 0, DOG_DBG_PRED_Y, DOG_DBG_PRED_VX, DOG_DBG_PRED_VY, DOG_DBG_PRED_W,
+  DOG_DBG_KEY, DOG_DBG_PERM, DOG_DBG_CELL_START, DOG_DBG_CELL_END, DOG_DBG_SUM_W,
+  DOG_DBG_SUM_GW, DOG_DBG_M_OCC_PRED, DOG_DBG_MU_A, DOG_DBG_MU_UA, DOG_DBG_W_NORM,
+  DOG_DBG_BIRTH_X, DOG_DBG_BIRTH_Y, DOG_DBG_BIRTH_VX, DOG_DBG_BIRTH_VY, DOG_DBG_BIRTH_W,
+  DOG_DBG_BIRTH_CELL, DOG_DBG_BIRTH_ASSOC, DOG_DBG_RESAMPLE_SRC, DOG_DBG_SCALARS,
+  DOG_DBG_COUNT
+};
+int dog_get_debug(dog_filter *f, int which, void *out, int mem_kind);
+
+/* Per-kernel device time (ms) summed over the steps since the last read (DOG_PROFILE,
+ * which issues kernels one by one with CUDA events between them).  names[k] receives a
+ * static string; *n_out the number of kernels (<= max); *steps_out the steps covered. */
+int dog_profile_read(dog_filter *f, float *ms, const char **names, int max, int *n_out,
+                     int *steps_out);
+
+/* Number of kernels one dog_step launches (for launch accounting). */
+int dog_kernels_per_step(const dog_filter *f);
+
+/* Release the handle (the caller's workspace is left untouched and may be freed after
+ * the stream has drained). */
+void dog_destroy(dog_filter *f);
+
+/* Static description of a dog_status. */
+const char *dog_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DOG_H */

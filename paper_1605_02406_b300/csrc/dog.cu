@@ -1,0 +1,569 @@
+// dog.cu -- host side of the C ABI declared in include/dog.h: parameter validation,
+// workspace carving, the per-frame launch sequence (optionally captured once into a CUDA
+// graph and replayed), checkpoint, intermediates and kernel profiling.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/dog.h"
+#include "dog_kernels.cuh"
+
+using namespace dog;
+
+namespace {
+
+constexpr int MAX_KERNELS = 12;
+constexpr int PROFILE_RING = 1024;
+
+struct Derived {
+  uint32_t C;
+  int key_bits, passes, dbits;
+  uint32_t radix;
+  uint32_t tiles_sort, tiles_seg, tiles_cell, tiles_norm;
+};
+
+int check_params(const dog_params *p, Derived *d) {
+  if (!p) return DOG_ERR_INVALID_ARG;
+  if (p->width <= 0 || p->height <= 0 || !(p->cell_size > 0.0f) || !std::isfinite(p->cell_size))
+    return DOG_ERR_INVALID_ARG;
+  if (p->num_particles == 0) return DOG_ERR_INVALID_ARG;
+  const float probs[] = {p->p_S, p->p_B, p->alpha_free};
+  for (float v : probs)
+    if (!(v >= 0.0f && v <= 1.0f)) return DOG_ERR_INVALID_ARG;
+  const float sds[] = {p->sigma_pos, p->sigma_vel, p->sigma_birth_vel};
+  for (float v : sds)
+    if (!(v >= 0.0f) || !std::isfinite(v)) return DOG_ERR_INVALID_ARG;
+  if (!std::isfinite(p->sensor_x) || !std::isfinite(p->sensor_y)) return DOG_ERR_INVALID_ARG;
+  const unsigned long long C = (unsigned long long)p->width * (unsigned long long)p->height;
+  if (C > (1ull << 24)) return DOG_ERR_UNSUPPORTED;
+  if (p->num_particles >= (1u << 25) || p->num_birth >= (1u << 25)) return DOG_ERR_UNSUPPORTED;
+  d->C = (uint32_t)C;
+  int bits = 1;
+  while ((1ull << bits) < C) ++bits;
+  d->key_bits = bits;
+  d->passes = (bits + 10) / 11;
+  d->dbits = (bits + d->passes - 1) / d->passes;
+  d->radix = 1u << d->dbits;
+  const uint32_t nu = p->num_particles, ntot = nu + p->num_birth;
+  d->tiles_sort = (nu + SORT_TILE - 1) / SORT_TILE;
+  d->tiles_seg = (nu + SEG_TILE - 1) / SEG_TILE;
+  d->tiles_cell = (d->C + CELL_TILE - 1) / CELL_TILE;
+  d->tiles_norm = (ntot + NORM_TILE - 1) / NORM_TILE;
+  return DOG_OK;
+}
+
+// Carve every array out of the workspace (base == nullptr: only count).  Returns bytes.
+size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> void * {
+    off = (off + 255) & ~(size_t)255;
+    void *ptr = base ? base + off : nullptr;
+    off += bytes;
+    return ptr;
+  };
+  const size_t nu = p.num_particles, nb = p.num_birth, C = d.C;
+  const bool record = (p.flags & DOG_RECORD) != 0;
+  B->ctl = (DevCtl *)take(sizeof(DevCtl));
+  float **pf[] = {&B->Bx, &B->By, &B->Bvx, &B->Bvy, &B->Bw, &B->Ax, &B->Ay, &B->Avx, &B->Avy, &B->Aw, &B->wn};
+  for (auto q : pf) *q = (float *)take(4 * nu);
+  uint32_t **pu[] = {&B->key_pred, &B->key_sorted, &B->perm};
+  for (auto q : pu) *q = (uint32_t *)take(4 * nu);
+  B->key_t0 = B->val_t0 = B->key_t1 = B->val_t1 = nullptr;
+  if (d.passes >= 2) {
+    B->key_t0 = (uint32_t *)take(4 * nu);
+    B->val_t0 = (uint32_t *)take(4 * nu);
+  }
+  if (d.passes >= 3) {
+    B->key_t1 = (uint32_t *)take(4 * nu);
+    B->val_t1 = (uint32_t *)take(4 * nu);
+  }
+  B->rsrc = record ? (uint32_t *)take(4 * nu) : nullptr;
+  float **pb[] = {&B->bx, &B->by, &B->bvx, &B->bvy, &B->bw};
+  for (auto q : pb) *q = (float *)take(4 * (nb ? nb : 1));
+  B->bcell = record ? (uint32_t *)take(4 * (nb ? nb : 1)) : nullptr;
+  B->bassoc = record ? (uint32_t *)take(4 * (nb ? nb : 1)) : nullptr;
+  float **pc[] = {&B->mF, &B->zO, &B->zF, &B->pA, &B->zv, &B->sgv, &B->mO, &B->rho_p, &B->rho_b,
+                  &B->pO, &B->mean_x, &B->mean_y, &B->var_x, &B->var_y, &B->cov, &B->mpred,
+                  &B->muA, &B->muU, &B->paeff};
+  for (auto q : pc) *q = (float *)take(4 * C);
+  B->S = (unsigned long long *)take(8 * C);
+  B->A = (unsigned long long *)take(8 * C);
+  B->tag = (uint32_t *)take(4 * C);
+  B->cstart = (uint32_t *)take(4 * C);
+  B->cend = (uint32_t *)take(4 * C);
+  B->bl_cell = (uint32_t *)take(4 * C);
+  B->bl_R = (unsigned long long *)take(8 * C);
+  B->hist = (uint32_t *)take(4 * 2048 * (size_t)d.passes);
+  B->lb_sort = (uint32_t *)take(4 * (size_t)d.passes * d.tiles_sort * d.radix);
+  B->seg_st = (uint32_t *)take(4 * (size_t)d.tiles_seg);
+  B->seg_v = (unsigned long long *)take(8 * 4 * (size_t)d.tiles_seg);
+  B->cell_st = (uint32_t *)take(4 * (size_t)d.tiles_cell);
+  B->cell_v = (unsigned long long *)take(8 * 4 * (size_t)d.tiles_cell);
+  B->cdf_st = (uint32_t *)take(4 * (size_t)d.tiles_norm);
+  B->cdf_v = (unsigned long long *)take(8 * 2 * (size_t)d.tiles_norm);
+  B->mom_st = (uint32_t *)take(4 * (size_t)d.tiles_norm);
+  B->mom_v = (unsigned long long *)take(8 * 10 * (size_t)d.tiles_norm);
+  return (off + 255) & ~(size_t)255;
+}
+
+const char *KNAMES[MAX_KERNELS] = {"k_tick", "k_predict", "k_sort_pass0", "k_sort_pass1", "k_sort_pass2",
+                                   "k_segsum", "k_cell", "k_birth", "k_normalise", "k_resample", "", ""};
+
+}  // namespace
+
+struct dog_filter {
+  dog_params p;
+  Derived d;
+  KParams K;
+  DevBufs B;
+  cudaStream_t st;
+  char *ws;
+  size_t ws_bytes;
+  bool has_grid = false, radar = false;
+  bool dt_valid = false;
+  float dt = 0.0f;
+  uint32_t frame = 0;  // host mirror of DevCtl::frame
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  bool use_graph = true;
+  // profiling
+  bool profile = false;
+  std::vector<cudaEvent_t> ev;  // PROFILE_RING * (MAX_KERNELS + 1)
+  int ring_head = 0, ring_count = 0;
+  int nk = 0;
+  int birth_grid = 1;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) {
+  if (e == cudaSuccess) return DOG_OK;
+  (void)cudaGetLastError();
+  return DOG_ERR_CUDA;
+}
+
+#define DOG_CUDA(x)                              \
+  do {                                           \
+    const cudaError_t e_ = (x);                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+// the kernels of one frame, in order; ev (optional) are recorded around each kernel
+int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
+  const KParams &K = f->K;
+  const DevBufs &B = f->B;
+  cudaStream_t st = f->st;
+  int k = 0;
+  auto mark = [&]() {
+    if (ev) cudaEventRecord(ev[k], st);
+  };
+  mark();
+  k_tick<<<1, 256, 0, st>>>(B, 2048 * K.passes);
+  ++k; mark();
+  const uint32_t pred_grid = (K.nu + PRED_TILE - 1) / PRED_TILE;
+  k_predict<<<pred_grid, PRED_BLOCK, 4u * K.passes * K.radix, st>>>(K, B);
+  ++k; mark();
+  const size_t ssm = sort_smem_bytes(K.radix);
+  const uint32_t *kin = B.key_pred, *vin = nullptr;
+  for (int p = 0; p < K.passes; ++p) {
+    uint32_t *kout, *vout;
+    if (p == K.passes - 1) {
+      kout = B.key_sorted;
+      vout = B.perm;
+    } else if (p == 0) {
+      kout = B.key_t0;
+      vout = B.val_t0;
+    } else {
+      kout = B.key_t1;
+      vout = B.val_t1;
+    }
+    k_sort_pass<<<K.tiles_sort, SORT_BLOCK, ssm, st>>>(K, B, kin, vin, kout, vout, p);
+    kin = kout;
+    vin = vout;
+    ++k; mark();
+  }
+  if (radar) k_segsum<true><<<K.tiles_seg, SEG_BLOCK, 0, st>>>(K, B);
+  else k_segsum<false><<<K.tiles_seg, SEG_BLOCK, 0, st>>>(K, B);
+  ++k; mark();
+  if (radar) k_cell<true><<<K.tiles_cell, CELL_BLOCK, 0, st>>>(K, B);
+  else k_cell<false><<<K.tiles_cell, CELL_BLOCK, 0, st>>>(K, B);
+  ++k; mark();
+  if (radar) k_birth<true><<<f->birth_grid, BIRTH_BLOCK, 0, st>>>(K, B);
+  else k_birth<false><<<f->birth_grid, BIRTH_BLOCK, 0, st>>>(K, B);
+  ++k; mark();
+  if (radar) k_normalise<true><<<K.tiles_norm, NORM_BLOCK, 0, st>>>(K, B);
+  else k_normalise<false><<<K.tiles_norm, NORM_BLOCK, 0, st>>>(K, B);
+  ++k; mark();
+  k_resample<<<K.tiles_norm, RES_BLOCK, 0, st>>>(K, B);
+  ++k; mark();
+  return cuda_fail(cudaGetLastError());
+}
+
+int read_err(dog_filter *f) {
+  DevCtl h;
+  DOG_CUDA(cudaMemcpyAsync(&h, f->B.ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, f->st));
+  DOG_CUDA(cudaStreamSynchronize(f->st));
+  if (h.err) {
+    const uint32_t zero = 0;
+    DOG_CUDA(cudaMemcpyAsync(&f->B.ctl->err, &zero, 4, cudaMemcpyHostToDevice, f->st));
+    DOG_CUDA(cudaStreamSynchronize(f->st));
+    if (h.err & ERR_INPUT) return DOG_ERR_INPUT;
+    return DOG_ERR_TIMEOUT;
+  }
+  return DOG_OK;
+}
+
+// zero the look-back status words and cell tags (needed whenever the frame counter is set
+// to a value that earlier frames may have used as an epoch)
+int reset_epochs(dog_filter *f) {
+  const Derived &d = f->d;
+  DevBufs &B = f->B;
+  DOG_CUDA(cudaMemsetAsync(B.tag, 0, 4 * (size_t)d.C, f->st));
+  DOG_CUDA(cudaMemsetAsync(B.lb_sort, 0, 4 * (size_t)d.passes * d.tiles_sort * d.radix, f->st));
+  DOG_CUDA(cudaMemsetAsync(B.seg_st, 0, 4 * (size_t)d.tiles_seg, f->st));
+  DOG_CUDA(cudaMemsetAsync(B.cell_st, 0, 4 * (size_t)d.tiles_cell, f->st));
+  DOG_CUDA(cudaMemsetAsync(B.cdf_st, 0, 4 * (size_t)d.tiles_norm, f->st));
+  DOG_CUDA(cudaMemsetAsync(B.mom_st, 0, 4 * (size_t)d.tiles_norm, f->st));
+  return DOG_OK;
+}
+
+cudaMemcpyKind kind_to(int mem) { return mem == DOG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+cudaMemcpyKind kind_from(int mem) { return mem == DOG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+
+}  // namespace
+
+extern "C" {
+
+const char *dog_error_string(int code) {
+  switch (code) {
+    case DOG_OK: return "ok";
+    case DOG_ERR_INVALID_ARG: return "invalid argument";
+    case DOG_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+    case DOG_ERR_CUDA: return "CUDA runtime error";
+    case DOG_ERR_TIMEOUT: return "device-side bounded wait timed out";
+    case DOG_ERR_INPUT: return "input outside its domain";
+    case DOG_ERR_BAD_STATE: return "call not valid in the current state";
+    case DOG_ERR_UNSUPPORTED: return "size beyond the supported maximum";
+    default: return "unknown error";
+  }
+}
+
+int dog_workspace_bytes(const dog_params *params, size_t *out_bytes) {
+  if (!out_bytes) return DOG_ERR_INVALID_ARG;
+  Derived d;
+  const int rc = check_params(params, &d);
+  if (rc) return rc;
+  DevBufs B;
+  *out_bytes = carve(*params, d, nullptr, &B);
+  return DOG_OK;
+}
+
+int dog_kernels_per_step(const dog_filter *f) { return f ? f->nk : 0; }
+
+int dog_create(const dog_params *params, void *d_workspace, size_t workspace_bytes, void *cuda_stream,
+               dog_filter **out) {
+  if (!out || !d_workspace) return DOG_ERR_INVALID_ARG;
+  *out = nullptr;
+  Derived d;
+  int rc = check_params(params, &d);
+  if (rc) return rc;
+  if (((uintptr_t)d_workspace & 255) != 0) return DOG_ERR_INVALID_ARG;
+  DevBufs B;
+  const size_t need = carve(*params, d, nullptr, &B);
+  if (workspace_bytes < need) return DOG_ERR_WORKSPACE_TOO_SMALL;
+  dog_filter *f = new (std::nothrow) dog_filter();
+  if (!f) return DOG_ERR_INVALID_ARG;
+  f->p = *params;
+  f->d = d;
+  f->st = (cudaStream_t)cuda_stream;
+  f->ws = (char *)d_workspace;
+  f->ws_bytes = workspace_bytes;
+  carve(*params, d, f->ws, &f->B);
+  KParams &K = f->K;
+  K.W = params->width;
+  K.H = params->height;
+  K.C = d.C;
+  K.s = params->cell_size;
+  K.nu = params->num_particles;
+  K.nu_b = params->num_birth;
+  K.p_S = params->p_S;
+  K.p_B = params->p_B;
+  K.alpha = params->alpha_free;
+  K.sigma_pos = params->sigma_pos;
+  K.sigma_vel = params->sigma_vel;
+  K.sigma_B = params->sigma_birth_vel;
+  K.sensor_x = params->sensor_x;
+  K.sensor_y = params->sensor_y;
+  K.seed_lo = (uint32_t)params->seed;
+  K.seed_hi = (uint32_t)(params->seed >> 32);
+  K.flags = params->flags;
+  K.passes = d.passes;
+  K.dbits = d.dbits;
+  K.radix = d.radix;
+  K.tiles_sort = d.tiles_sort;
+  K.tiles_seg = d.tiles_seg;
+  K.tiles_cell = d.tiles_cell;
+  K.tiles_norm = d.tiles_norm;
+  f->nk = 7 + d.passes;
+  f->profile = (params->flags & DOG_PROFILE) != 0;
+  f->use_graph = !(params->flags & DOG_NO_GRAPH) && f->st != nullptr && !f->profile;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  f->birth_grid = sms * 4;
+  const size_t ssm = sort_smem_bytes(d.radix);
+  cudaError_t e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f->ws, 0, need, f->st);
+  if (e == cudaSuccess) {
+    k_init<<<sms * 8, 256, 0, f->st>>>(K, f->B);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && f->profile) {
+    f->ev.assign((size_t)PROFILE_RING * (MAX_KERNELS + 1), nullptr);
+    for (auto &x : f->ev)
+      if (e == cudaSuccess) e = cudaEventCreate(&x);
+  }
+  if (e != cudaSuccess) {
+    for (auto &x : f->ev)
+      if (x) cudaEventDestroy(x);
+    delete f;
+    return cuda_fail(e);
+  }
+  *out = f;
+  return DOG_OK;
+}
+
+void dog_destroy(dog_filter *f) {
+  if (!f) return;
+  if (f->st) cudaStreamSynchronize(f->st);
+  for (auto &g : f->gexec)
+    if (g) cudaGraphExecDestroy(g);
+  for (auto &x : f->ev)
+    if (x) cudaEventDestroy(x);
+  delete f;
+}
+
+int dog_set_measurement_grid(dog_filter *f, const dog_meas_grid *g, int mem_kind) {
+  if (!f || !g || !g->m_occ || !g->m_free) return DOG_ERR_INVALID_ARG;
+  if (mem_kind != DOG_HOST && mem_kind != DOG_DEVICE) return DOG_ERR_INVALID_ARG;
+  const bool radar = g->p_A != nullptr;
+  if (radar && (!g->z_vr || !g->sigma_vr)) return DOG_ERR_INVALID_ARG;
+  const size_t C = f->d.C;
+  if (mem_kind == DOG_HOST) {
+    for (size_t c = 0; c < C; ++c) {
+      const float a = g->m_occ[c], b = g->m_free[c];
+      if (!(a >= 0.0f && a <= 1.0f && b >= 0.0f && b <= 1.0f && a + b <= 1.000001f)) return DOG_ERR_INPUT;
+      if (radar) {
+        const float pa = g->p_A[c];
+        if (!(pa >= 0.0f && pa <= 1.0f)) return DOG_ERR_INPUT;
+        if (pa > 0.0f && !(g->sigma_vr[c] > 0.0f)) return DOG_ERR_INPUT;
+        if (!std::isfinite(g->z_vr[c])) return DOG_ERR_INPUT;
+      }
+    }
+  }
+  const cudaMemcpyKind kd = kind_from(mem_kind);
+  DOG_CUDA(cudaMemcpyAsync(f->B.zO, g->m_occ, 4 * C, kd, f->st));
+  DOG_CUDA(cudaMemcpyAsync(f->B.zF, g->m_free, 4 * C, kd, f->st));
+  if (radar) {
+    DOG_CUDA(cudaMemcpyAsync(f->B.pA, g->p_A, 4 * C, kd, f->st));
+    DOG_CUDA(cudaMemcpyAsync(f->B.zv, g->z_vr, 4 * C, kd, f->st));
+    DOG_CUDA(cudaMemcpyAsync(f->B.sgv, g->sigma_vr, 4 * C, kd, f->st));
+  }
+  if (mem_kind == DOG_DEVICE) {
+    k_validate<<<256, 256, 0, f->st>>>(f->K, f->B, radar ? 1 : 0);
+    DOG_CUDA(cudaGetLastError());
+  } else {
+    DOG_CUDA(cudaStreamSynchronize(f->st));  // the caller may reuse its host arrays
+  }
+  f->has_grid = true;
+  f->radar = radar;
+  return DOG_OK;
+}
+
+int dog_step(dog_filter *f, float dt) {
+  if (!f) return DOG_ERR_INVALID_ARG;
+  if (!(dt >= 0.0f) || !std::isfinite(dt)) return DOG_ERR_INVALID_ARG;
+  if (!f->has_grid) return DOG_ERR_BAD_STATE;
+  if (!f->dt_valid || dt != f->dt) {
+    const float h = dt;  // pageable source: staged before cudaMemcpyAsync returns
+    DOG_CUDA(cudaMemcpyAsync(&f->B.ctl->dt, &h, 4, cudaMemcpyHostToDevice, f->st));
+    f->dt = dt;
+    f->dt_valid = true;
+  }
+  const int gi = f->radar ? 1 : 0;
+  if (f->profile) {
+    cudaEvent_t *ev = &f->ev[(size_t)f->ring_head * (MAX_KERNELS + 1)];
+    const int rc = enqueue_frame(f, f->radar, ev);
+    if (rc) return rc;
+    f->ring_head = (f->ring_head + 1) % PROFILE_RING;
+    if (f->ring_count < PROFILE_RING) ++f->ring_count;
+  } else if (f->use_graph) {
+    if (!f->gexec[gi]) {
+      cudaGraph_t graph;
+      DOG_CUDA(cudaStreamBeginCapture(f->st, cudaStreamCaptureModeThreadLocal));
+      const int rc = enqueue_frame(f, f->radar, nullptr);
+      const cudaError_t e = cudaStreamEndCapture(f->st, &graph);
+      if (rc) return rc;
+      DOG_CUDA(e);
+      const cudaError_t e2 = cudaGraphInstantiate(&f->gexec[gi], graph, 0);
+      cudaGraphDestroy(graph);
+      DOG_CUDA(e2);
+    }
+    DOG_CUDA(cudaGraphLaunch(f->gexec[gi], f->st));
+  } else {
+    const int rc = enqueue_frame(f, f->radar, nullptr);
+    if (rc) return rc;
+  }
+  f->frame += 1;
+  return DOG_OK;
+}
+
+int dog_sync(dog_filter *f) {
+  if (!f) return DOG_ERR_INVALID_ARG;
+  return read_err(f);
+}
+
+int dog_get_cells(dog_filter *f, const dog_cells *out, int mem_kind) {
+  if (!f || !out) return DOG_ERR_INVALID_ARG;
+  if (mem_kind != DOG_HOST && mem_kind != DOG_DEVICE) return DOG_ERR_INVALID_ARG;
+  const size_t n = 4 * (size_t)f->d.C;
+  const cudaMemcpyKind kd = kind_to(mem_kind);
+  float *dst[] = {out->m_occ, out->m_free, out->rho_p, out->rho_b, out->p_occ,
+                  out->mean_vx, out->mean_vy, out->var_vx, out->var_vy, out->cov_vxy};
+  const float *src[] = {f->B.mO, f->B.mF, f->B.rho_p, f->B.rho_b, f->B.pO,
+                        f->B.mean_x, f->B.mean_y, f->B.var_x, f->B.var_y, f->B.cov};
+  for (int k = 0; k < 10; ++k)
+    if (dst[k]) DOG_CUDA(cudaMemcpyAsync(dst[k], src[k], n, kd, f->st));
+  return read_err(f);
+}
+
+int dog_get_state(dog_filter *f, const dog_state *out, int mem_kind, uint32_t *frame) {
+  if (!f || !out) return DOG_ERR_INVALID_ARG;
+  if (mem_kind != DOG_HOST && mem_kind != DOG_DEVICE) return DOG_ERR_INVALID_ARG;
+  const size_t n = 4 * (size_t)f->p.num_particles;
+  const cudaMemcpyKind kd = kind_to(mem_kind);
+  float *dst[] = {out->x, out->y, out->vx, out->vy, out->w};
+  const float *src[] = {f->B.Bx, f->B.By, f->B.Bvx, f->B.Bvy, f->B.Bw};
+  for (int k = 0; k < 5; ++k)
+    if (dst[k]) DOG_CUDA(cudaMemcpyAsync(dst[k], src[k], n, kd, f->st));
+  if (out->m_free) DOG_CUDA(cudaMemcpyAsync(out->m_free, f->B.mF, 4 * (size_t)f->d.C, kd, f->st));
+  const int rc = read_err(f);
+  if (frame) *frame = f->frame;
+  return rc;
+}
+
+int dog_set_state(dog_filter *f, const dog_state *in, int mem_kind, uint32_t frame) {
+  if (!f || !in || !in->x || !in->y || !in->vx || !in->vy || !in->w || !in->m_free)
+    return DOG_ERR_INVALID_ARG;
+  if (mem_kind != DOG_HOST && mem_kind != DOG_DEVICE) return DOG_ERR_INVALID_ARG;
+  const size_t n = 4 * (size_t)f->p.num_particles;
+  const cudaMemcpyKind kd = kind_from(mem_kind);
+  const float *src[] = {in->x, in->y, in->vx, in->vy, in->w};
+  float *dst[] = {f->B.Bx, f->B.By, f->B.Bvx, f->B.Bvy, f->B.Bw};
+  for (int k = 0; k < 5; ++k) DOG_CUDA(cudaMemcpyAsync(dst[k], src[k], n, kd, f->st));
+  DOG_CUDA(cudaMemcpyAsync(f->B.mF, in->m_free, 4 * (size_t)f->d.C, kd, f->st));
+  const int rc = reset_epochs(f);
+  if (rc) return rc;
+  const uint32_t fr = frame;
+  DOG_CUDA(cudaMemcpyAsync(&f->B.ctl->frame, &fr, 4, cudaMemcpyHostToDevice, f->st));
+  DOG_CUDA(cudaStreamSynchronize(f->st));
+  f->frame = frame;
+  return DOG_OK;
+}
+
+int dog_get_debug(dog_filter *f, int which, void *out, int mem_kind) {
+  if (!f || !out || which < 0 || which >= DOG_DBG_COUNT) return DOG_ERR_INVALID_ARG;
+  if (mem_kind != DOG_HOST && mem_kind != DOG_DEVICE) return DOG_ERR_INVALID_ARG;
+  const DevBufs &B = f->B;
+  const size_t nu = f->p.num_particles, nb = f->p.num_birth, C = f->d.C;
+  const bool record = (f->p.flags & DOG_RECORD) != 0;
+  const void *src = nullptr;
+  size_t bytes = 0;
+  bool masked = false;
+  switch (which) {
+    case DOG_DBG_PRED_X: src = B.Ax; bytes = 4 * nu; break;
+    case DOG_DBG_PRED_Y: src = B.Ay; bytes = 4 * nu; break;
+    case DOG_DBG_PRED_VX: src = B.Avx; bytes = 4 * nu; break;
+    case DOG_DBG_PRED_VY: src = B.Avy; bytes = 4 * nu; break;
+    case DOG_DBG_PRED_W: src = B.Aw; bytes = 4 * nu; break;
+    case DOG_DBG_KEY: src = B.key_pred; bytes = 4 * nu; break;
+    case DOG_DBG_PERM: src = B.perm; bytes = 4 * nu; break;
+    case DOG_DBG_CELL_START: src = B.cstart; bytes = 4 * C; masked = true; break;
+    case DOG_DBG_CELL_END: src = B.cend; bytes = 4 * C; masked = true; break;
+    case DOG_DBG_SUM_W: src = B.S; bytes = 8 * C; masked = true; break;
+    case DOG_DBG_SUM_GW: src = B.A; bytes = 8 * C; masked = true; break;
+    case DOG_DBG_M_OCC_PRED: src = B.mpred; bytes = 4 * C; break;
+    case DOG_DBG_MU_A: src = B.muA; bytes = 4 * C; break;
+    case DOG_DBG_MU_UA: src = B.muU; bytes = 4 * C; break;
+    case DOG_DBG_W_NORM: src = B.wn; bytes = 4 * nu; break;
+    case DOG_DBG_BIRTH_X: src = B.bx; bytes = 4 * nb; break;
+    case DOG_DBG_BIRTH_Y: src = B.by; bytes = 4 * nb; break;
+    case DOG_DBG_BIRTH_VX: src = B.bvx; bytes = 4 * nb; break;
+    case DOG_DBG_BIRTH_VY: src = B.bvy; bytes = 4 * nb; break;
+    case DOG_DBG_BIRTH_W: src = B.bw; bytes = 4 * nb; break;
+    case DOG_DBG_BIRTH_CELL: src = B.bcell; bytes = 4 * nb; break;
+    case DOG_DBG_BIRTH_ASSOC: src = B.bassoc; bytes = 4 * nb; break;
+    case DOG_DBG_RESAMPLE_SRC: src = B.rsrc; bytes = 4 * nu; break;
+    case DOG_DBG_SCALARS: break;
+    default: return DOG_ERR_INVALID_ARG;
+  }
+  if ((which == DOG_DBG_BIRTH_CELL || which == DOG_DBG_BIRTH_ASSOC || which == DOG_DBG_RESAMPLE_SRC) && !record)
+    return DOG_ERR_BAD_STATE;
+  DOG_CUDA(cudaStreamSynchronize(f->st));
+  if (which == DOG_DBG_SCALARS) {
+    DevCtl h;
+    DOG_CUDA(cudaMemcpy(&h, B.ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost));
+    const unsigned long long v[4] = {h.frame, h.W_total, h.R_total, h.u_offset};
+    DOG_CUDA(cudaMemcpy(out, v, sizeof(v), mem_kind == DOG_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+    return read_err(f);
+  }
+  if (!masked) {
+    if (bytes) DOG_CUDA(cudaMemcpyAsync(out, src, bytes, kind_to(mem_kind), f->st));
+    return read_err(f);
+  }
+  // cell arrays valid only where the cell received particles this frame (tag == frame)
+  std::vector<uint32_t> tag(C);
+  std::vector<unsigned char> buf(bytes);
+  DOG_CUDA(cudaMemcpy(tag.data(), B.tag, 4 * C, cudaMemcpyDeviceToHost));
+  DOG_CUDA(cudaMemcpy(buf.data(), src, bytes, cudaMemcpyDeviceToHost));
+  const size_t es = bytes / C;
+  for (size_t c = 0; c < C; ++c)
+    if (tag[c] != f->frame || f->frame == 0) std::memset(buf.data() + c * es, 0, es);
+  DOG_CUDA(cudaMemcpy(out, buf.data(), bytes, mem_kind == DOG_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+  return read_err(f);
+}
+
+int dog_profile_read(dog_filter *f, float *ms, const char **names, int max, int *n_out, int *steps_out) {
+  if (!f || !ms || max <= 0) return DOG_ERR_INVALID_ARG;
+  if (!f->profile) return DOG_ERR_BAD_STATE;
+  DOG_CUDA(cudaStreamSynchronize(f->st));
+  // kernel slots in launch order: tick, predict, sort passes, segsum, cell, birth, norm, resample
+  int slot_kind[MAX_KERNELS];
+  int nk = 0;
+  slot_kind[nk++] = 0;
+  slot_kind[nk++] = 1;
+  for (int p = 0; p < f->d.passes; ++p) slot_kind[nk++] = 2 + p;
+  for (int k = 5; k <= 9; ++k) slot_kind[nk++] = k;
+  const int n = nk < max ? nk : max;
+  for (int k = 0; k < n; ++k) ms[k] = 0.0f;
+  for (int r = 0; r < f->ring_count; ++r) {
+    const int slot = (f->ring_head - 1 - r + 2 * PROFILE_RING) % PROFILE_RING;
+    cudaEvent_t *ev = &f->ev[(size_t)slot * (MAX_KERNELS + 1)];
+    for (int k = 0; k < n; ++k) {
+      float t = 0.0f;
+      DOG_CUDA(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+      ms[k] += t;
+    }
+  }
+  if (names)
+    for (int k = 0; k < n; ++k) names[k] = KNAMES[slot_kind[k]];
+  if (n_out) *n_out = n;
+  if (steps_out) *steps_out = f->ring_count;
+  f->ring_count = 0;
+  return DOG_OK;
+}
+
+}  // extern "C"

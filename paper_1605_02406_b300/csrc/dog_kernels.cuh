@@ -1,0 +1,1087 @@
+// dog_kernels.cuh -- the per-frame kernels of the DS-PHD/MIB filter (Sect. VII, Alg. 1-7).
+//
+// Frame data flow (nu persistent particles, nu_b newborn slots, C cells):
+//   k_tick        frame counter, reset of per-frame counters and digit histograms
+//   k_predict     Alg. 1  B -> A: constant-velocity prediction with Philox process noise,
+//                          persistence weight, cell index; digit histograms for the sort
+//   k_sort_pass   Alg. 2  onesweep LSD radix pass(es) of (cell index, particle index)
+//   k_segsum      Alg. 2/3 cell ranges and exact fixed-point per-cell sums of w (and g w)
+//   k_cell        Alg. 3  occupancy prediction, DS update, newborn split, normalisers;
+//                          single-pass scan of the newborn masses -> list of birth cells
+//   k_birth       Alg. 5  newborn particles, slots proportional to the newborn mass
+//   k_normalise   Alg. 4/6 normalised persistent weights, velocity moments, scan of the
+//                          joint weights for resampling
+//   k_resample    Alg. 7  systematic resampling A + newborns -> B
+#pragma once
+#include "dog_common.cuh"
+#include "dog_math.cuh"
+
+namespace dog {
+
+// ====================================================================================
+// k_tick: begin a frame
+// ====================================================================================
+__global__ void k_tick(DevBufs B, int n_hist) {
+  for (int i = threadIdx.x; i < n_hist; i += blockDim.x) B.hist[i] = 0u;
+  if (threadIdx.x < CTR_COUNT) B.ctl->ctr[threadIdx.x] = 0ull;
+  if (threadIdx.x == 0) B.ctl->frame += 1u;
+}
+
+// ====================================================================================
+// k_init: initial state -- particles uniform over the grid, birth-distribution
+// velocities, weight 0 (frame 0 draws); free mass 0.
+// ====================================================================================
+__global__ void k_init(KParams P, DevBufs B) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  const float gx = __fmul_rn((float)P.W, P.s), gy = __fmul_rn((float)P.H, P.s);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P.nu; i += stride) {
+    const U4 r = philox(i, 0u, TAG_INIT, P.seed_lo, P.seed_hi);
+    float n0, n1;
+    gauss2(r.c, r.d, n0, n1);
+    B.Bx[i] = __fmul_rn(u01_co(r.a), gx);
+    B.By[i] = __fmul_rn(u01_co(r.b), gy);
+    B.Bvx[i] = __fmul_rn(P.sigma_B, n0);
+    B.Bvy[i] = __fmul_rn(P.sigma_B, n1);
+    B.Bw[i] = 0.0f;
+  }
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < P.C; c += stride) B.mF[c] = 0.0f;
+}
+
+// ====================================================================================
+// k_validate: measurement grid domain check (device-resident input)
+// ====================================================================================
+__global__ void k_validate(KParams P, DevBufs B, int radar) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  bool bad = false;
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < P.C; c += stride) {
+    const float a = B.zO[c], b = B.zF[c];
+    bad |= !(a >= 0.0f && a <= 1.0f && b >= 0.0f && b <= 1.0f && a + b <= 1.000001f);
+    if (radar) {
+      const float pa = B.pA[c];
+      bad |= !(pa >= 0.0f && pa <= 1.0f);
+      bad |= (pa > 0.0f) && !(B.sgv[c] > 0.0f);
+      bad |= !(fabsf(B.zv[c]) < 3.0e38f);
+    }
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&B.ctl->err, ERR_INPUT);
+}
+
+// ====================================================================================
+// k_predict (Alg. 1): Eq. process with per-frame Gaussian noise, Eq. particle_persistence,
+// cell index floor(x/s), floor(y/s) (outside the grid: nearest border cell, weight 0).
+// Each block handles 4096 particles, 4 per thread per round with 16-byte accesses, and
+// accumulates the digit histograms of all sort passes in shared memory.
+// ====================================================================================
+constexpr int PRED_BLOCK = 256, PRED_ROUNDS = 4, PRED_TILE = PRED_BLOCK * 4 * PRED_ROUNDS;
+
+__device__ __forceinline__ void predict_one(const KParams &P, uint32_t i, uint32_t frame, float T,
+                                            float &x, float &y, float &vx, float &vy, float &w,
+                                            uint32_t &key) {
+  const U4 r = philox(i, frame, TAG_PREDICT, P.seed_lo, P.seed_hi);
+  float n0, n1, n2, n3;
+  gauss2(r.a, r.b, n0, n1);
+  gauss2(r.c, r.d, n2, n3);
+  x = __fadd_rn(__fadd_rn(x, __fmul_rn(T, vx)), __fmul_rn(P.sigma_pos, n0));
+  y = __fadd_rn(__fadd_rn(y, __fmul_rn(T, vy)), __fmul_rn(P.sigma_pos, n1));
+  vx = __fadd_rn(vx, __fmul_rn(P.sigma_vel, n2));
+  vy = __fadd_rn(vy, __fmul_rn(P.sigma_vel, n3));
+  w = __fmul_rn(P.p_S, w);
+  const float fx = __fdiv_rn(x, P.s), fy = __fdiv_rn(y, P.s);
+  const float Wf = (float)P.W, Hf = (float)P.H;
+  const bool in = fx >= 0.0f && fx < Wf && fy >= 0.0f && fy < Hf;
+  const int col = !(fx >= 0.0f) ? 0 : (!(fx < Wf) ? P.W - 1 : (int)fx);
+  const int row = !(fy >= 0.0f) ? 0 : (!(fy < Hf) ? P.H - 1 : (int)fy);
+  if (!in) w = 0.0f;
+  key = (uint32_t)row * (uint32_t)P.W + (uint32_t)col;
+}
+
+__global__ void __launch_bounds__(PRED_BLOCK) k_predict(KParams P, DevBufs B) {
+  extern __shared__ uint32_t sh_hist[];  // [passes][radix]
+  const uint32_t nh = (uint32_t)P.passes * P.radix;
+  for (uint32_t k = threadIdx.x; k < nh; k += PRED_BLOCK) sh_hist[k] = 0u;
+  __syncthreads();
+  const uint32_t frame = B.ctl->frame;
+  const float T = B.ctl->dt;
+  const uint32_t mask = P.radix - 1u;
+  for (int rnd = 0; rnd < PRED_ROUNDS; ++rnd) {
+    const uint32_t i0 = blockIdx.x * PRED_TILE + (uint32_t)rnd * (PRED_BLOCK * 4) + threadIdx.x * 4;
+    uint32_t key[4];
+    bool valid[4];
+    if (i0 + 4 <= P.nu) {
+      float4 x = *reinterpret_cast<const float4 *>(B.Bx + i0);
+      float4 y = *reinterpret_cast<const float4 *>(B.By + i0);
+      float4 vx = *reinterpret_cast<const float4 *>(B.Bvx + i0);
+      float4 vy = *reinterpret_cast<const float4 *>(B.Bvy + i0);
+      float4 w = *reinterpret_cast<const float4 *>(B.Bw + i0);
+      predict_one(P, i0 + 0, frame, T, x.x, y.x, vx.x, vy.x, w.x, key[0]);
+      predict_one(P, i0 + 1, frame, T, x.y, y.y, vx.y, vy.y, w.y, key[1]);
+      predict_one(P, i0 + 2, frame, T, x.z, y.z, vx.z, vy.z, w.z, key[2]);
+      predict_one(P, i0 + 3, frame, T, x.w, y.w, vx.w, vy.w, w.w, key[3]);
+      *reinterpret_cast<float4 *>(B.Ax + i0) = x;
+      *reinterpret_cast<float4 *>(B.Ay + i0) = y;
+      *reinterpret_cast<float4 *>(B.Avx + i0) = vx;
+      *reinterpret_cast<float4 *>(B.Avy + i0) = vy;
+      *reinterpret_cast<float4 *>(B.Aw + i0) = w;
+      *reinterpret_cast<uint4 *>(B.key_pred + i0) = make_uint4(key[0], key[1], key[2], key[3]);
+      valid[0] = valid[1] = valid[2] = valid[3] = true;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t i = i0 + k;
+        valid[k] = i < P.nu;
+        key[k] = 0u;
+        if (valid[k]) {
+          float x = B.Bx[i], y = B.By[i], vx = B.Bvx[i], vy = B.Bvy[i], w = B.Bw[i];
+          predict_one(P, i, frame, T, x, y, vx, vy, w, key[k]);
+          B.Ax[i] = x; B.Ay[i] = y; B.Avx[i] = vx; B.Avy[i] = vy; B.Aw[i] = w;
+          B.key_pred[i] = key[k];
+        }
+      }
+    }
+    // digit histograms: one shared-memory add per distinct digit per warp
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      for (int p = 0; p < P.passes; ++p) {
+        const uint32_t d = valid[k] ? ((key[k] >> (p * P.dbits)) & mask) : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(FULL, d);
+        if (d != 0xffffffffu && (peers & lanemask_lt()) == 0u)
+          atomicAdd(&sh_hist[p * P.radix + d], (uint32_t)__popc(peers));
+      }
+    }
+  }
+  __syncthreads();
+  for (uint32_t k = threadIdx.x; k < nh; k += PRED_BLOCK) {
+    const uint32_t v = sh_hist[k];
+    if (v) atomicAdd(&B.hist[(k / P.radix) * 2048u + (k % P.radix)], v);
+  }
+}
+
+// ====================================================================================
+// k_sort_pass (Alg. 2, sort): one onesweep LSD radix pass (Adinets & Merrill, 2022) of
+// (cell index, particle index) pairs on a digit of up to 11 bits.  A tile of 4096 keys is
+// ranked stably in shared memory (per-warp histograms with match.any), its digit counts
+// are published immediately, the global digit offsets come from a bounded decoupled
+// look-back over earlier tiles, and the tile is scattered through shared memory so that
+// equal digits leave as contiguous runs.
+// ====================================================================================
+constexpr int SORT_BLOCK = 512, SORT_ITEMS = 8, SORT_WARPS = SORT_BLOCK / 32,
+              SORT_TILE = SORT_BLOCK * SORT_ITEMS;
+
+__host__ __device__ constexpr size_t sort_smem_bytes(uint32_t radix) {
+  // ranking: per-warp u16 histograms, later reused for the staged keys and values
+  return ((size_t)SORT_WARPS * radix * 2 > (size_t)SORT_TILE * 8 ? (size_t)SORT_WARPS * radix * 2
+                                                                  : (size_t)SORT_TILE * 8) +
+         (size_t)4 * radix * 4 + 128;
+}
+
+__device__ __forceinline__ uint32_t pack_digit(uint32_t ep5, uint32_t st, uint32_t cnt) {
+  return (ep5 << 27) | (st << 25) | cnt;
+}
+
+// exclusive scan of n <= 2048 values in shared memory by SORT_BLOCK threads
+__device__ void block_excl_scan_u32(const uint32_t *in, uint32_t *out, uint32_t n, uint32_t *s_warp) {
+  const uint32_t per = (n + SORT_BLOCK - 1) / SORT_BLOCK;  // <= 4
+  const uint32_t b = threadIdx.x * per;
+  uint32_t loc = 0;
+  for (uint32_t k = 0; k < per; ++k)
+    if (b + k < n) loc += in[b + k];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = loc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(FULL, inc, o);
+    if (lane >= (uint32_t)o) inc += t;
+  }
+  if (lane == 31) s_warp[warp] = inc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int w = 0; w < SORT_WARPS; ++w) {
+      const uint32_t t = s_warp[w];
+      s_warp[w] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+  uint32_t run = s_warp[warp] + inc - loc;
+  for (uint32_t k = 0; k < per; ++k)
+    if (b + k < n) {
+      const uint32_t v = in[b + k];
+      out[b + k] = run;
+      run += v;
+    }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(SORT_BLOCK, 2)
+    k_sort_pass(KParams P, DevBufs B, const uint32_t *__restrict__ keys_in,
+                const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
+                uint32_t *__restrict__ vals_out, int pass) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint32_t radix = P.radix;
+  const size_t big = sort_smem_bytes(radix) - (size_t)4 * radix * 4 - 128;
+  uint16_t *s_whist = reinterpret_cast<uint16_t *>(smem);      // [warps][radix]
+  uint32_t *s_keys = reinterpret_cast<uint32_t *>(smem);       // [tile] (after ranking)
+  uint32_t *s_vals = s_keys + SORT_TILE;                       // [tile]
+  uint32_t *s_cnt = reinterpret_cast<uint32_t *>(smem + big);  // [radix]
+  uint32_t *s_excl = s_cnt + radix;
+  uint32_t *s_base = s_excl + radix;
+  uint32_t *s_gst = s_base + radix;
+  uint32_t *s_misc = s_gst + radix;  // [32]: tile id, warp sums
+
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int shift = pass * P.dbits;
+  const uint32_t mask = radix - 1u;
+  if (tid == 0) s_misc[0] = (uint32_t)atomicAdd(&B.ctl->ctr[CTR_SORT0 + pass], 1ull);
+  for (uint32_t k = tid; k < SORT_WARPS * radix / 2; k += SORT_BLOCK)
+    reinterpret_cast<uint32_t *>(s_whist)[k] = 0u;
+  __syncthreads();
+  const uint32_t tile = s_misc[0];
+  const uint32_t ep5 = B.ctl->frame & 31u;
+  uint32_t *lb = B.lb_sort + ((size_t)pass * P.tiles_sort + tile) * radix;
+
+  // load: warp w covers positions [w*256, w*256+256) of the tile, item k at k*32 + lane
+  uint32_t key[SORT_ITEMS], val[SORT_ITEMS];
+  const uint32_t base = tile * SORT_TILE + warp * (32 * SORT_ITEMS);
+#pragma unroll
+  for (int k = 0; k < SORT_ITEMS; ++k) {
+    const uint32_t pos = base + k * 32 + lane;
+    const bool ok = pos < P.nu;
+    key[k] = ok ? __ldg(keys_in + pos) : 0xffffffffu;
+    val[k] = ok ? (vals_in ? __ldg(vals_in + pos) : pos) : 0u;
+  }
+  // stable rank within the warp, item by item
+  uint32_t rk[SORT_ITEMS];
+  const uint32_t lt = lanemask_lt();
+#pragma unroll
+  for (int k = 0; k < SORT_ITEMS; ++k) {
+    const uint32_t d = (key[k] >> shift) & mask;
+    const uint32_t peers = __match_any_sync(FULL, d);
+    const uint16_t pre = s_whist[warp * radix + d];
+    __syncwarp();
+    if ((peers & lt) == 0u) s_whist[warp * radix + d] = (uint16_t)(pre + __popc(peers));
+    __syncwarp();
+    rk[k] = pre + __popc(peers & lt);
+  }
+  __syncthreads();
+  // per digit: exclusive offsets of the warps, tile count, publish the tile aggregate
+  for (uint32_t d = tid; d < radix; d += SORT_BLOCK) {
+    uint32_t run = 0;
+    for (int w = 0; w < SORT_WARPS; ++w) {
+      const uint32_t c = s_whist[w * radix + d];
+      s_whist[w * radix + d] = (uint16_t)run;
+      run += c;
+    }
+    s_cnt[d] = run;
+    st_volatile(lb + d, pack_digit(ep5, tile == 0 ? ST_INCL : ST_AGG, run));
+  }
+  // global digit starts (exclusive scan of this pass's histogram)
+  __syncthreads();
+  for (uint32_t d = tid; d < radix; d += SORT_BLOCK) s_base[d] = B.hist[pass * 2048u + d];
+  __syncthreads();
+  block_excl_scan_u32(s_base, s_gst, radix, s_misc + 1);
+  block_excl_scan_u32(s_cnt, s_excl, radix, s_misc + 1);
+  // tile-local sorted position of each key
+  uint32_t lpos[SORT_ITEMS];
+#pragma unroll
+  for (int k = 0; k < SORT_ITEMS; ++k) {
+    const uint32_t d = (key[k] >> shift) & mask;
+    lpos[k] = s_excl[d] + s_whist[warp * radix + d] + rk[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < SORT_ITEMS; ++k) {
+    s_keys[lpos[k]] = key[k];
+    s_vals[lpos[k]] = val[k];
+  }
+  // decoupled look-back per digit
+  const uint32_t *lb_pass = B.lb_sort + (size_t)pass * P.tiles_sort * radix;
+  for (uint32_t d = tid; d < radix; d += SORT_BLOCK) {
+    uint32_t excl = 0;
+    if (tile > 0) {
+      long long t = (long long)tile - 1;
+      int spins = 0;
+      while (t >= 0) {
+        const uint32_t w = ld_volatile(lb_pass + (size_t)t * radix + d);
+        const uint32_t st = (w >> 25) & 3u;
+        if ((w >> 27) != ep5 || st == ST_NONE) {
+          if (++spins > SPIN_LIMIT) {
+            atomicOr(&B.ctl->err, ERR_TIMEOUT_SORT);
+            break;
+          }
+          if ((spins & 255) == 0 && ld_volatile(&B.ctl->err) != 0u) break;
+          __nanosleep(32);
+          continue;
+        }
+        excl += w & 0x1ffffffu;
+        if (st == ST_INCL) break;
+        --t;
+      }
+      st_volatile(lb + d, pack_digit(ep5, ST_INCL, (excl + s_cnt[d]) & 0x1ffffffu));
+    }
+    s_base[d] = s_gst[d] + excl - s_excl[d];
+  }
+  __syncthreads();
+  // scatter: runs of equal digits are contiguous in shared memory and in the output
+  for (uint32_t p = tid; p < SORT_TILE; p += SORT_BLOCK) {
+    const uint32_t k = s_keys[p];
+    const uint32_t gp = s_base[(k >> shift) & mask] + p;
+    if (gp < P.nu) {
+      keys_out[gp] = k;
+      vals_out[gp] = s_vals[p];
+    }
+  }
+}
+
+// ====================================================================================
+// Segmented sums over the sorted particles.  A thread owns ITEMS consecutive sorted
+// positions; segments are the cells (runs of equal keys).  Sums of segments that cross
+// thread and tile boundaries are carried by a block-wide segmented scan and a decoupled
+// look-back over tiles; the thread holding a segment's last position writes its total.
+// ====================================================================================
+constexpr int SEG_BLOCK = 256, SEG_ITEMS = 8, SEG_TILE = SEG_BLOCK * SEG_ITEMS;
+
+template <int N>
+struct Seg {
+  uint32_t f;  // a segment head lies in the covered range
+  unsigned long long v[N];
+};
+
+// (a then b): a head in b cuts off a
+template <int N>
+__device__ __forceinline__ Seg<N> seg_combine(const Seg<N> &a, const Seg<N> &b) {
+  Seg<N> r;
+  r.f = a.f | b.f;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.v[k] = b.f ? b.v[k] : a.v[k] + b.v[k];
+  return r;
+}
+
+template <int N>
+__device__ __forceinline__ Seg<N> seg_shfl_up(const Seg<N> &a, int o) {
+  Seg<N> r;
+  r.f = __shfl_up_sync(FULL, a.f, o);
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.v[k] = __shfl_up_sync(FULL, a.v[k], o);
+  return r;
+}
+
+// Block-wide exclusive segmented scan of per-thread aggregates (SEG_BLOCK threads).
+// Returns the thread's exclusive prefix; tile_total receives the whole block's value.
+template <int N>
+__device__ Seg<N> block_seg_excl(const Seg<N> &x, Seg<N> *s_w /* [SEG_BLOCK/32 + 1] */,
+                                 Seg<N> &tile_total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Seg<N> inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const Seg<N> t = seg_shfl_up(inc, o);
+    if (lane >= o) inc = seg_combine(t, inc);
+  }
+  if (lane == 31) s_w[warp] = inc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Seg<N> run;
+    run.f = 0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) run.v[k] = 0ull;
+    for (int w = 0; w < SEG_BLOCK / 32; ++w) {
+      const Seg<N> t = s_w[w];
+      s_w[w] = run;
+      run = seg_combine(run, t);
+    }
+    s_w[SEG_BLOCK / 32] = run;
+  }
+  __syncthreads();
+  Seg<N> prev = seg_shfl_up(inc, 1);
+  if (lane == 0) {
+    prev.f = 0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) prev.v[k] = 0ull;
+  }
+  tile_total = s_w[SEG_BLOCK / 32];
+  return seg_combine(s_w[warp], prev);
+}
+
+// Tile carry of a segmented scan: publish (a tile with a head is inclusive at once),
+// look back when the tile's leading run continues an earlier segment.
+template <int N>
+__device__ void seg_tile_carry(uint32_t *st, unsigned long long *vals, uint32_t tile, uint32_t epoch,
+                               const Seg<N> &tot, unsigned long long (&cin)[N], uint32_t *err,
+                               uint32_t errbit, unsigned long long *s_cin /* [N] */) {
+  if (threadIdx.x == 0) lb_publish<N>(st, vals, tile, epoch, tot.f ? ST_INCL : ST_AGG, tot.v);
+  if (threadIdx.x < 32) {
+    unsigned long long acc[N];
+    if (tile > 0) {
+      lb_lookback<N>(st, vals, tile, epoch, acc, err, errbit);
+    } else {
+#pragma unroll
+      for (int k = 0; k < N; ++k) acc[k] = 0ull;
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < N; ++k) s_cin[k] = acc[k];
+      if (!tot.f) {
+        unsigned long long inc[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) inc[k] = acc[k] + tot.v[k];
+        lb_publish<N>(st, vals, tile, epoch, ST_INCL, inc);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < N; ++k) cin[k] = s_cin[k];
+}
+
+// radial-velocity likelihood g (constant factor dropped; it cancels in mu_A)
+__device__ __forceinline__ float radar_lik(const KParams &P, float x, float y, float vx, float vy,
+                                           float zv, float sg) {
+  const float dx = __fsub_rn(x, P.sensor_x), dy = __fsub_rn(y, P.sensor_y);
+  const float r = __fsqrt_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)));
+  float vr = 0.0f;
+  if (r > 0.0f) vr = __fdiv_rn(__fadd_rn(__fmul_rn(dx, vx), __fmul_rn(dy, vy)), r);
+  const float d = __fdiv_rn(__fsub_rn(vr, zv), sg);
+  return exp_f(__fmul_rn(-0.5f, __fmul_rn(d, d)));
+}
+
+// load ITEMS consecutive u32 at position j0 (16-byte accesses when the run is interior)
+template <int ITEMS>
+__device__ __forceinline__ void load_run(const uint32_t *p, uint32_t j0, uint32_t n, uint32_t (&o)[ITEMS],
+                                         uint32_t fill) {
+  if (j0 + ITEMS <= n) {
+#pragma unroll
+    for (int k = 0; k < ITEMS; k += 4) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p + j0 + k));
+      o[k] = v.x; o[k + 1] = v.y; o[k + 2] = v.z; o[k + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) o[k] = (j0 + k < n) ? __ldg(p + j0 + k) : fill;
+  }
+}
+
+// k_segsum: cell ranges (Alg. 2) and S_c = sum of q40(w) (Eq. DS_particle_sum_pred as an
+// exact fixed-point sum), plus A_c = sum of q40(g w) where the cell has a radar likelihood.
+template <bool RADAR>
+__global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
+  constexpr int N = RADAR ? 2 : 1;
+  __shared__ Seg<N> s_w[SEG_BLOCK / 32 + 1];
+  __shared__ unsigned long long s_cin[N];
+  __shared__ uint32_t s_tile;
+  if (threadIdx.x == 0) s_tile = (uint32_t)atomicAdd(&B.ctl->ctr[CTR_SEG], 1ull);
+  __syncthreads();
+  const uint32_t tile = s_tile, frame = B.ctl->frame, epoch = frame & 0x3fffffffu;
+  const uint32_t j0 = tile * SEG_TILE + threadIdx.x * SEG_ITEMS;
+  uint32_t key[SEG_ITEMS], idx[SEG_ITEMS];
+  load_run<SEG_ITEMS>(B.key_sorted, j0, P.nu, key, 0xffffffffu);
+  load_run<SEG_ITEMS>(B.perm, j0, P.nu, idx, 0u);
+  const uint32_t kprev = (j0 > 0 && j0 <= P.nu) ? __ldg(B.key_sorted + j0 - 1) : 0xfffffffeu;
+  const uint32_t knext = (j0 + SEG_ITEMS < P.nu) ? __ldg(B.key_sorted + j0 + SEG_ITEMS) : 0xfffffffeu;
+  unsigned long long v[SEG_ITEMS][N];
+  uint32_t head = 0, tail = 0;
+  Seg<N> agg;
+  agg.f = 0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) agg.v[k] = 0ull;
+#pragma unroll
+  for (int it = 0; it < SEG_ITEMS; ++it) {
+    const uint32_t j = j0 + it;
+    const bool ok = j < P.nu;
+    const uint32_t kp = it == 0 ? kprev : key[it - 1];
+    const uint32_t kn = it == SEG_ITEMS - 1 ? knext : key[it + 1];
+    const bool h = ok && (j == 0 || key[it] != kp);
+    const bool t = ok && (j == P.nu - 1 || key[it] != kn);
+    head |= (uint32_t)h << it;
+    tail |= (uint32_t)t << it;
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[it][k] = 0ull;
+    if (ok) {
+      const uint32_t i = idx[it];
+      const float w = __ldg(B.Aw + i);
+      v[it][0] = q40(w);
+      if constexpr (RADAR) {
+        const uint32_t c = key[it];
+        if (__ldg(B.pA + c) > 0.0f) {
+          const float g = radar_lik(P, __ldg(B.Ax + i), __ldg(B.Ay + i), __ldg(B.Avx + i),
+                                    __ldg(B.Avy + i), __ldg(B.zv + c), __ldg(B.sgv + c));
+          v[it][N - 1] = q40(__fmul_rn(g, w));
+        }
+      }
+    }
+    Seg<N> e;
+    e.f = h;
+#pragma unroll
+    for (int k = 0; k < N; ++k) e.v[k] = v[it][k];
+    agg = seg_combine(agg, e);
+  }
+  Seg<N> tot;
+  const Seg<N> ex = block_seg_excl<N>(agg, s_w, tot);
+  unsigned long long cin[N];
+  seg_tile_carry<N>(B.seg_st, B.seg_v, tile, epoch, tot, cin, &B.ctl->err, ERR_TIMEOUT_SEG, s_cin);
+  unsigned long long run[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) run[k] = ex.f ? ex.v[k] : ex.v[k] + cin[k];
+#pragma unroll
+  for (int it = 0; it < SEG_ITEMS; ++it) {
+    const bool h = (head >> it) & 1u, t = (tail >> it) & 1u;
+#pragma unroll
+    for (int k = 0; k < N; ++k) run[k] = h ? v[it][k] : run[k] + v[it][k];
+    const uint32_t c = key[it];
+    if (h) B.cstart[c] = j0 + it;
+    if (t) {
+      B.cend[c] = j0 + it + 1;
+      B.S[c] = run[0];
+      if constexpr (RADAR) B.A[c] = run[N - 1];
+      B.tag[c] = frame;
+    }
+  }
+}
+
+// ====================================================================================
+// k_cell (Alg. 3 + the cell half of Alg. 4): per cell the predicted occupied mass
+// min(S, 1), the free-mass prediction, Dempster's rule with the measurement BBA, the
+// newborn / persistent split and the normalisers mu_A, mu_UA.  The newborn masses are
+// scanned in cell order (single pass, decoupled look-back) and the cells with newborn
+// mass are listed in order with their exclusive prefix for k_birth.
+// ====================================================================================
+constexpr int CELL_BLOCK = 256, CELL_ITEMS = 4, CELL_TILE = CELL_BLOCK * CELL_ITEMS;
+
+__device__ __forceinline__ void cell_update(const KParams &P, float mp, float mFprev, float zO, float zF,
+                                            float &mO, float &mF, float &rb) {
+  const float mFp = fminf(__fmul_rn(P.alpha, mFprev), __fsub_rn(1.0f, mp));
+  const float mT = __fsub_rn(__fsub_rn(1.0f, mp), mFp);
+  const float zT = __fsub_rn(__fsub_rn(1.0f, zO), zF);
+  const float K = __fadd_rn(__fmul_rn(mp, zF), __fmul_rn(mFp, zO));
+  const float den = __fsub_rn(1.0f, K);
+  if (den < 1e-6f) {
+    mO = mp;
+    mF = mFp;
+  } else {
+    const float nO = __fadd_rn(__fadd_rn(__fmul_rn(mp, zO), __fmul_rn(mp, zT)), __fmul_rn(mT, zO));
+    const float nF = __fadd_rn(__fadd_rn(__fmul_rn(mFp, zF), __fmul_rn(mFp, zT)), __fmul_rn(mT, zF));
+    mO = __fdiv_rn(nO, den);
+    mF = __fdiv_rn(nF, den);
+  }
+  rb = 0.0f;
+  if (zO > 0.0f) {
+    const float pb = __fmul_rn(P.p_B, __fsub_rn(1.0f, mp));
+    const float d = __fadd_rn(mp, pb);
+    if (d > 0.0f) rb = __fdiv_rn(__fmul_rn(mO, pb), d);
+    if (rb > mO) rb = mO;
+  }
+}
+
+template <bool RADAR>
+__global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
+  __shared__ unsigned long long s_wq[CELL_BLOCK / 32 + 1];
+  __shared__ uint32_t s_wn[CELL_BLOCK / 32 + 1];
+  __shared__ unsigned long long s_cin[2];
+  __shared__ uint32_t s_tile;
+  if (threadIdx.x == 0) s_tile = (uint32_t)atomicAdd(&B.ctl->ctr[CTR_CELL], 1ull);
+  __syncthreads();
+  const uint32_t tile = s_tile, frame = B.ctl->frame, epoch = frame & 0x3fffffffu;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long qex[CELL_ITEMS];
+  uint32_t nex[CELL_ITEMS];
+  bool has[CELL_ITEMS];
+  unsigned long long wq = 0ull;  // running sums of this warp, in cell order
+  uint32_t wn = 0u;
+#pragma unroll
+  for (int it = 0; it < CELL_ITEMS; ++it) {
+    const uint32_t c = tile * CELL_TILE + warp * (32 * CELL_ITEMS) + it * 32 + lane;
+    unsigned long long qb = 0ull;
+    if (c < P.C) {
+      const bool occ = B.tag[c] == frame;
+      const unsigned long long S = occ ? B.S[c] : 0ull;
+      const float Sf = fx40_to_f(S);
+      const float mp = fminf(Sf, 1.0f);
+      float mO, mF, rb;
+      cell_update(P, mp, B.mF[c], B.zO[c], B.zF[c], mO, mF, rb);
+      const float rp = __fsub_rn(mO, rb);
+      B.mpred[c] = mp;
+      B.mO[c] = mO;
+      B.mF[c] = mF;
+      B.rho_b[c] = rb;
+      B.rho_p[c] = rp;
+      B.pO[c] = __fadd_rn(mO, __fmul_rn(0.5f, __fsub_rn(__fsub_rn(1.0f, mO), mF)));
+      B.muU[c] = (S > 0ull) ? __fdiv_rn(rp, Sf) : 0.0f;
+      float muA = 0.0f, pa = 0.0f;
+      if constexpr (RADAR) {
+        const unsigned long long A = occ ? B.A[c] : 0ull;
+        if (A > 0ull) {
+          muA = __fdiv_rn(rp, fx40_to_f(A));
+          pa = B.pA[c];
+        }
+        B.paeff[c] = pa;
+      }
+      B.muA[c] = muA;
+      if (!occ) {
+        B.mean_x[c] = 0.0f; B.mean_y[c] = 0.0f; B.var_x[c] = 0.0f; B.var_y[c] = 0.0f; B.cov[c] = 0.0f;
+      }
+      qb = q40(rb);
+    }
+    has[it] = qb > 0ull;
+    // inclusive warp scan of (qb, has)
+    unsigned long long sq = qb;
+    uint32_t sn = has[it] ? 1u : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long tq = __shfl_up_sync(FULL, sq, o);
+      const uint32_t tn = __shfl_up_sync(FULL, sn, o);
+      if (lane >= (uint32_t)o) {
+        sq += tq;
+        sn += tn;
+      }
+    }
+    qex[it] = wq + sq - qb;
+    nex[it] = wn + sn - (has[it] ? 1u : 0u);
+    wq += __shfl_sync(FULL, sq, 31);
+    wn += __shfl_sync(FULL, sn, 31);
+  }
+  if (lane == 0) {
+    s_wq[warp] = wq;
+    s_wn[warp] = wn;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long rq = 0ull;
+    uint32_t rn = 0u;
+    for (int w = 0; w < CELL_BLOCK / 32; ++w) {
+      const unsigned long long tq = s_wq[w];
+      const uint32_t tn = s_wn[w];
+      s_wq[w] = rq;
+      s_wn[w] = rn;
+      rq += tq;
+      rn += tn;
+    }
+    s_wq[CELL_BLOCK / 32] = rq;
+    s_wn[CELL_BLOCK / 32] = rn;
+    const unsigned long long agg[2] = {rq, (unsigned long long)rn};
+    lb_publish<2>(B.cell_st, B.cell_v, tile, epoch, tile == 0 ? ST_INCL : ST_AGG, agg);
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    unsigned long long acc[2] = {0ull, 0ull};
+    if (tile > 0) lb_lookback<2>(B.cell_st, B.cell_v, tile, epoch, acc, &B.ctl->err, ERR_TIMEOUT_CELL);
+    if (threadIdx.x == 0) {
+      s_cin[0] = acc[0];
+      s_cin[1] = acc[1];
+      const unsigned long long inc[2] = {acc[0] + s_wq[CELL_BLOCK / 32],
+                                         acc[1] + (unsigned long long)s_wn[CELL_BLOCK / 32]};
+      if (tile > 0) lb_publish<2>(B.cell_st, B.cell_v, tile, epoch, ST_INCL, inc);
+      if (tile == P.tiles_cell - 1) {
+        B.ctl->R_total = inc[0];
+        B.ctl->n_birth_cells = (uint32_t)inc[1];
+      }
+    }
+  }
+  __syncthreads();
+  const unsigned long long cq = s_cin[0] + s_wq[warp];
+  const uint32_t cn = (uint32_t)s_cin[1] + s_wn[warp];
+#pragma unroll
+  for (int it = 0; it < CELL_ITEMS; ++it) {
+    if (has[it]) {
+      const uint32_t c = tile * CELL_TILE + warp * (32 * CELL_ITEMS) + it * 32 + lane;
+      const uint32_t pos = cn + nex[it];
+      if (pos < P.C) {  // always true unless a look-back failure was latched
+        B.bl_cell[pos] = c;
+        B.bl_R[pos] = cq + qex[it];
+      }
+    }
+  }
+}
+
+// ====================================================================================
+// k_birth (Alg. 5): cell c owns the newborn slots [floor(nu_b R_{c-1}/R), floor(nu_b R_c/R))
+// of the fixed-point scan R of the newborn masses; nu_A = round(n p_A) of them form the
+// associated set (Eq. assoc_relation, assoc_sum), with weights Eq. weights_associated /
+// weights_unassociated.  A warp takes 32 consecutive birth cells and fills their slots,
+// which are contiguous, 32 at a time.
+// ====================================================================================
+constexpr int BIRTH_BLOCK = 256;
+
+__device__ __forceinline__ void birth_init(const KParams &P, const DevBufs &B, uint32_t slot,
+                                           uint32_t c, bool assoc, float w, float zv, float sg,
+                                           uint32_t frame, bool record) {
+  const U4 r = philox(slot, frame, TAG_BIRTH, P.seed_lo, P.seed_hi);
+  const float col = (float)(c % (uint32_t)P.W), row = (float)(c / (uint32_t)P.W);
+  const float x = __fmul_rn(__fadd_rn(col, u01_co(r.a)), P.s);
+  const float y = __fmul_rn(__fadd_rn(row, u01_co(r.b)), P.s);
+  float n0, n1;
+  gauss2(r.c, r.d, n0, n1);
+  float vx, vy;
+  if (assoc) {
+    const float dx = __fsub_rn(x, P.sensor_x), dy = __fsub_rn(y, P.sensor_y);
+    const float rr = __fsqrt_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)));
+    float ex = 1.0f, ey = 0.0f;
+    if (rr > 0.0f) {
+      ex = __fdiv_rn(dx, rr);
+      ey = __fdiv_rn(dy, rr);
+    }
+    const float vr = __fadd_rn(zv, __fmul_rn(sg, n0));
+    const float vt = __fmul_rn(P.sigma_B, n1);
+    vx = __fsub_rn(__fmul_rn(vr, ex), __fmul_rn(vt, ey));
+    vy = __fadd_rn(__fmul_rn(vr, ey), __fmul_rn(vt, ex));
+  } else {
+    vx = __fmul_rn(P.sigma_B, n0);
+    vy = __fmul_rn(P.sigma_B, n1);
+  }
+  B.bx[slot] = x;
+  B.by[slot] = y;
+  B.bvx[slot] = vx;
+  B.bvy[slot] = vy;
+  B.bw[slot] = w;
+  if (record) {
+    B.bcell[slot] = c;
+    B.bassoc[slot] = assoc ? 1u : 0u;
+  }
+}
+
+template <bool RADAR>
+__global__ void __launch_bounds__(BIRTH_BLOCK) k_birth(KParams P, DevBufs B) {
+  const uint32_t frame = B.ctl->frame;
+  const unsigned long long R = B.ctl->R_total;
+  const uint32_t nbc = min(B.ctl->n_birth_cells, P.C);
+  const bool record = (P.flags & 0x4u) != 0u;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t gwarp = (blockIdx.x * BIRTH_BLOCK + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * BIRTH_BLOCK) >> 5;
+  if (R == 0ull) {
+    // no newborn mass anywhere: weight 0, cell = slot mod C
+    for (uint32_t s = blockIdx.x * BIRTH_BLOCK + threadIdx.x; s < P.nu_b; s += gridDim.x * BIRTH_BLOCK)
+      birth_init(P, B, s, s % P.C, false, 0.0f, 0.0f, 1.0f, frame, record);
+    return;
+  }
+  for (uint32_t e0 = gwarp * 32u; e0 < nbc; e0 += nwarps * 32u) {
+    const uint32_t e = e0 + lane;
+    const bool ok = e < nbc;
+    uint32_t c = 0, lo = 0xffffffffu, n = 0, nA = 0;
+    float wA = 0.0f, wUA = 0.0f, zv = 0.0f, sg = 1.0f;
+    if (ok) {
+      c = B.bl_cell[e];
+      const unsigned long long Rex = B.bl_R[e];
+      const float rb = B.rho_b[c];
+      lo = floor_muldiv(P.nu_b, Rex, R);
+      const uint32_t hi = floor_muldiv(P.nu_b, Rex + q40(rb), R);
+      n = hi > lo ? hi - lo : 0u;  // hi < lo only after a latched look-back failure
+      float pA = 0.0f;
+      if constexpr (RADAR) {
+        pA = B.pA[c];
+        zv = B.zv[c];
+        sg = B.sgv[c];
+      }
+      nA = (uint32_t)__fadd_rn(__fmul_rn((float)n, pA), 0.5f);
+      if (nA > n) nA = n;
+      const uint32_t nUA = n - nA;
+      if (nA > 0u && nUA > 0u) {
+        wA = __fdiv_rn(__fmul_rn(pA, rb), (float)nA);
+        wUA = __fdiv_rn(__fmul_rn(__fsub_rn(1.0f, pA), rb), (float)nUA);
+      } else if (nA > 0u) {
+        wA = __fdiv_rn(rb, (float)nA);
+      } else if (n > 0u) {
+        wUA = __fdiv_rn(rb, (float)nUA);
+      }
+    }
+    const uint32_t last = min(31u, nbc - 1u - e0);
+    const uint32_t s_begin = __shfl_sync(FULL, lo, 0);
+    const uint32_t s_end = __shfl_sync(FULL, lo, last) + __shfl_sync(FULL, n, last);
+    for (uint32_t sb = s_begin; sb < s_end; sb += 32u) {
+      const uint32_t s = sb + lane;
+      // owner entry: the last lane L <= last with lo_L <= s
+      uint32_t L = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t cand = L + step;
+        const uint32_t lo_c = __shfl_sync(FULL, lo, cand & 31u);
+        if (cand <= last && lo_c <= s) L = cand;
+      }
+      const uint32_t lo_L = __shfl_sync(FULL, lo, L);
+      const uint32_t c_L = __shfl_sync(FULL, c, L);
+      const uint32_t nA_L = __shfl_sync(FULL, nA, L);
+      const float wA_L = __shfl_sync(FULL, wA, L), wUA_L = __shfl_sync(FULL, wUA, L);
+      const float zv_L = __shfl_sync(FULL, zv, L), sg_L = __shfl_sync(FULL, sg, L);
+      if (s < s_end && s < P.nu_b) {
+        const bool assoc = (s - lo_L) < nA_L;
+        birth_init(P, B, s, c_L, assoc, assoc ? wA_L : wUA_L, zv_L, sg_L, frame, record);
+      }
+    }
+  }
+}
+
+// ====================================================================================
+// k_normalise (Alg. 4 / Alg. 6): over the joint source index space (persistent particles
+// in sorted order, then newborn slots):
+//   w' = p_A mu_A g w + (1 - p_A) mu_UA w   (Eq. DSnormalization; lidar cells: mu_UA w),
+//   velocity moments of the persistent particles per cell (Eq. mean_x, var_x, covar_xy):
+//   the terms u v, u v^2, u vx vy of the cell-normalised weight u = w'/rho_p are summed in
+//   exact fixed point by a segmented scan and finalised by the thread holding the cell's
+//   last particle; and the tile sums of q40 of the joint weights with a decoupled look-back
+//   that leaves each tile's inclusive prefix for k_resample.
+// ====================================================================================
+constexpr int NORM_BLOCK = 256, NORM_ITEMS = 8, NORM_TILE = NORM_BLOCK * NORM_ITEMS;
+
+template <bool RADAR>
+__global__ void __launch_bounds__(NORM_BLOCK) k_normalise(KParams P, DevBufs B) {
+  __shared__ Seg<5> s_w[NORM_BLOCK / 32 + 1];
+  __shared__ unsigned long long s_cin[5];
+  __shared__ unsigned long long s_red[NORM_BLOCK / 32];
+  __shared__ uint32_t s_tile;
+  if (threadIdx.x == 0) s_tile = (uint32_t)atomicAdd(&B.ctl->ctr[CTR_NORM], 1ull);
+  __syncthreads();
+  const uint32_t tile = s_tile, frame = B.ctl->frame, epoch = frame & 0x3fffffffu;
+  const uint32_t ntot = P.nu + P.nu_b;
+  const uint32_t j0 = tile * NORM_TILE + threadIdx.x * NORM_ITEMS;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long qsum = 0ull;
+  const bool has_pers = tile * NORM_TILE < P.nu;  // block-uniform
+  uint32_t key[NORM_ITEMS];
+  unsigned long long mv[NORM_ITEMS][5];
+  uint32_t head = 0, tail = 0;
+  Seg<5> agg;
+  agg.f = 0;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) agg.v[k] = 0ull;
+  if (has_pers) {
+    uint32_t idx[NORM_ITEMS];
+    load_run<NORM_ITEMS>(B.key_sorted, j0, P.nu, key, 0xffffffffu);
+    load_run<NORM_ITEMS>(B.perm, j0, P.nu, idx, 0u);
+    const uint32_t kprev = (j0 > 0 && j0 <= P.nu) ? __ldg(B.key_sorted + j0 - 1) : 0xfffffffeu;
+    const uint32_t knext = (j0 + NORM_ITEMS < P.nu) ? __ldg(B.key_sorted + j0 + NORM_ITEMS) : 0xfffffffeu;
+    float wn_out[NORM_ITEMS];
+#pragma unroll
+    for (int it = 0; it < NORM_ITEMS; ++it) {
+      const uint32_t j = j0 + it;
+      const bool ok = j < P.nu;
+      const uint32_t kp = it == 0 ? kprev : key[it - 1];
+      const uint32_t kn = it == NORM_ITEMS - 1 ? knext : key[it + 1];
+      const bool h = ok && (j == 0 || key[it] != kp);
+      const bool t = ok && (j == P.nu - 1 || key[it] != kn);
+      head |= (uint32_t)h << it;
+      tail |= (uint32_t)t << it;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) mv[it][k] = 0ull;
+      wn_out[it] = 0.0f;
+      if (ok) {
+        const uint32_t i = idx[it], c = key[it];
+        const float w = __ldg(B.Aw + i);
+        const float vx = __ldg(B.Avx + i), vy = __ldg(B.Avy + i);
+        const float muU = __ldg(B.muU + c);
+        float wn;
+        const float pa = RADAR ? __ldg(B.paeff + c) : 0.0f;
+        if (RADAR && pa > 0.0f) {
+          const float g = radar_lik(P, __ldg(B.Ax + i), __ldg(B.Ay + i), vx, vy, __ldg(B.zv + c),
+                                    __ldg(B.sgv + c));
+          const float a = __fmul_rn(__fmul_rn(__fmul_rn(pa, __ldg(B.muA + c)), g), w);
+          const float b = __fmul_rn(__fmul_rn(__fsub_rn(1.0f, pa), muU), w);
+          wn = __fadd_rn(a, b);
+        } else {
+          wn = __fmul_rn(muU, w);
+        }
+        wn_out[it] = wn;
+        qsum += q40(wn);
+        const float rp = __ldg(B.rho_p + c);
+        const float u = rp > 0.0f ? __fdiv_rn(wn, rp) : 0.0f;
+        const float mx = __fmul_rn(u, vx), my = __fmul_rn(u, vy);
+        mv[it][0] = q40s(mx);
+        mv[it][1] = q40s(my);
+        mv[it][2] = q40s(__fmul_rn(mx, vx));
+        mv[it][3] = q40s(__fmul_rn(my, vy));
+        mv[it][4] = q40s(__fmul_rn(mx, vy));
+      }
+      Seg<5> e;
+      e.f = h;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) e.v[k] = mv[it][k];
+      agg = seg_combine(agg, e);
+    }
+    if (j0 + NORM_ITEMS <= P.nu) {
+#pragma unroll
+      for (int k = 0; k < NORM_ITEMS; k += 4)
+        *reinterpret_cast<float4 *>(B.wn + j0 + k) = make_float4(wn_out[k], wn_out[k + 1], wn_out[k + 2], wn_out[k + 3]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < NORM_ITEMS; ++k)
+        if (j0 + k < P.nu) B.wn[j0 + k] = wn_out[k];
+    }
+  }
+  // newborn sources of this tile
+#pragma unroll
+  for (int it = 0; it < NORM_ITEMS; ++it) {
+    const uint32_t j = j0 + it;
+    if (j >= P.nu && j < ntot) qsum += q40(__ldg(B.bw + (j - P.nu)));
+  }
+  // tile sum of the joint quantised weights -> look-back -> inclusive prefix
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) qsum += __shfl_xor_sync(FULL, qsum, o);
+  if (lane == 0) s_red[warp] = qsum;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    unsigned long long tsum = threadIdx.x < NORM_BLOCK / 32 ? s_red[threadIdx.x] : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(FULL, tsum, o);
+    const unsigned long long a1[1] = {tsum};
+    if (threadIdx.x == 0) lb_publish<1>(B.cdf_st, B.cdf_v, tile, epoch, tile == 0 ? ST_INCL : ST_AGG, a1);
+    if (tile > 0) {
+      unsigned long long acc[1];
+      lb_lookback<1>(B.cdf_st, B.cdf_v, tile, epoch, acc, &B.ctl->err, ERR_TIMEOUT_NORM);
+      const unsigned long long inc[1] = {acc[0] + tsum};
+      if (threadIdx.x == 0) lb_publish<1>(B.cdf_st, B.cdf_v, tile, epoch, ST_INCL, inc);
+    }
+  }
+  if (!has_pers) return;  // block-uniform
+  // segmented moment sums
+  Seg<5> tot;
+  const Seg<5> ex = block_seg_excl<5>(agg, s_w, tot);
+  unsigned long long cin[5];
+  seg_tile_carry<5>(B.mom_st, B.mom_v, tile, epoch, tot, cin, &B.ctl->err, ERR_TIMEOUT_NORM, s_cin);
+  unsigned long long run[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) run[k] = ex.f ? ex.v[k] : ex.v[k] + cin[k];
+#pragma unroll
+  for (int it = 0; it < NORM_ITEMS; ++it) {
+    const bool h = (head >> it) & 1u, t = (tail >> it) & 1u;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) run[k] = h ? mv[it][k] : run[k] + mv[it][k];
+    if (t) {
+      const uint32_t c = key[it];
+      const float rp = __ldg(B.rho_p + c);
+      float mx = 0.0f, my = 0.0f, vxx = 0.0f, vyy = 0.0f, cxy = 0.0f;
+      if (rp > 0.0f) {
+        const double ax = fx40s_to_d(run[0]), ay = fx40s_to_d(run[1]);
+        const double sxx = fx40s_to_d(run[2]) - ax * ax;
+        const double syy = fx40s_to_d(run[3]) - ay * ay;
+        const double sxy = fx40s_to_d(run[4]) - ax * ay;
+        mx = (float)ax;
+        my = (float)ay;
+        vxx = (float)(sxx > 0.0 ? sxx : 0.0);
+        vyy = (float)(syy > 0.0 ? syy : 0.0);
+        cxy = (float)sxy;
+      }
+      B.mean_x[c] = mx;
+      B.mean_y[c] = my;
+      B.var_x[c] = vxx;
+      B.var_y[c] = vyy;
+      B.cov[c] = cxy;
+    }
+  }
+}
+
+// ====================================================================================
+// k_resample (Alg. 7, systematic): with joint inclusive fixed-point CDF Q, total W and one
+// uniform offset u in [0, W), output i takes the first source j with Q_j * nu > i W + u
+// (i.e. Q_j > floor((i W + u) / nu)).  A block takes the outputs that fall in its tile of
+// sources, finds each output's source by bisection in the tile's CDF (shared memory) and
+// copies the source's state with the equal weight W / nu (Eq. resampledParticleWeights).
+// ====================================================================================
+constexpr int RES_BLOCK = 256;
+
+// number of outputs i in [0, nu) with i W + u < X nu
+__device__ __forceinline__ uint32_t outputs_below(unsigned long long X, unsigned long long Wt,
+                                                  unsigned long long u, uint32_t nu) {
+  const U128 lim = mul_64x64(X, nu);
+  uint32_t lo = 0, hi = nu;  // smallest i in [0, nu] with i W + u >= X nu
+  while (lo < hi) {
+    const uint32_t mid = lo + (hi - lo) / 2;
+    if (lt_128(add_128_64(mul_64x64(mid, Wt), u), lim)) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(RES_BLOCK) k_resample(KParams P, DevBufs B) {
+  __shared__ unsigned long long s_Q[NORM_TILE];
+  __shared__ uint32_t s_perm[NORM_TILE];
+  __shared__ unsigned long long s_wsum[RES_BLOCK / 32];
+  __shared__ uint32_t s_range[2];
+  const uint32_t tile = blockIdx.x, frame = B.ctl->frame;
+  const uint32_t base = tile * NORM_TILE, ntot = P.nu + P.nu_b;
+  const bool record = (P.flags & 0x4u) != 0u;
+  const unsigned long long Wt = __ldcg(B.cdf_v + (size_t)(P.tiles_norm - 1) * 2 + 1);
+  const unsigned long long E = tile > 0 ? __ldcg(B.cdf_v + (size_t)(tile - 1) * 2 + 1) : 0ull;
+  if ((P.flags & 0x2u) != 0u || Wt == 0ull) {
+    // no resampling: the persistent particles carry over in sorted order
+    for (uint32_t i = base + threadIdx.x; i < min(base + NORM_TILE, P.nu); i += RES_BLOCK) {
+      const uint32_t s = B.perm[i];
+      B.Bx[i] = B.Ax[s]; B.By[i] = B.Ay[s]; B.Bvx[i] = B.Avx[s]; B.Bvy[i] = B.Avy[s];
+      B.Bw[i] = B.wn[i];
+      if (record) B.rsrc[i] = i;
+    }
+    if (tile == 0 && threadIdx.x == 0) {
+      B.ctl->W_total = Wt;
+      B.ctl->u_offset = 0ull;
+    }
+    return;
+  }
+  const U4 r = philox(0u, frame, TAG_RESAMPLE, P.seed_lo, P.seed_hi);
+  const unsigned long long r64 = ((unsigned long long)r.a << 32) | r.b;
+  const unsigned long long u = __umul64hi(r64, Wt);
+  const float wnew = (float)((__ull2double_rn(Wt) * 0x1p-40) / (double)P.nu);
+  if (tile == 0 && threadIdx.x == 0) {
+    B.ctl->W_total = Wt;
+    B.ctl->u_offset = u;
+  }
+  // the tile's quantised weights -> inclusive CDF in shared memory
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t j0 = base + threadIdx.x * NORM_ITEMS;
+  unsigned long long q[NORM_ITEMS];
+  unsigned long long loc = 0ull;
+#pragma unroll
+  for (int it = 0; it < NORM_ITEMS; ++it) {
+    const uint32_t j = j0 + it;
+    float w = 0.0f;
+    uint32_t pm = 0xffffffffu;
+    if (j < P.nu) {
+      w = __ldg(B.wn + j);
+      pm = __ldg(B.perm + j);
+    } else if (j < ntot) {
+      w = __ldg(B.bw + (j - P.nu));
+    }
+    q[it] = q40(w);
+    loc += q[it];
+    s_perm[threadIdx.x * NORM_ITEMS + it] = pm;
+  }
+  unsigned long long inc = loc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long t = __shfl_up_sync(FULL, inc, o);
+    if (lane >= (uint32_t)o) inc += t;
+  }
+  if (lane == 31) s_wsum[warp] = inc;
+  __syncthreads();
+  unsigned long long wbase = 0ull;
+  for (uint32_t w = 0; w < warp; ++w) wbase += s_wsum[w];
+  unsigned long long run = E + wbase + inc - loc;
+#pragma unroll
+  for (int it = 0; it < NORM_ITEMS; ++it) {
+    run += q[it];
+    s_Q[threadIdx.x * NORM_ITEMS + it] = run;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_range[0] = outputs_below(E, Wt, u, P.nu);
+    s_range[1] = outputs_below(s_Q[NORM_TILE - 1], Wt, u, P.nu);
+  }
+  __syncthreads();
+  const uint32_t o_lo = s_range[0], o_hi = s_range[1];
+  for (uint32_t i = o_lo + threadIdx.x; i < o_hi; i += RES_BLOCK) {
+    const U128 X = add_128_64(mul_64x64(i, Wt), u);
+    uint32_t lo = 0, hi = NORM_TILE - 1;  // smallest m with Q_m nu > X
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (lt_128(X, mul_64x64(s_Q[mid], P.nu))) hi = mid; else lo = mid + 1;
+    }
+    const uint32_t j = base + lo;
+    float x, y, vx, vy;
+    if (j < P.nu) {
+      const uint32_t s = s_perm[lo];
+      x = __ldg(B.Ax + s); y = __ldg(B.Ay + s); vx = __ldg(B.Avx + s); vy = __ldg(B.Avy + s);
+    } else {
+      const uint32_t b = P.nu_b ? min(j - P.nu, P.nu_b - 1u) : 0u;
+      x = __ldg(B.bx + b); y = __ldg(B.by + b); vx = __ldg(B.bvx + b); vy = __ldg(B.bvy + b);
+    }
+    B.Bx[i] = x; B.By[i] = y; B.Bvx[i] = vx; B.Bvy[i] = vy; B.Bw[i] = wnew;
+    if (record) B.rsrc[i] = j;
+  }
+}
+
+}  // namespace dog

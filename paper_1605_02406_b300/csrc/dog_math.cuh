@@ -1,0 +1,175 @@
+// dog_math.cuh -- device arithmetic shared by the filter kernels.
+//
+// Every floating-point operation on the filter's path is an explicit IEEE binary32
+// round-to-nearest intrinsic (__fadd_rn, __fmul_rn, ...), so no multiply-add is ever
+// contracted and the sequence of roundings is fixed.  The transcendentals the filter needs
+// (ln and sin/cos of 2 pi u for Box-Muller, exp for the radar likelihood) are this file's
+// own series evaluations, not CUDA's math library.
+#pragma once
+#include <cstdint>
+
+namespace dog {
+
+// ------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 multiplications with
+// the Weyl-sequence key schedule.  Counter = (element, frame, purpose tag, 0).
+// ------------------------------------------------------------------------------------
+struct U4 {
+  uint32_t a, b, c, d;
+};
+
+__device__ __forceinline__ U4 philox(uint32_t e, uint32_t frame, uint32_t tag, uint32_t k0,
+                                     uint32_t k1) {
+  uint32_t x0 = e, x1 = frame, x2 = tag, x3 = 0u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * x0, hi0 = __umulhi(0xD2511F53u, x0);
+    const uint32_t lo1 = 0xCD9E8D57u * x2, hi1 = __umulhi(0xCD9E8D57u, x2);
+    const uint32_t y0 = hi1 ^ x1 ^ k0, y2 = hi0 ^ x3 ^ k1;
+    x0 = y0; x1 = lo1; x2 = y2; x3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return U4{x0, x1, x2, x3};
+}
+
+enum : uint32_t { TAG_INIT = 0, TAG_PREDICT = 1, TAG_BIRTH = 2, TAG_RESAMPLE = 3 };
+
+// uniform draws from the top 24 bits: [0,1) and (0,1]
+__device__ __forceinline__ float u01_co(uint32_t r) { return __fmul_rn((float)(r >> 8), 0x1p-24f); }
+__device__ __forceinline__ float u01_oc(uint32_t r) { return __fmul_rn((float)((r >> 8) + 1u), 0x1p-24f); }
+
+// ln(u) for a positive normal u: fold the mantissa into [sqrt(1/2), sqrt(2)], then
+// ln m = 2 atanh((m-1)/(m+1)) by its odd series to the 11th power (Horner in s^2), and
+// add e*ln2 with ln2 split in a short high part (exact products) and a correction.
+__device__ __forceinline__ float ln_f(float u) {
+  const uint32_t bits = __float_as_uint(u);
+  int e = (int)((bits >> 23) & 0xffu) - 127;
+  float m = __uint_as_float((bits & 0x7fffffu) | 0x3f800000u);
+  if (m > 0x1.6a09e6p+0f) {
+    m = __fmul_rn(m, 0.5f);
+    e += 1;
+  }
+  const float f = __fsub_rn(m, 1.0f);
+  const float s = __fdiv_rn(f, __fadd_rn(2.0f, f));
+  const float z = __fmul_rn(s, s);
+  float p = 0x1.745d18p-4f;
+  p = __fadd_rn(__fmul_rn(p, z), 0x1.c71c72p-4f);
+  p = __fadd_rn(__fmul_rn(p, z), 0x1.24924ap-3f);
+  p = __fadd_rn(__fmul_rn(p, z), 0x1.99999ap-3f);
+  p = __fadd_rn(__fmul_rn(p, z), 0x1.555556p-2f);
+  p = __fadd_rn(__fmul_rn(p, z), 1.0f);
+  const float lnm = __fmul_rn(__fadd_rn(s, s), p);
+  const float ef = (float)e;
+  const float lo = __fadd_rn(lnm, __fmul_rn(ef, 0x1.7f7d1cp-20f));
+  return __fadd_rn(__fmul_rn(ef, 0x1.62e4p-1f), lo);
+}
+
+// sin and cos of 2*pi*u, u = k 2^-24 in [0,1): octant by the exact value 8u, reduced angle
+// in [0, pi/4] (odd octants mirrored to 1 - t), Taylor series of sin (to theta^9) and
+// cos (to theta^10), then the octant's symmetry.
+__device__ __forceinline__ void sincos2pi_f(float u, float &sn, float &cs) {
+  const float v = __fmul_rn(u, 8.0f);
+  const int k = (int)v;
+  const float t = __fsub_rn(v, (float)k);
+  const float tt = (k & 1) ? __fsub_rn(1.0f, t) : t;
+  const float th = __fmul_rn(tt, 0x1.921fb6p-1f);
+  const float z = __fmul_rn(th, th);
+  float ps = 0x1.71de3ap-19f;
+  ps = __fadd_rn(__fmul_rn(ps, z), -0x1.a01a02p-13f);
+  ps = __fadd_rn(__fmul_rn(ps, z), 0x1.111112p-7f);
+  ps = __fadd_rn(__fmul_rn(ps, z), -0x1.555556p-3f);
+  ps = __fadd_rn(__fmul_rn(ps, z), 1.0f);
+  const float S = __fmul_rn(th, ps);
+  float pc = -0x1.27e4fcp-22f;
+  pc = __fadd_rn(__fmul_rn(pc, z), 0x1.a01a02p-16f);
+  pc = __fadd_rn(__fmul_rn(pc, z), -0x1.6c16c2p-10f);
+  pc = __fadd_rn(__fmul_rn(pc, z), 0x1.555556p-5f);
+  pc = __fadd_rn(__fmul_rn(pc, z), -0.5f);
+  pc = __fadd_rn(__fmul_rn(pc, z), 1.0f);
+  const float Cc = pc;
+  // octant k: (sin, cos) = k0 (S, C)  k1 (C, S)  k2 (C,-S)  k3 (S,-C)
+  //                        k4 (-S,-C) k5 (-C,-S) k6 (-C, S) k7 (-S, C)
+  const bool swap = ((k + 1) & 2) != 0;  // k = 1, 2, 5, 6
+  const float a = swap ? Cc : S;
+  const float b = swap ? S : Cc;
+  sn = (k >= 4) ? -a : a;
+  cs = (k >= 2 && k <= 5) ? -b : b;
+}
+
+// e^x for x <= 0: x = k ln2 + r, k = floor(x/ln2 + 1/2), r by a two-part ln2, Taylor
+// series of e^r to r^7, scaled by 2^k through the exponent field; 0 below -87.
+__device__ __forceinline__ float exp_f(float x) {
+  if (!(x > -87.0f)) return 0.0f;
+  const float kf = floorf(__fadd_rn(__fmul_rn(x, 0x1.715476p+0f), 0.5f));
+  const int k = (int)kf;
+  const float r = __fsub_rn(__fsub_rn(x, __fmul_rn(kf, 0x1.62e4p-1f)), __fmul_rn(kf, 0x1.7f7d1cp-20f));
+  float p = 0x1.a01a02p-13f;
+  p = __fadd_rn(__fmul_rn(p, r), 0x1.6c16c2p-10f);
+  p = __fadd_rn(__fmul_rn(p, r), 0x1.111112p-7f);
+  p = __fadd_rn(__fmul_rn(p, r), 0x1.555556p-5f);
+  p = __fadd_rn(__fmul_rn(p, r), 0x1.555556p-3f);
+  p = __fadd_rn(__fmul_rn(p, r), 0.5f);
+  p = __fadd_rn(__fmul_rn(p, r), 1.0f);
+  p = __fadd_rn(__fmul_rn(p, r), 1.0f);
+  return __fmul_rn(p, __uint_as_float((uint32_t)(k + 127) << 23));
+}
+
+// Box-Muller pair from two 32-bit draws
+__device__ __forceinline__ void gauss2(uint32_t ra, uint32_t rb, float &n0, float &n1) {
+  const float rad = __fsqrt_rn(__fmul_rn(-2.0f, ln_f(u01_oc(ra))));
+  float sn, cs;
+  sincos2pi_f(u01_co(rb), sn, cs);
+  n0 = __fmul_rn(rad, cs);
+  n1 = __fmul_rn(rad, sn);
+}
+
+// ------------------------------------------------------------------------------------
+// Fixed point.  Weights: unsigned 64-bit, scale 2^40, truncation; back to float by
+// round-to-nearest.  Moment terms (products of a cell-normalised weight with velocities):
+// two's-complement 64-bit, scale 2^40, truncation toward 0, saturated at +-2^62.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long q40(float w) {
+  return (w > 0.0f) ? __float2ull_rz(__fmul_rn(w, 0x1p40f)) : 0ull;
+}
+__device__ __forceinline__ float fx40_to_f(unsigned long long s) {
+  return __fmul_rn(__ull2float_rn(s), 0x1p-40f);
+}
+__device__ __forceinline__ unsigned long long q40s(float t) {
+  float v = __fmul_rn(t, 0x1p40f);
+  v = fminf(fmaxf(v, -0x1p62f), 0x1p62f);
+  return (unsigned long long)__float2ll_rz(v);
+}
+__device__ __forceinline__ double fx40s_to_d(unsigned long long s) {
+  return __ll2double_rn((long long)s) * 0x1p-40;
+}
+
+// ------------------------------------------------------------------------------------
+// 128-bit helpers for the exact integer allocation rules
+// ------------------------------------------------------------------------------------
+struct U128 {
+  unsigned long long hi, lo;
+};
+__device__ __forceinline__ U128 mul_64x64(unsigned long long a, unsigned long long b) {
+  return U128{__umul64hi(a, b), a * b};
+}
+__device__ __forceinline__ U128 add_128_64(U128 a, unsigned long long b) {
+  const unsigned long long lo = a.lo + b;
+  return U128{a.hi + (lo < b ? 1ull : 0ull), lo};
+}
+__device__ __forceinline__ bool lt_128(U128 a, U128 b) {
+  return (a.hi < b.hi) || (a.hi == b.hi && a.lo < b.lo);
+}
+// floor(a * b / d) for b <= d (so the result lies in [0, a]): bisection on the quotient
+// with exact 128-bit comparisons
+__device__ __forceinline__ uint32_t floor_muldiv(uint32_t a, unsigned long long b, unsigned long long d) {
+  const U128 ab = mul_64x64(a, b);
+  uint32_t lo = 0, hi = a;
+  while (lo < hi) {
+    const uint32_t mid = lo + (hi - lo + 1) / 2;
+    if (lt_128(ab, mul_64x64(mid, d))) hi = mid - 1; else lo = mid;
+  }
+  return lo;
+}
+
+}  // namespace dog
