@@ -1,0 +1,333 @@
+"""Benchmark of the DS-PHD/MIB filter hot path on B300.
+
+Workload: the automotive-size filter -- 1024x1024 grid at 0.1 m, 4,194,304 persistent +
+1,048,576 newborn particles per frame, seeded synthetic lidar scene (30 moving rectangles,
+200 static boxes, 2,160 beams), dt = 0.1 s.  A step is one full recursion (Alg. 1-7) on one
+frame's measurement grid: dog_set_measurement_grid + dog_step.
+
+Prints one JSON line.  `value` is particle-updates/s (persistent particles x steps / time)
+over K timed steps with the grids already resident in HBM (particle state 168 MB > L2, so
+no L2 flush is needed); `e2e` is the same metric through the C ABI with host buffers (the
+grid copied from pinned host memory and the occupancy and velocity grids read back every
+step); `roofline` reports the dominant kernel's achieved bandwidth from per-kernel CUDA
+events (a second timed region with DOG_PROFILE); `cpu_baseline` times the CPU oracle on a
+bounded sample.  With --impl reference the CPU oracle itself is timed as the reference arm.
+Under torchrun each rank runs an independent replica (the filter does not shard).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1605_02406_b300 import scene  # noqa: E402
+
+METRIC = "particle-updates/s at 1024² grid, 4M particles; p50/p99 latency batched vs plain"
+CFG_ID = 2
+
+# algorithmic bytes per launch of each kernel: (bytes per persistent particle, per newborn
+# slot, per cell); the derivation is in the design doc
+ALG_BYTES = {
+    "k_predict": (44, 0, 0),
+    "k_sort_pass0": (12, 0, 0),
+    "k_sort_pass1": (16, 0, 0),
+    "k_sort_pass2": (16, 0, 0),
+    "k_segsum": (12, 0, 0),
+    "k_cell": (0, 0, 68),
+    "k_birth": (0, 20, 0),
+    "k_normalise": (24, 4, 0),
+    "k_resample": (44, 4, 0),
+    "k_tick": (0, 0, 0),
+}
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_1605_02406_b300", "csrc")
+    for n in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, n), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def peaks() -> tuple:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.f = tempfile.NamedTemporaryFile("w+", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(dev), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for k, n in enumerate(names):
+                if len(r) > 3 + k and r[3 + k].strip() == "Active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(params: dict, grids: list, budget_s: float = 12.0) -> dict:
+    """The oracle (FP32 mirror) on frames of the same workload until about budget_s."""
+    from oracle import OracleFilter
+    o = OracleFilter(params, "f32")
+    n, t0 = 0, time.perf_counter()
+    while True:
+        g = grids[n % len(grids)]
+        o.set_measurement_grid(g["m_occ"], g["m_free"])
+        o.step(0.1)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or n >= len(grids):
+            break
+    return {"value": params["nu"] * n / el, "unit": "particle-updates/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{n} consecutive frames of the full 1024x1024 / 4,194,304 + 1,048,576 "
+                      f"particle workload from the initial state, single thread"}
+
+
+def run_reference(args) -> None:
+    """Reference arm: the CPU oracle, one full frame of the workload per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import OracleFilter
+    cfg = scene.CONFIGS[CFG_ID]
+    params = scene.filter_params(cfg)
+    grids = scene.frame_sequence(cfg, min(args.steps + args.warmup, 16), 1002)
+    o = OracleFilter(params, "f32")
+    for k in range(args.warmup):
+        g = grids[k % len(grids)]
+        o.set_measurement_grid(g["m_occ"], g["m_free"])
+        o.step(0.1)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        g = grids[(args.warmup + k) % len(grids)]
+        o.set_measurement_grid(g["m_occ"], g["m_free"])
+        o.step(0.1)
+    el = time.perf_counter() - t0
+    v = params["nu"] * args.steps / el
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "particle-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": cfg["name"], "grid": "1024x1024", "cell_size_m": 0.1,
+                   "num_particles": params["nu"], "num_birth": params["nu_b"]},
+        "cpu_baseline": {"value": v, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full frames after {args.warmup} warm-up frames"},
+        "e2e": {"value": v, "unit": "particle-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1605_02406_b300 import native as N
+    from paper_1605_02406_b300.filter import DogFilter
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    cfg = scene.CONFIGS[CFG_ID]
+    params = scene.filter_params(cfg, seed=42 + rank)
+    n_grids = min(args.steps + args.warmup, 24)
+    grids = scene.frame_sequence(cfg, n_grids, 1002)
+    dev_grids = [{k: torch.tensor(v, device="cuda") for k, v in g.items()} for g in grids]
+
+    # ---------------------------------------------------------------- device-resident run
+    f = DogFilter(params)
+    st = f.stream
+    for k in range(args.warmup):
+        f.set_measurement_grid(**dev_grids[k % n_grids])
+        f.step(cfg["dt"])
+    f.sync()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    clk = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    ev[0].record(st)
+    for k in range(args.steps):
+        f.set_measurement_grid(**dev_grids[(args.warmup + k) % n_grids])
+        f.step(cfg["dt"])
+        ev[k + 1].record(st)
+    f.sync()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    per_step = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    ms_total = ev[0].elapsed_time(ev[-1])
+    t = torch.tensor([ms_total], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * params["nu"] * args.steps / (ms_max * 1e-3)
+    launches = args.steps * (f.kernels_per_step() + 1)  # + the grid validation kernel
+    cells_check = f.cells(["m_occ"])["m_occ"]
+    assert np.isfinite(cells_check).all()
+    f.close()
+
+    # ------------------------------------------------------------- end-to-end, host buffers
+    fe = DogFilter(params)
+    C = params["width"] * params["height"]
+    pin = [{k: torch.from_numpy(v).pin_memory() for k, v in g.items()} for g in grids]
+    out = {k: torch.empty(C, dtype=torch.float32).pin_memory() for k in ("p_occ", "mean_vx", "mean_vy")}
+
+    def e2e_step(k):
+        g = pin[k % n_grids]
+        N.dog_set_measurement_grid(fe.h, {kk: v.data_ptr() for kk, v in g.items()}, N.DOG_HOST)
+        N.dog_step(fe.h, cfg["dt"])
+        N.dog_get_cells(fe.h, {kk: v.data_ptr() for kk, v in out.items()}, N.DOG_HOST)
+
+    for k in range(args.warmup):
+        e2e_step(k)
+    barrier()
+    ee = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    t0 = time.perf_counter()
+    ee[0].record(fe.stream)
+    for k in range(args.steps):
+        e2e_step(args.warmup + k)
+    ee[1].record(fe.stream)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * params["nu"] * args.steps / float(te.item())
+    fe.close()
+
+    # ------------------------------------------------------ per-kernel events (roofline)
+    fp = DogFilter(dict(params, flags=N.DOG_PROFILE))
+    for k in range(args.warmup):
+        fp.set_measurement_grid(**dev_grids[k % n_grids])
+        fp.step(cfg["dt"])
+    fp.sync()
+    fp.profile()
+    kp = min(args.steps, 30)
+    for k in range(kp):
+        fp.set_measurement_grid(**dev_grids[(args.warmup + k) % n_grids])
+        fp.step(cfg["dt"])
+    prof, nsteps = fp.profile()
+    fp.close()
+    per_kernel_us = {k: v / max(nsteps, 1) * 1e3 for k, v in prof.items()}
+    nu, nb = params["nu"], params["nu_b"]
+    kern_gbs = {}
+    for k, us in per_kernel_us.items():
+        a, b, c = ALG_BYTES.get(k, (0, 0, 0))
+        byts = a * nu + b * nb + c * C
+        kern_gbs[k] = byts / (us * 1e-6) / 1e9 if us > 0 and byts else None
+    dom = max(per_kernel_us, key=lambda k: per_kernel_us[k])
+    peak, peak_kind = peaks()
+    a, b, c = ALG_BYTES[dom]
+    alg = a * nu + b * nb + c * C
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if os.path.exists(tf):
+        tj = json.load(open(tf))
+        if tj.get("csrc_hash") == csrc_hash() and dom in tj.get("kernels", {}):
+            traffic = tj["kernels"][dom]
+    achieved = kern_gbs[dom]
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(scene.filter_params(cfg), grids[:8])
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": cfg["name"], "grid": "1024x1024", "cell_size_m": 0.1,
+                   "num_particles": nu, "num_birth": nb, "scene": "30 moving rectangles, 200 static boxes, 2160 beams",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (particle state 168 MB); no flush",
+                   "launch": "CUDA graph per step"},
+        "latency_ms": {"plain_p50": float(np.percentile(per_step, 50)),
+                       "plain_p99": float(np.percentile(per_step, 99)),
+                       "batched_p50": None, "batched_p99": None},
+        "e2e": {"value": e2e_value, "unit": "particle-updates/s",
+                "h2d_bytes_per_step": 2 * 4 * C, "d2h_bytes_per_step": 3 * 4 * C},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "peak_source": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None,
+                     "traffic": traffic, "algorithmic_bytes": alg,
+                     "timing": "per-kernel CUDA events, DOG_PROFILE region of "
+                               f"{nsteps} steps (kernels launched one by one)"},
+        "kernels_us": {k: round(v, 2) for k, v in per_kernel_us.items()},
+        "kernels_gbs": {k: (round(v, 1) if v else None) for k, v in kern_gbs.items()},
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
 // min(S, 1), the free-mass prediction, Dempster's rule with the measurement BBA, the
 // newborn / persistent split and the normalisers mu_A, mu_UA.  The newborn masses are
 // scanned in cell order (single pass, decoupled look-back) and the cells with newborn
-// mass are listed in order with their exclusive prefix for k_birth.
+// mass are listed in order with their inclusive prefix for k_birth.
 // ====================================================================================
 constexpr int CELL_BLOCK = 256, CELL_ITEMS = 4, CELL_TILE = CELL_BLOCK * CELL_ITEMS;
 
@@ -582,7 +582,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
   __syncthreads();
   const uint32_t tile = s_tile, frame = B.ctl->frame, epoch = frame & 0x3fffffffu;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned long long qex[CELL_ITEMS];
+  unsigned long long qex[CELL_ITEMS], qin[CELL_ITEMS];
   uint32_t nex[CELL_ITEMS];
   bool has[CELL_ITEMS];
   unsigned long long wq = 0ull;  // running sums of this warp, in cell order
@@ -635,6 +635,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
       }
     }
     qex[it] = wq + sq - qb;
+    qin[it] = wq + sq;
     nex[it] = wn + sn - (has[it] ? 1u : 0u);
     wq += __shfl_sync(FULL, sq, 31);
     wn += __shfl_sync(FULL, sn, 31);
@@ -686,7 +687,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
       const uint32_t pos = cn + nex[it];
       if (pos < P.C) {  // always true unless a look-back failure was latched
         B.bl_cell[pos] = c;
-        B.bl_R[pos] = cq + qex[it];
+        B.bl_R[pos] = cq + qin[it];
       }
     }
   }
@@ -696,8 +697,8 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
 // k_birth (Alg. 5): cell c owns the newborn slots [floor(nu_b R_{c-1}/R), floor(nu_b R_c/R))
 // of the fixed-point scan R of the newborn masses; nu_A = round(n p_A) of them form the
 // associated set (Eq. assoc_relation, assoc_sum), with weights Eq. weights_associated /
-// weights_unassociated.  A warp takes 32 consecutive birth cells and fills their slots,
-// which are contiguous, 32 at a time.
+// weights_unassociated.  One thread per slot finds its cell by bisection in the list of
+// birth cells (exact 128-bit comparisons of nu_b R_incl against (slot + 1) R).
 // ====================================================================================
 constexpr int BIRTH_BLOCK = 256;
 
@@ -744,68 +745,46 @@ __global__ void __launch_bounds__(BIRTH_BLOCK) k_birth(KParams P, DevBufs B) {
   const unsigned long long R = B.ctl->R_total;
   const uint32_t nbc = min(B.ctl->n_birth_cells, P.C);
   const bool record = (P.flags & 0x4u) != 0u;
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t gwarp = (blockIdx.x * BIRTH_BLOCK + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * BIRTH_BLOCK) >> 5;
-  if (R == 0ull) {
+  const uint32_t stride = gridDim.x * BIRTH_BLOCK;
+  if (R == 0ull || nbc == 0u) {
     // no newborn mass anywhere: weight 0, cell = slot mod C
-    for (uint32_t s = blockIdx.x * BIRTH_BLOCK + threadIdx.x; s < P.nu_b; s += gridDim.x * BIRTH_BLOCK)
+    for (uint32_t s = blockIdx.x * BIRTH_BLOCK + threadIdx.x; s < P.nu_b; s += stride)
       birth_init(P, B, s, s % P.C, false, 0.0f, 0.0f, 1.0f, frame, record);
     return;
   }
-  for (uint32_t e0 = gwarp * 32u; e0 < nbc; e0 += nwarps * 32u) {
-    const uint32_t e = e0 + lane;
-    const bool ok = e < nbc;
-    uint32_t c = 0, lo = 0xffffffffu, n = 0, nA = 0;
-    float wA = 0.0f, wUA = 0.0f, zv = 0.0f, sg = 1.0f;
-    if (ok) {
-      c = B.bl_cell[e];
-      const unsigned long long Rex = B.bl_R[e];
-      const float rb = B.rho_b[c];
-      lo = floor_muldiv(P.nu_b, Rex, R);
-      const uint32_t hi = floor_muldiv(P.nu_b, Rex + q40(rb), R);
-      n = hi > lo ? hi - lo : 0u;  // hi < lo only after a latched look-back failure
-      float pA = 0.0f;
-      if constexpr (RADAR) {
-        pA = B.pA[c];
-        zv = B.zv[c];
-        sg = B.sgv[c];
-      }
-      nA = (uint32_t)__fadd_rn(__fmul_rn((float)n, pA), 0.5f);
-      if (nA > n) nA = n;
-      const uint32_t nUA = n - nA;
-      if (nA > 0u && nUA > 0u) {
-        wA = __fdiv_rn(__fmul_rn(pA, rb), (float)nA);
-        wUA = __fdiv_rn(__fmul_rn(__fsub_rn(1.0f, pA), rb), (float)nUA);
-      } else if (nA > 0u) {
-        wA = __fdiv_rn(rb, (float)nA);
-      } else if (n > 0u) {
-        wUA = __fdiv_rn(rb, (float)nUA);
-      }
+  for (uint32_t s = blockIdx.x * BIRTH_BLOCK + threadIdx.x; s < P.nu_b; s += stride) {
+    // owning birth cell: the first list entry e with nu_b * Rincl_e >= (s + 1) * R
+    const U128 target = mul_64x64((unsigned long long)s + 1ull, R);
+    uint32_t lo = 0, hi = nbc - 1u;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (lt_128(mul_64x64(P.nu_b, __ldg(B.bl_R + mid)), target)) lo = mid + 1u; else hi = mid;
     }
-    const uint32_t last = min(31u, nbc - 1u - e0);
-    const uint32_t s_begin = __shfl_sync(FULL, lo, 0);
-    const uint32_t s_end = __shfl_sync(FULL, lo, last) + __shfl_sync(FULL, n, last);
-    for (uint32_t sb = s_begin; sb < s_end; sb += 32u) {
-      const uint32_t s = sb + lane;
-      // owner entry: the last lane L <= last with lo_L <= s
-      uint32_t L = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const uint32_t cand = L + step;
-        const uint32_t lo_c = __shfl_sync(FULL, lo, cand & 31u);
-        if (cand <= last && lo_c <= s) L = cand;
-      }
-      const uint32_t lo_L = __shfl_sync(FULL, lo, L);
-      const uint32_t c_L = __shfl_sync(FULL, c, L);
-      const uint32_t nA_L = __shfl_sync(FULL, nA, L);
-      const float wA_L = __shfl_sync(FULL, wA, L), wUA_L = __shfl_sync(FULL, wUA, L);
-      const float zv_L = __shfl_sync(FULL, zv, L), sg_L = __shfl_sync(FULL, sg, L);
-      if (s < s_end && s < P.nu_b) {
-        const bool assoc = (s - lo_L) < nA_L;
-        birth_init(P, B, s, c_L, assoc, assoc ? wA_L : wUA_L, zv_L, sg_L, frame, record);
-      }
+    const uint32_t c = __ldg(B.bl_cell + lo);
+    const unsigned long long Rin = __ldg(B.bl_R + lo);
+    const unsigned long long Rex = lo > 0u ? __ldg(B.bl_R + lo - 1u) : 0ull;
+    const uint32_t first = floor_muldiv(P.nu_b, Rex, R);
+    const uint32_t last = floor_muldiv(P.nu_b, Rin, R);
+    const uint32_t n = last > first ? last - first : 1u;  // n = 0 only after a latched failure
+    const uint32_t t = s >= first ? s - first : 0u;
+    const float rb = __ldg(B.rho_b + c);
+    float pA = 0.0f, zv = 0.0f, sg = 1.0f;
+    if constexpr (RADAR) {
+      pA = __ldg(B.pA + c);
+      zv = __ldg(B.zv + c);
+      sg = __ldg(B.sgv + c);
     }
+    uint32_t nA = (uint32_t)__fadd_rn(__fmul_rn((float)n, pA), 0.5f);
+    if (nA > n) nA = n;
+    const uint32_t nUA = n - nA;
+    const bool assoc = t < nA;
+    float w;
+    if (nA > 0u && nUA > 0u)
+      w = assoc ? __fdiv_rn(__fmul_rn(pA, rb), (float)nA)
+                : __fdiv_rn(__fmul_rn(__fsub_rn(1.0f, pA), rb), (float)nUA);
+    else
+      w = __fdiv_rn(rb, (float)n);
+    birth_init(P, B, s, c, assoc, w, zv, sg, frame, record);
   }
 }
 
@@ -820,6 +799,16 @@ __global__ void __launch_bounds__(BIRTH_BLOCK) k_birth(KParams P, DevBufs B) {
 //   that leaves each tile's inclusive prefix for k_resample.
 // ====================================================================================
 constexpr int NORM_BLOCK = 256, NORM_ITEMS = 8, NORM_TILE = NORM_BLOCK * NORM_ITEMS;
+
+// fixed-point moment terms of one particle: u v_x, u v_y, u v_x^2, u v_y^2, u v_x v_y
+__device__ __forceinline__ void moment_terms(float u, float vx, float vy, unsigned long long (&m)[5]) {
+  const float mx = __fmul_rn(u, vx), my = __fmul_rn(u, vy);
+  m[0] = q40s(mx);
+  m[1] = q40s(my);
+  m[2] = q40s(__fmul_rn(mx, vx));
+  m[3] = q40s(__fmul_rn(my, vy));
+  m[4] = q40s(__fmul_rn(mx, vy));
+}
 
 template <bool RADAR>
 __global__ void __launch_bounds__(NORM_BLOCK) k_normalise(KParams P, DevBufs B) {
@@ -836,7 +825,7 @@ __global__ void __launch_bounds__(NORM_BLOCK) k_normalise(KParams P, DevBufs B) 
   unsigned long long qsum = 0ull;
   const bool has_pers = tile * NORM_TILE < P.nu;  // block-uniform
   uint32_t key[NORM_ITEMS];
-  unsigned long long mv[NORM_ITEMS][5];
+  float mu[NORM_ITEMS], mvx[NORM_ITEMS], mvy[NORM_ITEMS];  // u = w'/rho_p and velocities
   uint32_t head = 0, tail = 0;
   Seg<5> agg;
   agg.f = 0;
@@ -859,8 +848,9 @@ __global__ void __launch_bounds__(NORM_BLOCK) k_normalise(KParams P, DevBufs B) 
       const bool t = ok && (j == P.nu - 1 || key[it] != kn);
       head |= (uint32_t)h << it;
       tail |= (uint32_t)t << it;
-#pragma unroll
-      for (int k = 0; k < 5; ++k) mv[it][k] = 0ull;
+      mu[it] = 0.0f;
+      mvx[it] = 0.0f;
+      mvy[it] = 0.0f;
       wn_out[it] = 0.0f;
       if (ok) {
         const uint32_t i = idx[it], c = key[it];
@@ -881,18 +871,13 @@ __global__ void __launch_bounds__(NORM_BLOCK) k_normalise(KParams P, DevBufs B) 
         wn_out[it] = wn;
         qsum += q40(wn);
         const float rp = __ldg(B.rho_p + c);
-        const float u = rp > 0.0f ? __fdiv_rn(wn, rp) : 0.0f;
-        const float mx = __fmul_rn(u, vx), my = __fmul_rn(u, vy);
-        mv[it][0] = q40s(mx);
-        mv[it][1] = q40s(my);
-        mv[it][2] = q40s(__fmul_rn(mx, vx));
-        mv[it][3] = q40s(__fmul_rn(my, vy));
-        mv[it][4] = q40s(__fmul_rn(mx, vy));
+        mu[it] = rp > 0.0f ? __fdiv_rn(wn, rp) : 0.0f;
+        mvx[it] = vx;
+        mvy[it] = vy;
       }
       Seg<5> e;
       e.f = h;
-#pragma unroll
-      for (int k = 0; k < 5; ++k) e.v[k] = mv[it][k];
+      moment_terms(mu[it], mvx[it], mvy[it], e.v);
       agg = seg_combine(agg, e);
     }
     if (j0 + NORM_ITEMS <= P.nu) {
@@ -941,8 +926,10 @@ __global__ void __launch_bounds__(NORM_BLOCK) k_normalise(KParams P, DevBufs B) 
 #pragma unroll
   for (int it = 0; it < NORM_ITEMS; ++it) {
     const bool h = (head >> it) & 1u, t = (tail >> it) & 1u;
+    unsigned long long m[5];
+    moment_terms(mu[it], mvx[it], mvy[it], m);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) run[k] = h ? mv[it][k] : run[k] + mv[it][k];
+    for (int k = 0; k < 5; ++k) run[k] = h ? m[k] : run[k] + m[k];
     if (t) {
       const uint32_t c = key[it];
       const float rp = __ldg(B.rho_p + c);

@@ -160,11 +160,19 @@ __device__ __forceinline__ U128 add_128_64(U128 a, unsigned long long b) {
 __device__ __forceinline__ bool lt_128(U128 a, U128 b) {
   return (a.hi < b.hi) || (a.hi == b.hi && a.lo < b.lo);
 }
-// floor(a * b / d) for b <= d (so the result lies in [0, a]): bisection on the quotient
-// with exact 128-bit comparisons
+// floor(a * b / d) for b <= d (so the result lies in [0, a]), exactly: a float estimate
+// brackets the quotient (+-16; the bracket is checked and widened to [0, a] if it fails),
+// then bisection with exact 128-bit comparisons
 __device__ __forceinline__ uint32_t floor_muldiv(uint32_t a, unsigned long long b, unsigned long long d) {
   const U128 ab = mul_64x64(a, b);
-  uint32_t lo = 0, hi = a;
+  const float est = __fmul_rn((float)a, __fdiv_rn(__ull2float_rn(b), __ull2float_rn(d)));
+  const uint32_t q = est >= (float)a ? a : (uint32_t)est;
+  uint32_t lo = q > 16u ? q - 16u : 0u;
+  uint32_t hi = (a - q) > 16u ? q + 16u : a;
+  if (lt_128(ab, mul_64x64(lo, d)) || (hi < a && !lt_128(ab, mul_64x64((unsigned long long)hi + 1, d)))) {
+    lo = 0;
+    hi = a;
+  }
   while (lo < hi) {
     const uint32_t mid = lo + (hi - lo + 1) / 2;
     if (lt_128(ab, mul_64x64(mid, d))) hi = mid - 1; else lo = mid;
