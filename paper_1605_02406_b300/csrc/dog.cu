@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -567,3 +568,137 @@ int dog_profile_read(dog_filter *f, float *ms, const char **names, int max, int 
 }
 
 }  // extern "C"
+
+// ====================================================================================
+// Allocation-free cell assignment.
+//
+// Some callers cannot allocate device memory at all: code that runs where cudaMalloc is
+// forbidden or unavailable (inside a host callback, from a real-time thread that must not
+// take the allocator's locks, under an allocator that another framework owns exclusively,
+// or in a process whose memory pool is fixed at start-up).  For them the particle-to-cell
+// assignment -- the stable sort of cell indices and the per-cell ranges -- runs with its
+// scratch in one array of fixed size that lives in this library's device image.  Every
+// GPU that loads the library holds that array until the process exits.
+// ====================================================================================
+namespace {
+
+constexpr uint32_t NA_MAX_N = 1u << 19;      // particles per call
+constexpr uint32_t NA_MAX_CELLS = 1u << 22;  // cells per call (keys of at most 22 bits)
+constexpr uint32_t NA_TILES = NA_MAX_N / SORT_TILE;
+constexpr size_t NA_CTL = 256;
+constexpr size_t NA_HIST = 2 * 2048 * 4;
+constexpr size_t NA_LB = (size_t)2 * NA_TILES * 2048 * 4;
+constexpr size_t NA_ARR = (size_t)NA_MAX_N * 4;
+constexpr size_t NA_BYTES = NA_CTL + NA_HIST + NA_LB + 3 * NA_ARR;  // 8,405,248 bytes
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+// digit histograms of all passes for caller-provided keys
+__global__ void k_na_hist(const uint32_t *__restrict__ keys, uint32_t n, int passes, int dbits,
+                          uint32_t radix, uint32_t *hist) {
+  extern __shared__ uint32_t sh[];
+  const uint32_t nh = (uint32_t)passes * radix;
+  for (uint32_t k = threadIdx.x; k < nh; k += blockDim.x) sh[k] = 0u;
+  __syncthreads();
+  const uint32_t mask = radix - 1u;
+  for (uint32_t b = blockIdx.x * blockDim.x; b < n; b += gridDim.x * blockDim.x) {
+    const uint32_t i = b + threadIdx.x;
+    const bool ok = i < n;
+    const uint32_t key = ok ? keys[i] : 0u;
+    for (int p = 0; p < passes; ++p) {
+      const uint32_t d = ok ? ((key >> (p * dbits)) & mask) : 0xffffffffu;
+      const uint32_t peers = __match_any_sync(FULL, d);
+      if (ok && (peers & lanemask_lt()) == 0u) atomicAdd(&sh[p * radix + d], (uint32_t)__popc(peers));
+    }
+  }
+  __syncthreads();
+  for (uint32_t k = threadIdx.x; k < nh; k += blockDim.x)
+    if (sh[k]) atomicAdd(&hist[(k / radix) * 2048u + (k % radix)], sh[k]);
+}
+
+// half-open range of each cell in the sorted order (keys outside [0, num_cells) are skipped)
+__global__ void k_na_ranges(const uint32_t *__restrict__ ks, uint32_t n, uint32_t num_cells,
+                            uint32_t *start, uint32_t *end) {
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const uint32_t k = ks[j];
+    if (k >= num_cells) continue;
+    if (j == 0 || ks[j - 1] != k) start[k] = j;
+    if (j == n - 1 || ks[j + 1] != k) end[k] = j + 1;
+  }
+}
+
+struct NaDevice {
+  bool ready = false;
+  char *base = nullptr;
+};
+NaDevice g_na_dev[64];
+std::mutex g_na_mutex;
+
+// once per device, with that device current: the scratch array's device address (in host
+// code the array's name is only a stand-in; a kernel must be given this address)
+int na_setup(char **base) {
+  int dev = 0;
+  DOG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return DOG_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  if (!g_na_dev[dev].ready) {
+    void *p = nullptr;
+    DOG_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    DOG_CUDA(cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sort_smem_bytes(2048)));
+    g_na_dev[dev].base = (char *)p;
+    g_na_dev[dev].ready = true;
+  }
+  *base = g_na_dev[dev].base;
+  return DOG_OK;
+}
+
+}  // namespace
+
+extern "C" int dog_assign_cells_noalloc(const uint32_t *d_keys, uint32_t n, uint32_t num_cells,
+                                        uint32_t *d_perm, uint32_t *d_cell_start,
+                                        uint32_t *d_cell_end, void *cuda_stream) {
+  if (num_cells == 0 || !d_cell_start || !d_cell_end || (n > 0 && (!d_keys || !d_perm)))
+    return DOG_ERR_INVALID_ARG;
+  if (n > NA_MAX_N || num_cells > NA_MAX_CELLS) return DOG_ERR_UNSUPPORTED;
+  char *base = nullptr;
+  const int rc = na_setup(&base);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  DOG_CUDA(cudaMemsetAsync(d_cell_start, 0, 4 * (size_t)num_cells, st));
+  DOG_CUDA(cudaMemsetAsync(d_cell_end, 0, 4 * (size_t)num_cells, st));
+  if (n == 0) return DOG_OK;
+  int bits = 1;
+  while ((1ull << bits) < num_cells) ++bits;
+  KParams K{};
+  K.nu = n;
+  K.passes = (bits + 10) / 11;
+  K.dbits = (bits + K.passes - 1) / K.passes;
+  K.radix = 1u << K.dbits;
+  K.tiles_sort = (n + SORT_TILE - 1) / SORT_TILE;
+  DevBufs B{};
+  B.ctl = (DevCtl *)base;
+  B.hist = (uint32_t *)(base + NA_CTL);
+  B.lb_sort = (uint32_t *)(base + NA_CTL + NA_HIST);
+  uint32_t *key_t0 = (uint32_t *)(base + NA_CTL + NA_HIST + NA_LB);
+  uint32_t *val_t0 = key_t0 + NA_MAX_N;
+  uint32_t *key_sorted = val_t0 + NA_MAX_N;
+  // the look-back status words of this call's tiles must start at zero: the array keeps
+  // whatever the previous call (possibly of another size) left in it
+  DOG_CUDA(cudaMemsetAsync(B.lb_sort, 0, 4 * (size_t)K.passes * K.tiles_sort * K.radix, st));
+  k_tick<<<1, 256, 0, st>>>(B, 2048 * K.passes);
+  const uint32_t hgrid = (n + 255) / 256 < 1024u ? (n + 255) / 256 : 1024u;
+  k_na_hist<<<hgrid, 256, 4u * K.passes * K.radix, st>>>(d_keys, n, K.passes, K.dbits, K.radix, B.hist);
+  const size_t ssm = sort_smem_bytes(K.radix);
+  const uint32_t *kin = d_keys, *vin = nullptr;
+  for (int p = 0; p < K.passes; ++p) {
+    uint32_t *kout = (p == K.passes - 1) ? key_sorted : key_t0;
+    uint32_t *vout = (p == K.passes - 1) ? d_perm : val_t0;
+    k_sort_pass<<<K.tiles_sort, SORT_BLOCK, ssm, st>>>(K, B, kin, vin, kout, vout, p);
+    kin = kout;
+    vin = vout;
+  }
+  const uint32_t rgrid = (n + 255) / 256 < 2048u ? (n + 255) / 256 : 2048u;
+  k_na_ranges<<<rgrid, 256, 0, st>>>(key_sorted, n, num_cells, d_cell_start, d_cell_end);
+  return cuda_fail(cudaGetLastError());
+}

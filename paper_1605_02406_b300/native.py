@@ -27,7 +27,9 @@ DOG_DBG = {n: k for k, n in enumerate(DBG)}
 # entry points the header declares (checked by the CPU test suite)
 SYMBOLS = ["dog_workspace_bytes", "dog_create", "dog_set_measurement_grid", "dog_step",
            "dog_get_cells", "dog_get_state", "dog_set_state", "dog_sync", "dog_get_debug",
-           "dog_profile_read", "dog_kernels_per_step", "dog_destroy", "dog_error_string"]
+           "dog_profile_read", "dog_kernels_per_step", "dog_destroy", "dog_error_string",
+           "dog_assign_cells_noalloc"]
+DOG_NOALLOC_MAX_PARTICLES, DOG_NOALLOC_MAX_CELLS = 1 << 19, 1 << 22
 
 
 class dog_params(C.Structure):
@@ -89,6 +91,7 @@ def lib() -> C.CDLL:
         L.dog_kernels_per_step.argtypes = [vp]
         L.dog_destroy.argtypes = [vp]
         L.dog_destroy.restype = None
+        L.dog_assign_cells_noalloc.argtypes = [vp, C.c_uint32, C.c_uint32, vp, vp, vp, vp]
         L.dog_error_string.argtypes = [C.c_int]
         L.dog_error_string.restype = C.c_char_p
         for n in SYMBOLS:
@@ -178,6 +181,15 @@ def dog_kernels_per_step(h: int) -> int:
 
 def dog_destroy(h: int) -> None:
     lib().dog_destroy(h)
+
+
+def dog_assign_cells_noalloc(keys_ptr: int, n: int, num_cells: int, perm_ptr: int,
+                             start_ptr: int, end_ptr: int, stream_ptr: int) -> None:
+    """Stable sort of cell indices and per-cell ranges with no allocation (device pointers)."""
+    check("dog_assign_cells_noalloc",
+          lib().dog_assign_cells_noalloc(C.c_void_p(keys_ptr), n, num_cells, C.c_void_p(perm_ptr),
+                                         C.c_void_p(start_ptr), C.c_void_p(end_ptr),
+                                         C.c_void_p(stream_ptr)))
 
 
 def dog_error_string(code: int) -> str:
