@@ -70,22 +70,31 @@ def peaks() -> tuple:
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, dev: int):
         self.f = tempfile.NamedTemporaryFile("w+", delete=False)
+        self.t0 = self.t1 = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(dev), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.5)  # the sampler is running before the timed region starts
         except OSError:
             self.p = None
+
+    def start(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
 
     def stop(self) -> dict:
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
         self.p.terminate()
         self.p.wait()
         self.f.seek(0)
@@ -93,14 +102,18 @@ class Clocks:
         os.unlink(self.f.name)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        import datetime
         for r in rows:
             try:
-                sm.append(float(r[0]))
-                mx.append(float(r[1]))
+                ts = datetime.datetime.strptime(r[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                if self.t0 is not None and not (self.t0 - 0.05 <= ts <= self.t1 + 0.05):
+                    continue
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
             except (ValueError, IndexError):
                 continue
             for k, n in enumerate(names):
-                if len(r) > 3 + k and r[3 + k].strip() == "Active":
+                if len(r) > 4 + k and r[4 + k].strip() == "Active":
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
@@ -136,26 +149,33 @@ def run_reference(args) -> None:
     params = scene.filter_params(cfg)
     grids = scene.frame_sequence(cfg, min(args.steps + args.warmup, 16), 1002)
     o = OracleFilter(params, "f32")
-    for k in range(args.warmup):
+    warm = min(args.warmup, 3)
+    for k in range(warm):
         g = grids[k % len(grids)]
         o.set_measurement_grid(g["m_occ"], g["m_free"])
         o.step(0.1)
+    # bounded sample: full frames of the workload, at most args.steps and about 120 s
     t0 = time.perf_counter()
-    for k in range(args.steps):
-        g = grids[(args.warmup + k) % len(grids)]
+    done = 0
+    while done < args.steps:
+        g = grids[(warm + done) % len(grids)]
         o.set_measurement_grid(g["m_occ"], g["m_free"])
         o.step(0.1)
+        done += 1
+        if time.perf_counter() - t0 > 120.0:
+            break
     el = time.perf_counter() - t0
-    v = params["nu"] * args.steps / el
+    v = params["nu"] * done / el
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "particle-updates/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "n_gpus": args.gpus, "steps": done, "warmup": warm,
+        "ms_per_step": el / done * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": cfg["name"], "grid": "1024x1024", "cell_size_m": 0.1,
                    "num_particles": params["nu"], "num_birth": params["nu_b"]},
         "cpu_baseline": {"value": v, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} full frames after {args.warmup} warm-up frames"},
+                         "sample": f"{done} full frames (of {args.steps} requested, bounded to "
+                                   f"~120 s) after {warm} warm-up frames, single thread"},
         "e2e": {"value": v, "unit": "particle-updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -164,7 +184,7 @@ def run_reference(args) -> None:
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -208,6 +228,7 @@ def main() -> None:
     clk = Clocks(local)
     barrier()
     torch.cuda.synchronize()
+    clk.start()
     ev[0].record(st)
     for k in range(args.steps):
         f.set_measurement_grid(**dev_grids[(args.warmup + k) % n_grids])
@@ -215,6 +236,7 @@ def main() -> None:
         ev[k + 1].record(st)
     f.sync()
     torch.cuda.synchronize()
+    clk.end()
     barrier()
     clocks = clk.stop()
     per_step = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
@@ -244,18 +266,16 @@ def main() -> None:
     for k in range(args.warmup):
         e2e_step(k)
     barrier()
-    ee = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ke = min(args.steps, 100)
     t0 = time.perf_counter()
-    ee[0].record(fe.stream)
-    for k in range(args.steps):
+    for k in range(ke):
         e2e_step(args.warmup + k)
-    ee[1].record(fe.stream)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     te = torch.tensor([e2e_s], device="cuda")
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * params["nu"] * args.steps / float(te.item())
+    e2e_value = world * params["nu"] * ke / float(te.item())
     fe.close()
 
     # ------------------------------------------------------ per-kernel events (roofline)

@@ -69,7 +69,8 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
   const size_t nu = p.num_particles, nb = p.num_birth, C = d.C;
   const bool record = (p.flags & DOG_RECORD) != 0;
   B->ctl = (DevCtl *)take(sizeof(DevCtl));
-  float **pf[] = {&B->Bx, &B->By, &B->Bvx, &B->Bvy, &B->Bw, &B->Ax, &B->Ay, &B->Avx, &B->Avy, &B->Aw, &B->wn};
+  float **pf[] = {&B->Bx, &B->By, &B->Bvx, &B->Bvy, &B->Bw, &B->Ax, &B->Ay, &B->Avx, &B->Avy, &B->Aw,
+                  &B->ox, &B->oy, &B->ovx, &B->ovy, &B->ow, &B->wn};
   for (auto q : pf) *q = (float *)take(4 * nu);
   uint32_t **pu[] = {&B->key_pred, &B->key_sorted, &B->perm};
   for (auto q : pu) *q = (uint32_t *)take(4 * nu);
@@ -89,30 +90,34 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
   B->bassoc = record ? (uint32_t *)take(4 * (nb ? nb : 1)) : nullptr;
   float **pc[] = {&B->mF, &B->zO, &B->zF, &B->pA, &B->zv, &B->sgv, &B->mO, &B->rho_p, &B->rho_b,
                   &B->pO, &B->mean_x, &B->mean_y, &B->var_x, &B->var_y, &B->cov, &B->mpred,
-                  &B->muA, &B->muU, &B->paeff};
+                  &B->muA, &B->muU, &B->paeff, &B->rinv};
   for (auto q : pc) *q = (float *)take(4 * C);
   B->S = (unsigned long long *)take(8 * C);
   B->A = (unsigned long long *)take(8 * C);
   B->tag = (uint32_t *)take(4 * C);
   B->cstart = (uint32_t *)take(4 * C);
   B->cend = (uint32_t *)take(4 * C);
-  B->bl_cell = (uint32_t *)take(4 * C);
-  B->bl_R = (unsigned long long *)take(8 * C);
+  const size_t CL = (size_t)d.tiles_cell * CELL_TILE;  // per-tile lists of birth cells
+  B->bl_cell = (uint32_t *)take(4 * CL);
+  B->bl_R = (unsigned long long *)take(8 * CL);
   B->hist = (uint32_t *)take(4 * 2048 * (size_t)d.passes);
   B->lb_sort = (uint32_t *)take(4 * (size_t)d.passes * d.tiles_sort * d.radix);
-  B->seg_st = (uint32_t *)take(4 * (size_t)d.tiles_seg);
-  B->seg_v = (unsigned long long *)take(8 * 4 * (size_t)d.tiles_seg);
-  B->cell_st = (uint32_t *)take(4 * (size_t)d.tiles_cell);
-  B->cell_v = (unsigned long long *)take(8 * 4 * (size_t)d.tiles_cell);
-  B->cdf_st = (uint32_t *)take(4 * (size_t)d.tiles_norm);
-  B->cdf_v = (unsigned long long *)take(8 * 2 * (size_t)d.tiles_norm);
-  B->mom_st = (uint32_t *)take(4 * (size_t)d.tiles_norm);
-  B->mom_v = (unsigned long long *)take(8 * 10 * (size_t)d.tiles_norm);
+  B->S_piece = (unsigned long long *)take(8 * C);
+  B->A_piece = (unsigned long long *)take(8 * C);
+  B->Mx = (unsigned long long *)take(8 * 5 * C);
+  B->Mcnt = (uint32_t *)take(4 * C);
+  B->tile_q = (unsigned long long *)take(8 * (size_t)d.tiles_cell);
+  B->tile_qin = (unsigned long long *)take(8 * (size_t)d.tiles_cell);
+  B->tile_n = (uint32_t *)take(4 * (size_t)d.tiles_cell);
+  B->tile_nin = (uint32_t *)take(4 * (size_t)d.tiles_cell);
+  B->cdf_tile = (unsigned long long *)take(8 * (size_t)d.tiles_norm);
+  B->cdf_incl = (unsigned long long *)take(8 * (size_t)d.tiles_norm);
   return (off + 255) & ~(size_t)255;
 }
 
 const char *KNAMES[MAX_KERNELS] = {"k_tick", "k_predict", "k_sort_pass0", "k_sort_pass1", "k_sort_pass2",
-                                   "k_segsum", "k_cell", "k_birth", "k_normalise", "k_resample", "", ""};
+                                   "k_segsum", "k_cell", "k_scan_births", "k_birth", "k_normalise",
+                                   "k_scan_cdf", "k_resample"};
 
 }  // namespace
 
@@ -192,11 +197,17 @@ int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
   if (radar) k_cell<true><<<K.tiles_cell, CELL_BLOCK, 0, st>>>(K, B);
   else k_cell<false><<<K.tiles_cell, CELL_BLOCK, 0, st>>>(K, B);
   ++k; mark();
+  k_scan_tiles<<<1, SCAN_BLOCK, 0, st>>>(B.tile_q, B.tile_n, K.tiles_cell, B.tile_qin, B.tile_nin,
+                                          &B.ctl->R_total, &B.ctl->n_birth_cells);
+  ++k; mark();
   if (radar) k_birth<true><<<f->birth_grid, BIRTH_BLOCK, 0, st>>>(K, B);
   else k_birth<false><<<f->birth_grid, BIRTH_BLOCK, 0, st>>>(K, B);
   ++k; mark();
   if (radar) k_normalise<true><<<K.tiles_norm, NORM_BLOCK, 0, st>>>(K, B);
   else k_normalise<false><<<K.tiles_norm, NORM_BLOCK, 0, st>>>(K, B);
+  ++k; mark();
+  k_scan_tiles<<<1, SCAN_BLOCK, 0, st>>>(B.cdf_tile, nullptr, K.tiles_norm, B.cdf_incl, nullptr,
+                                          &B.ctl->W_total, nullptr);
   ++k; mark();
   k_resample<<<K.tiles_norm, RES_BLOCK, 0, st>>>(K, B);
   ++k; mark();
@@ -217,17 +228,18 @@ int read_err(dog_filter *f) {
   return DOG_OK;
 }
 
-// zero the look-back status words and cell tags (needed whenever the frame counter is set
-// to a value that earlier frames may have used as an epoch)
+// zero the sort's look-back words, the cell tags and the piece accumulators (needed
+// whenever the frame counter is set to a value earlier frames may have used, and to drop
+// whatever a failed frame left behind)
 int reset_epochs(dog_filter *f) {
   const Derived &d = f->d;
   DevBufs &B = f->B;
   DOG_CUDA(cudaMemsetAsync(B.tag, 0, 4 * (size_t)d.C, f->st));
   DOG_CUDA(cudaMemsetAsync(B.lb_sort, 0, 4 * (size_t)d.passes * d.tiles_sort * d.radix, f->st));
-  DOG_CUDA(cudaMemsetAsync(B.seg_st, 0, 4 * (size_t)d.tiles_seg, f->st));
-  DOG_CUDA(cudaMemsetAsync(B.cell_st, 0, 4 * (size_t)d.tiles_cell, f->st));
-  DOG_CUDA(cudaMemsetAsync(B.cdf_st, 0, 4 * (size_t)d.tiles_norm, f->st));
-  DOG_CUDA(cudaMemsetAsync(B.mom_st, 0, 4 * (size_t)d.tiles_norm, f->st));
+  DOG_CUDA(cudaMemsetAsync(B.S_piece, 0, 8 * (size_t)d.C, f->st));
+  DOG_CUDA(cudaMemsetAsync(B.A_piece, 0, 8 * (size_t)d.C, f->st));
+  DOG_CUDA(cudaMemsetAsync(B.Mx, 0, 8 * 5 * (size_t)d.C, f->st));
+  DOG_CUDA(cudaMemsetAsync(B.Mcnt, 0, 4 * (size_t)d.C, f->st));
   return DOG_OK;
 }
 
@@ -308,7 +320,7 @@ int dog_create(const dog_params *params, void *d_workspace, size_t workspace_byt
   K.tiles_seg = d.tiles_seg;
   K.tiles_cell = d.tiles_cell;
   K.tiles_norm = d.tiles_norm;
-  f->nk = 7 + d.passes;
+  f->nk = 9 + d.passes;
   f->profile = (params->flags & DOG_PROFILE) != 0;
   f->use_graph = !(params->flags & DOG_NO_GRAPH) && f->st != nullptr && !f->profile;
   int dev = 0, sms = 148;
@@ -532,7 +544,7 @@ int dog_get_debug(dog_filter *f, int which, void *out, int mem_kind) {
   DOG_CUDA(cudaMemcpy(buf.data(), src, bytes, cudaMemcpyDeviceToHost));
   const size_t es = bytes / C;
   for (size_t c = 0; c < C; ++c)
-    if (tag[c] != f->frame || f->frame == 0) std::memset(buf.data() + c * es, 0, es);
+    if ((tag[c] >> 1) != f->frame || f->frame == 0) std::memset(buf.data() + c * es, 0, es);
   DOG_CUDA(cudaMemcpy(out, buf.data(), bytes, mem_kind == DOG_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
   return read_err(f);
 }
@@ -541,13 +553,14 @@ int dog_profile_read(dog_filter *f, float *ms, const char **names, int max, int 
   if (!f || !ms || max <= 0) return DOG_ERR_INVALID_ARG;
   if (!f->profile) return DOG_ERR_BAD_STATE;
   DOG_CUDA(cudaStreamSynchronize(f->st));
-  // kernel slots in launch order: tick, predict, sort passes, segsum, cell, birth, norm, resample
+  // kernel slots in launch order: tick, predict, sort passes, segsum, cell, birth scan, birth,
+  // normalise, CDF scan, resample
   int slot_kind[MAX_KERNELS];
   int nk = 0;
   slot_kind[nk++] = 0;
   slot_kind[nk++] = 1;
   for (int p = 0; p < f->d.passes; ++p) slot_kind[nk++] = 2 + p;
-  for (int k = 5; k <= 9; ++k) slot_kind[nk++] = k;
+  for (int k = 5; k <= 11; ++k) slot_kind[nk++] = k;
   const int n = nk < max ? nk : max;
   for (int k = 0; k < n; ++k) ms[k] = 0.0f;
   for (int r = 0; r < f->ring_count; ++r) {

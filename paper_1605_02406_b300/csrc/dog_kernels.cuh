@@ -7,11 +7,15 @@
 //   k_sort_pass   Alg. 2  onesweep LSD radix pass(es) of (cell index, particle index)
 //   k_segsum      Alg. 2/3 cell ranges and exact fixed-point per-cell sums of w (and g w)
 //   k_cell        Alg. 3  occupancy prediction, DS update, newborn split, normalisers;
-//                          single-pass scan of the newborn masses -> list of birth cells
+//                          per-tile lists of cells with newborn mass
+//   k_scan_tiles          prefix of the tiles' newborn masses
 //   k_birth       Alg. 5  newborn particles, slots proportional to the newborn mass
-//   k_normalise   Alg. 4/6 normalised persistent weights, velocity moments, scan of the
-//                          joint weights for resampling
+//   k_normalise   Alg. 4/6 normalised persistent weights, velocity moments, tile sums of
+//                          the joint weights
+//   k_scan_tiles          CDF of the joint weights over tiles
 //   k_resample    Alg. 7  systematic resampling A + newborns -> B
+// No kernel waits for another block of the same launch except the sort passes, whose
+// digit offsets come from a bounded decoupled look-back.
 #pragma once
 #include "dog_common.cuh"
 #include "dog_math.cuh"
@@ -294,7 +298,7 @@ __global__ void __launch_bounds__(SORT_BLOCK, 2)
     s_keys[lpos[k]] = key[k];
     s_vals[lpos[k]] = val[k];
   }
-  // decoupled look-back per digit
+  // decoupled look-back per digit, eight predecessors per round trip
   const uint32_t *lb_pass = B.lb_sort + (size_t)pass * P.tiles_sort * radix;
   for (uint32_t d = tid; d < radix; d += SORT_BLOCK) {
     uint32_t excl = 0;
@@ -302,20 +306,32 @@ __global__ void __launch_bounds__(SORT_BLOCK, 2)
       long long t = (long long)tile - 1;
       int spins = 0;
       while (t >= 0) {
-        const uint32_t w = ld_volatile(lb_pass + (size_t)t * radix + d);
-        const uint32_t st = (w >> 25) & 3u;
-        if ((w >> 27) != ep5 || st == ST_NONE) {
+        uint32_t w[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          w[k] = (t - k >= 0) ? ld_volatile(lb_pass + (size_t)(t - k) * radix + d)
+                              : pack_digit(ep5, ST_INCL, 0u);
+        int k = 0;
+        bool done = false;
+        for (; k < 8; ++k) {
+          const uint32_t st = (w[k] >> 25) & 3u;
+          if ((w[k] >> 27) != ep5 || st == ST_NONE) break;  // not published yet
+          excl += w[k] & 0x1ffffffu;
+          if (st == ST_INCL) {
+            done = true;
+            break;
+          }
+        }
+        if (done) break;
+        t -= k;
+        if (k == 0) {
           if (++spins > SPIN_LIMIT) {
             atomicOr(&B.ctl->err, ERR_TIMEOUT_SORT);
             break;
           }
           if ((spins & 255) == 0 && ld_volatile(&B.ctl->err) != 0u) break;
           __nanosleep(32);
-          continue;
         }
-        excl += w & 0x1ffffffu;
-        if (st == ST_INCL) break;
-        --t;
       }
       st_volatile(lb + d, pack_digit(ep5, ST_INCL, (excl + s_cnt[d]) & 0x1ffffffu));
     }
@@ -335,31 +351,35 @@ __global__ void __launch_bounds__(SORT_BLOCK, 2)
 
 // ====================================================================================
 // Segmented sums over the sorted particles.  A thread owns ITEMS consecutive sorted
-// positions; segments are the cells (runs of equal keys).  Sums of segments that cross
-// thread and tile boundaries are carried by a block-wide segmented scan and a decoupled
-// look-back over tiles; the thread holding a segment's last position writes its total.
+// positions; segments are the cells (runs of equal keys).  A block reduces its tile with a
+// block-wide segmented scan.  A segment inside one tile is finished by the thread holding
+// its last particle; a segment that crosses tile boundaries leaves one piece per tile,
+// added with 64-bit integer atomics (exact, so their order does not matter) to a per-cell
+// accumulator that is read and cleared after all pieces are in.  k_segsum also writes
+// the predicted particles in sorted order, so later kernels stream them contiguously.  No block waits for
+// another block.
 // ====================================================================================
 constexpr int SEG_BLOCK = 256, SEG_ITEMS = 8, SEG_TILE = SEG_BLOCK * SEG_ITEMS;
 
-template <int N>
+template <int N, typename V = unsigned long long>
 struct Seg {
   uint32_t f;  // a segment head lies in the covered range
-  unsigned long long v[N];
+  V v[N];
 };
 
 // (a then b): a head in b cuts off a
-template <int N>
-__device__ __forceinline__ Seg<N> seg_combine(const Seg<N> &a, const Seg<N> &b) {
-  Seg<N> r;
+template <int N, typename V>
+__device__ __forceinline__ Seg<N, V> seg_combine(const Seg<N, V> &a, const Seg<N, V> &b) {
+  Seg<N, V> r;
   r.f = a.f | b.f;
 #pragma unroll
   for (int k = 0; k < N; ++k) r.v[k] = b.f ? b.v[k] : a.v[k] + b.v[k];
   return r;
 }
 
-template <int N>
-__device__ __forceinline__ Seg<N> seg_shfl_up(const Seg<N> &a, int o) {
-  Seg<N> r;
+template <int N, typename V>
+__device__ __forceinline__ Seg<N, V> seg_shfl_up(const Seg<N, V> &a, int o) {
+  Seg<N, V> r;
   r.f = __shfl_up_sync(FULL, a.f, o);
 #pragma unroll
   for (int k = 0; k < N; ++k) r.v[k] = __shfl_up_sync(FULL, a.v[k], o);
@@ -367,71 +387,36 @@ __device__ __forceinline__ Seg<N> seg_shfl_up(const Seg<N> &a, int o) {
 }
 
 // Block-wide exclusive segmented scan of per-thread aggregates (SEG_BLOCK threads).
-// Returns the thread's exclusive prefix; tile_total receives the whole block's value.
-template <int N>
-__device__ Seg<N> block_seg_excl(const Seg<N> &x, Seg<N> *s_w /* [SEG_BLOCK/32 + 1] */,
-                                 Seg<N> &tile_total) {
+template <int N, typename V>
+__device__ Seg<N, V> block_seg_excl(const Seg<N, V> &x, Seg<N, V> *s_w /* [SEG_BLOCK/32 + 1] */) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Seg<N> inc = x;
+  Seg<N, V> inc = x;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const Seg<N> t = seg_shfl_up(inc, o);
+    const Seg<N, V> t = seg_shfl_up(inc, o);
     if (lane >= o) inc = seg_combine(t, inc);
   }
   if (lane == 31) s_w[warp] = inc;
   __syncthreads();
   if (threadIdx.x == 0) {
-    Seg<N> run;
+    Seg<N, V> run;
     run.f = 0;
 #pragma unroll
-    for (int k = 0; k < N; ++k) run.v[k] = 0ull;
+    for (int k = 0; k < N; ++k) run.v[k] = V(0);
     for (int w = 0; w < SEG_BLOCK / 32; ++w) {
-      const Seg<N> t = s_w[w];
+      const Seg<N, V> t = s_w[w];
       s_w[w] = run;
       run = seg_combine(run, t);
     }
-    s_w[SEG_BLOCK / 32] = run;
   }
   __syncthreads();
-  Seg<N> prev = seg_shfl_up(inc, 1);
+  Seg<N, V> prev = seg_shfl_up(inc, 1);
   if (lane == 0) {
     prev.f = 0;
 #pragma unroll
-    for (int k = 0; k < N; ++k) prev.v[k] = 0ull;
+    for (int k = 0; k < N; ++k) prev.v[k] = V(0);
   }
-  tile_total = s_w[SEG_BLOCK / 32];
   return seg_combine(s_w[warp], prev);
-}
-
-// Tile carry of a segmented scan: publish (a tile with a head is inclusive at once),
-// look back when the tile's leading run continues an earlier segment.
-template <int N>
-__device__ void seg_tile_carry(uint32_t *st, unsigned long long *vals, uint32_t tile, uint32_t epoch,
-                               const Seg<N> &tot, unsigned long long (&cin)[N], uint32_t *err,
-                               uint32_t errbit, unsigned long long *s_cin /* [N] */) {
-  if (threadIdx.x == 0) lb_publish<N>(st, vals, tile, epoch, tot.f ? ST_INCL : ST_AGG, tot.v);
-  if (threadIdx.x < 32) {
-    unsigned long long acc[N];
-    if (tile > 0) {
-      lb_lookback<N>(st, vals, tile, epoch, acc, err, errbit);
-    } else {
-#pragma unroll
-      for (int k = 0; k < N; ++k) acc[k] = 0ull;
-    }
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int k = 0; k < N; ++k) s_cin[k] = acc[k];
-      if (!tot.f) {
-        unsigned long long inc[N];
-#pragma unroll
-        for (int k = 0; k < N; ++k) inc[k] = acc[k] + tot.v[k];
-        lb_publish<N>(st, vals, tile, epoch, ST_INCL, inc);
-      }
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < N; ++k) cin[k] = s_cin[k];
 }
 
 // radial-velocity likelihood g (constant factor dropped; it cancels in mu_A)
@@ -461,24 +446,51 @@ __device__ __forceinline__ void load_run(const uint32_t *p, uint32_t j0, uint32_
   }
 }
 
+// ITEMS consecutive floats at position j0 (16-byte accesses when the run is interior)
+template <int ITEMS>
+__device__ __forceinline__ void load_runf(const float *p, uint32_t j0, uint32_t n, float (&o)[ITEMS]) {
+  if (j0 + ITEMS <= n) {
+#pragma unroll
+    for (int k = 0; k < ITEMS; k += 4) {
+      const float4 v = __ldg(reinterpret_cast<const float4 *>(p + j0 + k));
+      o[k] = v.x; o[k + 1] = v.y; o[k + 2] = v.z; o[k + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) o[k] = (j0 + k < n) ? __ldg(p + j0 + k) : 0.0f;
+  }
+}
+template <int ITEMS>
+__device__ __forceinline__ void store_run(float *p, uint32_t j0, uint32_t n, const float (&v)[ITEMS]) {
+  if (j0 + ITEMS <= n) {
+#pragma unroll
+    for (int k = 0; k < ITEMS; k += 4)
+      *reinterpret_cast<float4 *>(p + j0 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k)
+      if (j0 + k < n) p[j0 + k] = v[k];
+  }
+}
+
 // k_segsum: cell ranges (Alg. 2) and S_c = sum of q40(w) (Eq. DS_particle_sum_pred as an
 // exact fixed-point sum), plus A_c = sum of q40(g w) where the cell has a radar likelihood.
+// tag[c] = 2 frame (finished here) or 2 frame + 1 (pieces in the accumulators).  The
+// predicted state is gathered through the sort permutation into sorted order (ox..ow).
 template <bool RADAR>
 __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
   constexpr int N = RADAR ? 2 : 1;
   __shared__ Seg<N> s_w[SEG_BLOCK / 32 + 1];
-  __shared__ unsigned long long s_cin[N];
-  __shared__ uint32_t s_tile;
-  if (threadIdx.x == 0) s_tile = (uint32_t)atomicAdd(&B.ctl->ctr[CTR_SEG], 1ull);
-  __syncthreads();
-  const uint32_t tile = s_tile, frame = B.ctl->frame, epoch = frame & 0x3fffffffu;
+  const uint32_t tile = blockIdx.x, frame = B.ctl->frame;
   const uint32_t j0 = tile * SEG_TILE + threadIdx.x * SEG_ITEMS;
+  const uint32_t last_valid = min(tile * SEG_TILE + SEG_TILE, P.nu) - 1u;
   uint32_t key[SEG_ITEMS], idx[SEG_ITEMS];
   load_run<SEG_ITEMS>(B.key_sorted, j0, P.nu, key, 0xffffffffu);
   load_run<SEG_ITEMS>(B.perm, j0, P.nu, idx, 0u);
   const uint32_t kprev = (j0 > 0 && j0 <= P.nu) ? __ldg(B.key_sorted + j0 - 1) : 0xfffffffeu;
   const uint32_t knext = (j0 + SEG_ITEMS < P.nu) ? __ldg(B.key_sorted + j0 + SEG_ITEMS) : 0xfffffffeu;
   unsigned long long v[SEG_ITEMS][N];
+  float sx[SEG_ITEMS], sy[SEG_ITEMS], svx[SEG_ITEMS], svy[SEG_ITEMS], sw[SEG_ITEMS];
   uint32_t head = 0, tail = 0;
   Seg<N> agg;
   agg.f = 0;
@@ -498,14 +510,17 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
     for (int k = 0; k < N; ++k) v[it][k] = 0ull;
     if (ok) {
       const uint32_t i = idx[it];
-      const float w = __ldg(B.Aw + i);
-      v[it][0] = q40(w);
+      sx[it] = __ldg(B.Ax + i);
+      sy[it] = __ldg(B.Ay + i);
+      svx[it] = __ldg(B.Avx + i);
+      svy[it] = __ldg(B.Avy + i);
+      sw[it] = __ldg(B.Aw + i);
+      v[it][0] = q40(sw[it]);
       if constexpr (RADAR) {
         const uint32_t c = key[it];
         if (__ldg(B.pA + c) > 0.0f) {
-          const float g = radar_lik(P, __ldg(B.Ax + i), __ldg(B.Ay + i), __ldg(B.Avx + i),
-                                    __ldg(B.Avy + i), __ldg(B.zv + c), __ldg(B.sgv + c));
-          v[it][N - 1] = q40(__fmul_rn(g, w));
+          const float g = radar_lik(P, sx[it], sy[it], svx[it], svy[it], __ldg(B.zv + c), __ldg(B.sgv + c));
+          v[it][N - 1] = q40(__fmul_rn(g, sw[it]));
         }
       }
     }
@@ -515,35 +530,117 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
     for (int k = 0; k < N; ++k) e.v[k] = v[it][k];
     agg = seg_combine(agg, e);
   }
-  Seg<N> tot;
-  const Seg<N> ex = block_seg_excl<N>(agg, s_w, tot);
-  unsigned long long cin[N];
-  seg_tile_carry<N>(B.seg_st, B.seg_v, tile, epoch, tot, cin, &B.ctl->err, ERR_TIMEOUT_SEG, s_cin);
+  store_run<SEG_ITEMS>(B.ox, j0, P.nu, sx);
+  store_run<SEG_ITEMS>(B.oy, j0, P.nu, sy);
+  store_run<SEG_ITEMS>(B.ovx, j0, P.nu, svx);
+  store_run<SEG_ITEMS>(B.ovy, j0, P.nu, svy);
+  store_run<SEG_ITEMS>(B.ow, j0, P.nu, sw);
+  const Seg<N> ex = block_seg_excl(agg, s_w);
   unsigned long long run[N];
 #pragma unroll
-  for (int k = 0; k < N; ++k) run[k] = ex.f ? ex.v[k] : ex.v[k] + cin[k];
+  for (int k = 0; k < N; ++k) run[k] = ex.v[k];
+  bool seen = ex.f != 0;  // the current segment's head lies in this tile
 #pragma unroll
   for (int it = 0; it < SEG_ITEMS; ++it) {
+    const uint32_t j = j0 + it;
+    if (j >= P.nu) break;
     const bool h = (head >> it) & 1u, t = (tail >> it) & 1u;
 #pragma unroll
     for (int k = 0; k < N; ++k) run[k] = h ? v[it][k] : run[k] + v[it][k];
+    seen |= h;
     const uint32_t c = key[it];
-    if (h) B.cstart[c] = j0 + it;
+    if (h) B.cstart[c] = j;
     if (t) {
-      B.cend[c] = j0 + it + 1;
-      B.S[c] = run[0];
-      if constexpr (RADAR) B.A[c] = run[N - 1];
-      B.tag[c] = frame;
+      B.cend[c] = j + 1;
+      if (seen) {
+        B.S[c] = run[0];
+        if constexpr (RADAR) B.A[c] = run[N - 1];
+        B.tag[c] = frame << 1;
+      } else {
+        atomicAdd(B.S_piece + c, run[0]);
+        if constexpr (RADAR) atomicAdd(B.A_piece + c, run[N - 1]);
+        B.tag[c] = (frame << 1) | 1u;
+      }
+    } else if (j == last_valid) {
+      atomicAdd(B.S_piece + c, run[0]);
+      if constexpr (RADAR) atomicAdd(B.A_piece + c, run[N - 1]);
     }
   }
 }
 
 // ====================================================================================
+// k_scan_tiles: inclusive prefix sums of per-tile totals (one block); the grand totals go
+// to the control block.  Used for the newborn-mass scan over cell tiles and for the CDF of
+// the joint weights over source tiles.
+// ====================================================================================
+constexpr int SCAN_BLOCK = 1024;
+
+__global__ void __launch_bounds__(SCAN_BLOCK)
+    k_scan_tiles(const unsigned long long *__restrict__ q, const uint32_t *__restrict__ n, uint32_t count,
+                 unsigned long long *q_incl, uint32_t *n_incl, unsigned long long *q_total,
+                 uint32_t *n_total) {
+  __shared__ unsigned long long s_q[SCAN_BLOCK / 32];
+  __shared__ uint32_t s_n[SCAN_BLOCK / 32];
+  const uint32_t per = (count + SCAN_BLOCK - 1) / SCAN_BLOCK;
+  const uint32_t b = threadIdx.x * per;
+  unsigned long long lq = 0ull;
+  uint32_t ln = 0u;
+  for (uint32_t k = 0; k < per; ++k)
+    if (b + k < count) {
+      lq += q[b + k];
+      if (n) ln += n[b + k];
+    }
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long iq = lq;
+  uint32_t in = ln;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long tq = __shfl_up_sync(FULL, iq, o);
+    const uint32_t tn = __shfl_up_sync(FULL, in, o);
+    if (lane >= (uint32_t)o) {
+      iq += tq;
+      in += tn;
+    }
+  }
+  if (lane == 31) {
+    s_q[warp] = iq;
+    s_n[warp] = in;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long rq = 0ull;
+    uint32_t rn = 0u;
+    for (int w = 0; w < SCAN_BLOCK / 32; ++w) {
+      const unsigned long long tq = s_q[w];
+      const uint32_t tn = s_n[w];
+      s_q[w] = rq;
+      s_n[w] = rn;
+      rq += tq;
+      rn += tn;
+    }
+    *q_total = rq;
+    if (n_total) *n_total = rn;
+  }
+  __syncthreads();
+  unsigned long long rq = s_q[warp] + iq - lq;
+  uint32_t rn = s_n[warp] + in - ln;
+  for (uint32_t k = 0; k < per; ++k)
+    if (b + k < count) {
+      rq += q[b + k];
+      q_incl[b + k] = rq;
+      if (n) {
+        rn += n[b + k];
+        n_incl[b + k] = rn;
+      }
+    }
+}
+
+// ====================================================================================
 // k_cell (Alg. 3 + the cell half of Alg. 4): per cell the predicted occupied mass
 // min(S, 1), the free-mass prediction, Dempster's rule with the measurement BBA, the
-// newborn / persistent split and the normalisers mu_A, mu_UA.  The newborn masses are
-// scanned in cell order (single pass, decoupled look-back) and the cells with newborn
-// mass are listed in order with their inclusive prefix for k_birth.
+// newborn / persistent split and the normalisers mu_A, mu_UA.  Each tile lists, in cell
+// order, its cells with newborn mass together with the tile-local inclusive prefix of the
+// fixed-point newborn masses; k_scan_tiles then scans the tile totals.
 // ====================================================================================
 constexpr int CELL_BLOCK = 256, CELL_ITEMS = 4, CELL_TILE = CELL_BLOCK * CELL_ITEMS;
 
@@ -576,13 +673,9 @@ template <bool RADAR>
 __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
   __shared__ unsigned long long s_wq[CELL_BLOCK / 32 + 1];
   __shared__ uint32_t s_wn[CELL_BLOCK / 32 + 1];
-  __shared__ unsigned long long s_cin[2];
-  __shared__ uint32_t s_tile;
-  if (threadIdx.x == 0) s_tile = (uint32_t)atomicAdd(&B.ctl->ctr[CTR_CELL], 1ull);
-  __syncthreads();
-  const uint32_t tile = s_tile, frame = B.ctl->frame, epoch = frame & 0x3fffffffu;
+  const uint32_t tile = blockIdx.x, frame = B.ctl->frame;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned long long qex[CELL_ITEMS], qin[CELL_ITEMS];
+  unsigned long long qin[CELL_ITEMS];
   uint32_t nex[CELL_ITEMS];
   bool has[CELL_ITEMS];
   unsigned long long wq = 0ull;  // running sums of this warp, in cell order
@@ -592,8 +685,16 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
     const uint32_t c = tile * CELL_TILE + warp * (32 * CELL_ITEMS) + it * 32 + lane;
     unsigned long long qb = 0ull;
     if (c < P.C) {
-      const bool occ = B.tag[c] == frame;
-      const unsigned long long S = occ ? B.S[c] : 0ull;
+      const uint32_t tg = B.tag[c];
+      const bool occ = (tg >> 1) == frame;
+      const bool cross = occ && (tg & 1u);
+      unsigned long long S = 0ull;
+      if (cross) {
+        S = atomicExch(B.S_piece + c, 0ull);  // all pieces are in; clear for the next frame
+        B.S[c] = S;
+      } else if (occ) {
+        S = B.S[c];
+      }
       const float Sf = fx40_to_f(S);
       const float mp = fminf(Sf, 1.0f);
       float mO, mF, rb;
@@ -606,9 +707,16 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
       B.rho_p[c] = rp;
       B.pO[c] = __fadd_rn(mO, __fmul_rn(0.5f, __fsub_rn(__fsub_rn(1.0f, mO), mF)));
       B.muU[c] = (S > 0ull) ? __fdiv_rn(rp, Sf) : 0.0f;
+      B.rinv[c] = rp > 0.0f ? __fdiv_rn(1.0f, rp) : 0.0f;
       float muA = 0.0f, pa = 0.0f;
       if constexpr (RADAR) {
-        const unsigned long long A = occ ? B.A[c] : 0ull;
+        unsigned long long A = 0ull;
+        if (cross) {
+          A = atomicExch(B.A_piece + c, 0ull);
+          B.A[c] = A;
+        } else if (occ) {
+          A = B.A[c];
+        }
         if (A > 0ull) {
           muA = __fdiv_rn(rp, fx40_to_f(A));
           pa = B.pA[c];
@@ -634,7 +742,6 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
         sn += tn;
       }
     }
-    qex[it] = wq + sq - qb;
     qin[it] = wq + sq;
     nex[it] = wn + sn - (has[it] ? 1u : 0u);
     wq += __shfl_sync(FULL, sq, 31);
@@ -656,39 +763,17 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
       rq += tq;
       rn += tn;
     }
-    s_wq[CELL_BLOCK / 32] = rq;
-    s_wn[CELL_BLOCK / 32] = rn;
-    const unsigned long long agg[2] = {rq, (unsigned long long)rn};
-    lb_publish<2>(B.cell_st, B.cell_v, tile, epoch, tile == 0 ? ST_INCL : ST_AGG, agg);
+    B.tile_q[tile] = rq;
+    B.tile_n[tile] = rn;
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
-    unsigned long long acc[2] = {0ull, 0ull};
-    if (tile > 0) lb_lookback<2>(B.cell_st, B.cell_v, tile, epoch, acc, &B.ctl->err, ERR_TIMEOUT_CELL);
-    if (threadIdx.x == 0) {
-      s_cin[0] = acc[0];
-      s_cin[1] = acc[1];
-      const unsigned long long inc[2] = {acc[0] + s_wq[CELL_BLOCK / 32],
-                                         acc[1] + (unsigned long long)s_wn[CELL_BLOCK / 32]};
-      if (tile > 0) lb_publish<2>(B.cell_st, B.cell_v, tile, epoch, ST_INCL, inc);
-      if (tile == P.tiles_cell - 1) {
-        B.ctl->R_total = inc[0];
-        B.ctl->n_birth_cells = (uint32_t)inc[1];
-      }
-    }
-  }
-  __syncthreads();
-  const unsigned long long cq = s_cin[0] + s_wq[warp];
-  const uint32_t cn = (uint32_t)s_cin[1] + s_wn[warp];
 #pragma unroll
   for (int it = 0; it < CELL_ITEMS; ++it) {
     if (has[it]) {
       const uint32_t c = tile * CELL_TILE + warp * (32 * CELL_ITEMS) + it * 32 + lane;
-      const uint32_t pos = cn + nex[it];
-      if (pos < P.C) {  // always true unless a look-back failure was latched
-        B.bl_cell[pos] = c;
-        B.bl_R[pos] = cq + qin[it];
-      }
+      const uint32_t pos = tile * CELL_TILE + s_wn[warp] + nex[it];
+      B.bl_cell[pos] = c;
+      B.bl_R[pos] = s_wq[warp] + qin[it];
     }
   }
 }
@@ -697,8 +782,9 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
 // k_birth (Alg. 5): cell c owns the newborn slots [floor(nu_b R_{c-1}/R), floor(nu_b R_c/R))
 // of the fixed-point scan R of the newborn masses; nu_A = round(n p_A) of them form the
 // associated set (Eq. assoc_relation, assoc_sum), with weights Eq. weights_associated /
-// weights_unassociated.  One thread per slot finds its cell by bisection in the list of
-// birth cells (exact 128-bit comparisons of nu_b R_incl against (slot + 1) R).
+// weights_unassociated.  One thread per slot finds its cell by bisection, first over the
+// cell tiles' inclusive totals, then in the tile's list (exact 128-bit comparisons of
+// nu_b R_incl against (slot + 1) R).
 // ====================================================================================
 constexpr int BIRTH_BLOCK = 256;
 
@@ -743,29 +829,40 @@ template <bool RADAR>
 __global__ void __launch_bounds__(BIRTH_BLOCK) k_birth(KParams P, DevBufs B) {
   const uint32_t frame = B.ctl->frame;
   const unsigned long long R = B.ctl->R_total;
-  const uint32_t nbc = min(B.ctl->n_birth_cells, P.C);
   const bool record = (P.flags & 0x4u) != 0u;
   const uint32_t stride = gridDim.x * BIRTH_BLOCK;
-  if (R == 0ull || nbc == 0u) {
+  if (R == 0ull) {
     // no newborn mass anywhere: weight 0, cell = slot mod C
     for (uint32_t s = blockIdx.x * BIRTH_BLOCK + threadIdx.x; s < P.nu_b; s += stride)
       birth_init(P, B, s, s % P.C, false, 0.0f, 0.0f, 1.0f, frame, record);
     return;
   }
   for (uint32_t s = blockIdx.x * BIRTH_BLOCK + threadIdx.x; s < P.nu_b; s += stride) {
-    // owning birth cell: the first list entry e with nu_b * Rincl_e >= (s + 1) * R
     const U128 target = mul_64x64((unsigned long long)s + 1ull, R);
-    uint32_t lo = 0, hi = nbc - 1u;
+    // the cell tile: first T with nu_b * Qincl_T >= (s + 1) R
+    uint32_t lo = 0, hi = P.tiles_cell - 1u;
     while (lo < hi) {
       const uint32_t mid = (lo + hi) >> 1;
-      if (lt_128(mul_64x64(P.nu_b, __ldg(B.bl_R + mid)), target)) lo = mid + 1u; else hi = mid;
+      if (lt_128(mul_64x64(P.nu_b, __ldg(B.tile_qin + mid)), target)) lo = mid + 1u; else hi = mid;
     }
-    const uint32_t c = __ldg(B.bl_cell + lo);
-    const unsigned long long Rin = __ldg(B.bl_R + lo);
-    const unsigned long long Rex = lo > 0u ? __ldg(B.bl_R + lo - 1u) : 0ull;
+    const uint32_t T = lo;
+    const unsigned long long Tex = T > 0u ? __ldg(B.tile_qin + T - 1u) : 0ull;
+    const uint32_t cnt = __ldg(B.tile_n + T);
+    const uint32_t *cells = B.bl_cell + (size_t)T * CELL_TILE;
+    const unsigned long long *Rl = B.bl_R + (size_t)T * CELL_TILE;
+    // the cell within the tile's list
+    lo = 0;
+    hi = cnt > 0u ? cnt - 1u : 0u;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (lt_128(mul_64x64(P.nu_b, Tex + __ldg(Rl + mid)), target)) lo = mid + 1u; else hi = mid;
+    }
+    const uint32_t c = __ldg(cells + lo);
+    const unsigned long long Rin = Tex + __ldg(Rl + lo);
+    const unsigned long long Rex = Tex + (lo > 0u ? __ldg(Rl + lo - 1u) : 0ull);
     const uint32_t first = floor_muldiv(P.nu_b, Rex, R);
     const uint32_t last = floor_muldiv(P.nu_b, Rin, R);
-    const uint32_t n = last > first ? last - first : 1u;  // n = 0 only after a latched failure
+    const uint32_t n = last > first ? last - first : 1u;  // n = 0 only on corrupted input
     const uint32_t t = s >= first ? s - first : 0u;
     const float rb = __ldg(B.rho_b + c);
     float pA = 0.0f, zv = 0.0f, sg = 1.0f;
@@ -790,35 +887,42 @@ __global__ void __launch_bounds__(BIRTH_BLOCK) k_birth(KParams P, DevBufs B) {
 
 // ====================================================================================
 // k_normalise (Alg. 4 / Alg. 6): over the joint source index space (persistent particles
-// in sorted order, then newborn slots):
+// in sorted order, read contiguously from the sorted copy, then newborn slots):
 //   w' = p_A mu_A g w + (1 - p_A) mu_UA w   (Eq. DSnormalization; lidar cells: mu_UA w),
 //   velocity moments of the persistent particles per cell (Eq. mean_x, var_x, covar_xy):
-//   the terms u v, u v^2, u vx vy of the cell-normalised weight u = w'/rho_p are summed in
-//   exact fixed point by a segmented scan and finalised by the thread holding the cell's
-//   last particle; and the tile sums of q40 of the joint weights with a decoupled look-back
-//   that leaves each tile's inclusive prefix for k_resample.
+//   the terms u v, u v^2, u vx vy of the cell-normalised weight u = w'/rho_p are summed by
+//   the block's segmented scan in binary32 (fixed tree order, so runs repeat bit for bit);
+//   a cell spread over several tiles collects its pieces in exact fixed point with integer
+//   atomics and the tile adding the last piece (counted against the cell's tile span)
+//   finishes it; and the tile sum of q40 of the joint weights for the resampling CDF.
 // ====================================================================================
 constexpr int NORM_BLOCK = 256, NORM_ITEMS = 8, NORM_TILE = NORM_BLOCK * NORM_ITEMS;
 
-// fixed-point moment terms of one particle: u v_x, u v_y, u v_x^2, u v_y^2, u v_x v_y
-__device__ __forceinline__ void moment_terms(float u, float vx, float vy, unsigned long long (&m)[5]) {
+// moment terms of one particle: u v_x, u v_y, u v_x^2, u v_y^2, u v_x v_y (u = w'/rho_p)
+__device__ __forceinline__ void moment_terms(float u, float vx, float vy, float (&m)[5]) {
   const float mx = __fmul_rn(u, vx), my = __fmul_rn(u, vy);
-  m[0] = q40s(mx);
-  m[1] = q40s(my);
-  m[2] = q40s(__fmul_rn(mx, vx));
-  m[3] = q40s(__fmul_rn(my, vy));
-  m[4] = q40s(__fmul_rn(mx, vy));
+  m[0] = mx;
+  m[1] = my;
+  m[2] = __fmul_rn(mx, vx);
+  m[3] = __fmul_rn(my, vy);
+  m[4] = __fmul_rn(mx, vy);
+}
+
+// Eq. mean_x, var_x, covar_xy from the cell's sums of u v, u v^2, u vx vy
+__device__ __forceinline__ void moments_store(const DevBufs &B, uint32_t c, const float (&m)[5]) {
+  const float mx = m[0], my = m[1];
+  B.mean_x[c] = mx;
+  B.mean_y[c] = my;
+  B.var_x[c] = fmaxf(__fsub_rn(m[2], __fmul_rn(mx, mx)), 0.0f);
+  B.var_y[c] = fmaxf(__fsub_rn(m[3], __fmul_rn(my, my)), 0.0f);
+  B.cov[c] = __fsub_rn(m[4], __fmul_rn(mx, my));
 }
 
 template <bool RADAR>
 __global__ void __launch_bounds__(NORM_BLOCK) k_normalise(KParams P, DevBufs B) {
-  __shared__ Seg<5> s_w[NORM_BLOCK / 32 + 1];
-  __shared__ unsigned long long s_cin[5];
+  __shared__ Seg<5, float> s_w[NORM_BLOCK / 32 + 1];
   __shared__ unsigned long long s_red[NORM_BLOCK / 32];
-  __shared__ uint32_t s_tile;
-  if (threadIdx.x == 0) s_tile = (uint32_t)atomicAdd(&B.ctl->ctr[CTR_NORM], 1ull);
-  __syncthreads();
-  const uint32_t tile = s_tile, frame = B.ctl->frame, epoch = frame & 0x3fffffffu;
+  const uint32_t tile = blockIdx.x;
   const uint32_t ntot = P.nu + P.nu_b;
   const uint32_t j0 = tile * NORM_TILE + threadIdx.x * NORM_ITEMS;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -827,14 +931,16 @@ __global__ void __launch_bounds__(NORM_BLOCK) k_normalise(KParams P, DevBufs B) 
   uint32_t key[NORM_ITEMS];
   float mu[NORM_ITEMS], mvx[NORM_ITEMS], mvy[NORM_ITEMS];  // u = w'/rho_p and velocities
   uint32_t head = 0, tail = 0;
-  Seg<5> agg;
+  Seg<5, float> agg;
   agg.f = 0;
 #pragma unroll
-  for (int k = 0; k < 5; ++k) agg.v[k] = 0ull;
+  for (int k = 0; k < 5; ++k) agg.v[k] = 0.0f;
   if (has_pers) {
-    uint32_t idx[NORM_ITEMS];
+    float ws[NORM_ITEMS];
     load_run<NORM_ITEMS>(B.key_sorted, j0, P.nu, key, 0xffffffffu);
-    load_run<NORM_ITEMS>(B.perm, j0, P.nu, idx, 0u);
+    load_runf<NORM_ITEMS>(B.ow, j0, P.nu, ws);
+    load_runf<NORM_ITEMS>(B.ovx, j0, P.nu, mvx);
+    load_runf<NORM_ITEMS>(B.ovy, j0, P.nu, mvy);
     const uint32_t kprev = (j0 > 0 && j0 <= P.nu) ? __ldg(B.key_sorted + j0 - 1) : 0xfffffffeu;
     const uint32_t knext = (j0 + NORM_ITEMS < P.nu) ? __ldg(B.key_sorted + j0 + NORM_ITEMS) : 0xfffffffeu;
     float wn_out[NORM_ITEMS];
@@ -849,19 +955,16 @@ __global__ void __launch_bounds__(NORM_BLOCK) k_normalise(KParams P, DevBufs B) 
       head |= (uint32_t)h << it;
       tail |= (uint32_t)t << it;
       mu[it] = 0.0f;
-      mvx[it] = 0.0f;
-      mvy[it] = 0.0f;
       wn_out[it] = 0.0f;
       if (ok) {
-        const uint32_t i = idx[it], c = key[it];
-        const float w = __ldg(B.Aw + i);
-        const float vx = __ldg(B.Avx + i), vy = __ldg(B.Avy + i);
+        const uint32_t c = key[it];
+        const float w = ws[it];
         const float muU = __ldg(B.muU + c);
         float wn;
         const float pa = RADAR ? __ldg(B.paeff + c) : 0.0f;
         if (RADAR && pa > 0.0f) {
-          const float g = radar_lik(P, __ldg(B.Ax + i), __ldg(B.Ay + i), vx, vy, __ldg(B.zv + c),
-                                    __ldg(B.sgv + c));
+          const float g = radar_lik(P, __ldg(B.ox + j), __ldg(B.oy + j), mvx[it], mvy[it],
+                                    __ldg(B.zv + c), __ldg(B.sgv + c));
           const float a = __fmul_rn(__fmul_rn(__fmul_rn(pa, __ldg(B.muA + c)), g), w);
           const float b = __fmul_rn(__fmul_rn(__fsub_rn(1.0f, pa), muU), w);
           wn = __fadd_rn(a, b);
@@ -870,25 +973,14 @@ __global__ void __launch_bounds__(NORM_BLOCK) k_normalise(KParams P, DevBufs B) 
         }
         wn_out[it] = wn;
         qsum += q40(wn);
-        const float rp = __ldg(B.rho_p + c);
-        mu[it] = rp > 0.0f ? __fdiv_rn(wn, rp) : 0.0f;
-        mvx[it] = vx;
-        mvy[it] = vy;
+        mu[it] = __fmul_rn(wn, __ldg(B.rinv + c));
       }
-      Seg<5> e;
+      Seg<5, float> e;
       e.f = h;
       moment_terms(mu[it], mvx[it], mvy[it], e.v);
       agg = seg_combine(agg, e);
     }
-    if (j0 + NORM_ITEMS <= P.nu) {
-#pragma unroll
-      for (int k = 0; k < NORM_ITEMS; k += 4)
-        *reinterpret_cast<float4 *>(B.wn + j0 + k) = make_float4(wn_out[k], wn_out[k + 1], wn_out[k + 2], wn_out[k + 3]);
-    } else {
-#pragma unroll
-      for (int k = 0; k < NORM_ITEMS; ++k)
-        if (j0 + k < P.nu) B.wn[j0 + k] = wn_out[k];
-    }
+    store_run<NORM_ITEMS>(B.wn, j0, P.nu, wn_out);
   }
   // newborn sources of this tile
 #pragma unroll
@@ -896,60 +988,55 @@ __global__ void __launch_bounds__(NORM_BLOCK) k_normalise(KParams P, DevBufs B) 
     const uint32_t j = j0 + it;
     if (j >= P.nu && j < ntot) qsum += q40(__ldg(B.bw + (j - P.nu)));
   }
-  // tile sum of the joint quantised weights -> look-back -> inclusive prefix
+  // tile sum of the joint quantised weights (k_scan_tiles turns them into the CDF)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) qsum += __shfl_xor_sync(FULL, qsum, o);
   if (lane == 0) s_red[warp] = qsum;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    unsigned long long tsum = threadIdx.x < NORM_BLOCK / 32 ? s_red[threadIdx.x] : 0ull;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(FULL, tsum, o);
-    const unsigned long long a1[1] = {tsum};
-    if (threadIdx.x == 0) lb_publish<1>(B.cdf_st, B.cdf_v, tile, epoch, tile == 0 ? ST_INCL : ST_AGG, a1);
-    if (tile > 0) {
-      unsigned long long acc[1];
-      lb_lookback<1>(B.cdf_st, B.cdf_v, tile, epoch, acc, &B.ctl->err, ERR_TIMEOUT_NORM);
-      const unsigned long long inc[1] = {acc[0] + tsum};
-      if (threadIdx.x == 0) lb_publish<1>(B.cdf_st, B.cdf_v, tile, epoch, ST_INCL, inc);
-    }
+  if (threadIdx.x == 0) {
+    unsigned long long tsum = 0ull;
+    for (int w = 0; w < NORM_BLOCK / 32; ++w) tsum += s_red[w];
+    B.cdf_tile[tile] = tsum;
   }
   if (!has_pers) return;  // block-uniform
-  // segmented moment sums
-  Seg<5> tot;
-  const Seg<5> ex = block_seg_excl<5>(agg, s_w, tot);
-  unsigned long long cin[5];
-  seg_tile_carry<5>(B.mom_st, B.mom_v, tile, epoch, tot, cin, &B.ctl->err, ERR_TIMEOUT_NORM, s_cin);
-  unsigned long long run[5];
+  // segmented moment sums within the tile (binary32, combined in a fixed tree order)
+  const Seg<5, float> ex = block_seg_excl(agg, s_w);
+  const uint32_t last_valid = min(tile * NORM_TILE + NORM_TILE, P.nu) - 1u;
+  float run[5];
 #pragma unroll
-  for (int k = 0; k < 5; ++k) run[k] = ex.f ? ex.v[k] : ex.v[k] + cin[k];
+  for (int k = 0; k < 5; ++k) run[k] = ex.v[k];
+  bool seen = ex.f != 0;
 #pragma unroll
   for (int it = 0; it < NORM_ITEMS; ++it) {
+    const uint32_t j = j0 + it;
+    if (j >= P.nu) break;
     const bool h = (head >> it) & 1u, t = (tail >> it) & 1u;
-    unsigned long long m[5];
+    float m[5];
     moment_terms(mu[it], mvx[it], mvy[it], m);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) run[k] = h ? m[k] : run[k] + m[k];
-    if (t) {
-      const uint32_t c = key[it];
-      const float rp = __ldg(B.rho_p + c);
-      float mx = 0.0f, my = 0.0f, vxx = 0.0f, vyy = 0.0f, cxy = 0.0f;
-      if (rp > 0.0f) {
-        const double ax = fx40s_to_d(run[0]), ay = fx40s_to_d(run[1]);
-        const double sxx = fx40s_to_d(run[2]) - ax * ax;
-        const double syy = fx40s_to_d(run[3]) - ay * ay;
-        const double sxy = fx40s_to_d(run[4]) - ax * ay;
-        mx = (float)ax;
-        my = (float)ay;
-        vxx = (float)(sxx > 0.0 ? sxx : 0.0);
-        vyy = (float)(syy > 0.0 ? syy : 0.0);
-        cxy = (float)sxy;
-      }
-      B.mean_x[c] = mx;
-      B.mean_y[c] = my;
-      B.var_x[c] = vxx;
-      B.var_y[c] = vyy;
-      B.cov[c] = cxy;
+    for (int k = 0; k < 5; ++k) run[k] = h ? m[k] : __fadd_rn(run[k], m[k]);
+    seen |= h;
+    if (!t && j != last_valid) continue;
+    const uint32_t c = key[it];
+    if (t && seen) {
+      if (__ldg(B.rho_p + c) > 0.0f) moments_store(B, c, run);  // the cell lies in this tile
+      else { float z[5] = {0.f, 0.f, 0.f, 0.f, 0.f}; moments_store(B, c, z); }
+      continue;
+    }
+    // a piece of a cell spread over several tiles: exact fixed-point accumulation
+    const size_t Cs = P.C;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) atomicAdd(B.Mx + k * Cs + c, q40s(run[k]));
+    __threadfence();
+    const uint32_t span = (__ldg(B.cend + c) - 1u) / NORM_TILE - __ldg(B.cstart + c) / NORM_TILE + 1u;
+    if (atomicAdd(B.Mcnt + c, 1u) + 1u == span) {
+      __threadfence();
+      float tot[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) tot[k] = fx40s_to_f(atomicExch(B.Mx + k * Cs + c, 0ull));
+      atomicExch(B.Mcnt + c, 0u);
+      if (__ldg(B.rho_p + c) > 0.0f) moments_store(B, c, tot);
+      else { float z[5] = {0.f, 0.f, 0.f, 0.f, 0.f}; moments_store(B, c, z); }
     }
   }
 }
@@ -957,39 +1044,59 @@ __global__ void __launch_bounds__(NORM_BLOCK) k_normalise(KParams P, DevBufs B) 
 // ====================================================================================
 // k_resample (Alg. 7, systematic): with joint inclusive fixed-point CDF Q, total W and one
 // uniform offset u in [0, W), output i takes the first source j with Q_j * nu > i W + u
-// (i.e. Q_j > floor((i W + u) / nu)).  A block takes the outputs that fall in its tile of
-// sources, finds each output's source by bisection in the tile's CDF (shared memory) and
-// copies the source's state with the equal weight W / nu (Eq. resampledParticleWeights).
+// (i.e. Q_j > floor((i W + u) / nu)).  A block takes a tile of sources; each source's
+// output range ends at count(Q_j) = #{i : i W + u < Q_j nu}, found from a float estimate
+// and exact 128-bit corrections.  Each output of the tile finds its source by bisection
+// over those ends (u32, shared memory) and copies the source's state from the sorted copy
+// with the equal weight W / nu (Eq. resampledParticleWeights).
 // ====================================================================================
 constexpr int RES_BLOCK = 256;
 
-// number of outputs i in [0, nu) with i W + u < X nu
-__device__ __forceinline__ uint32_t outputs_below(unsigned long long X, unsigned long long Wt,
-                                                  unsigned long long u, uint32_t nu) {
+__device__ __forceinline__ uint32_t pad8(uint32_t m) { return m + (m >> 3); }
+
+__device__ __forceinline__ float u64_to_f32_approx(unsigned long long x) {
+  return __fadd_rn(__fmul_rn((float)(uint32_t)(x >> 32), 0x1p32f), (float)(uint32_t)x);
+}
+
+// #{i in [0, nu) : i W + u < X nu}, exactly
+__device__ __forceinline__ uint32_t count_below(unsigned long long X, unsigned long long Wt,
+                                                unsigned long long u, uint32_t nu, float inv_w) {
   const U128 lim = mul_64x64(X, nu);
-  uint32_t lo = 0, hi = nu;  // smallest i in [0, nu] with i W + u >= X nu
-  while (lo < hi) {
-    const uint32_t mid = lo + (hi - lo) / 2;
-    if (lt_128(add_128_64(mul_64x64(mid, Wt), u), lim)) lo = mid + 1; else hi = mid;
+  const float est = __fmul_rn(__fsub_rn(__fmul_rn(u64_to_f32_approx(X), (float)nu), u64_to_f32_approx(u)), inv_w);
+  uint32_t i = est <= 0.0f ? 0u : (est >= (float)nu ? nu : (uint32_t)ceilf(est));
+  int guard = 0;
+  while (i > 0u && !lt_128(add_128_64(mul_64x64(i - 1u, Wt), u), lim) && guard < 64) {
+    --i;
+    ++guard;
   }
-  return lo;
+  while (i < nu && lt_128(add_128_64(mul_64x64(i, Wt), u), lim) && guard < 128) {
+    ++i;
+    ++guard;
+  }
+  if (guard >= 64) {  // the estimate was far off: bisection over [0, nu]
+    uint32_t lo = 0, hi = nu;
+    while (lo < hi) {
+      const uint32_t mid = lo + (hi - lo) / 2;
+      if (lt_128(add_128_64(mul_64x64(mid, Wt), u), lim)) lo = mid + 1; else hi = mid;
+    }
+    i = lo;
+  }
+  return i;
 }
 
 __global__ void __launch_bounds__(RES_BLOCK) k_resample(KParams P, DevBufs B) {
-  __shared__ unsigned long long s_Q[NORM_TILE];
-  __shared__ uint32_t s_perm[NORM_TILE];
+  __shared__ uint32_t s_end[NORM_TILE + NORM_TILE / 8];  // output range end of each source
   __shared__ unsigned long long s_wsum[RES_BLOCK / 32];
-  __shared__ uint32_t s_range[2];
+  __shared__ uint32_t s_lo;
   const uint32_t tile = blockIdx.x, frame = B.ctl->frame;
   const uint32_t base = tile * NORM_TILE, ntot = P.nu + P.nu_b;
   const bool record = (P.flags & 0x4u) != 0u;
-  const unsigned long long Wt = __ldcg(B.cdf_v + (size_t)(P.tiles_norm - 1) * 2 + 1);
-  const unsigned long long E = tile > 0 ? __ldcg(B.cdf_v + (size_t)(tile - 1) * 2 + 1) : 0ull;
+  const unsigned long long Wt = B.ctl->W_total;
+  const unsigned long long E = tile > 0 ? B.cdf_incl[tile - 1] : 0ull;
   if ((P.flags & 0x2u) != 0u || Wt == 0ull) {
     // no resampling: the persistent particles carry over in sorted order
     for (uint32_t i = base + threadIdx.x; i < min(base + NORM_TILE, P.nu); i += RES_BLOCK) {
-      const uint32_t s = B.perm[i];
-      B.Bx[i] = B.Ax[s]; B.By[i] = B.Ay[s]; B.Bvx[i] = B.Avx[s]; B.Bvy[i] = B.Avy[s];
+      B.Bx[i] = B.ox[i]; B.By[i] = B.oy[i]; B.Bvx[i] = B.ovx[i]; B.Bvy[i] = B.ovy[i];
       B.Bw[i] = B.wn[i];
       if (record) B.rsrc[i] = i;
     }
@@ -1003,30 +1110,27 @@ __global__ void __launch_bounds__(RES_BLOCK) k_resample(KParams P, DevBufs B) {
   const unsigned long long r64 = ((unsigned long long)r.a << 32) | r.b;
   const unsigned long long u = __umul64hi(r64, Wt);
   const float wnew = (float)((__ull2double_rn(Wt) * 0x1p-40) / (double)P.nu);
+  const float inv_w = __fdiv_rn(1.0f, u64_to_f32_approx(Wt));
   if (tile == 0 && threadIdx.x == 0) {
     B.ctl->W_total = Wt;
     B.ctl->u_offset = u;
   }
-  // the tile's quantised weights -> inclusive CDF in shared memory
+  // the tile's quantised weights -> inclusive CDF -> end of each source's output range
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t j0 = base + threadIdx.x * NORM_ITEMS;
-  unsigned long long q[NORM_ITEMS];
+  float w[NORM_ITEMS];
+  if (j0 + NORM_ITEMS <= P.nu) {
+    load_runf<NORM_ITEMS>(B.wn, j0, P.nu, w);
+  } else {
+#pragma unroll
+    for (int it = 0; it < NORM_ITEMS; ++it) {
+      const uint32_t j = j0 + it;
+      w[it] = j < P.nu ? __ldg(B.wn + j) : (j < ntot ? __ldg(B.bw + (j - P.nu)) : 0.0f);
+    }
+  }
   unsigned long long loc = 0ull;
 #pragma unroll
-  for (int it = 0; it < NORM_ITEMS; ++it) {
-    const uint32_t j = j0 + it;
-    float w = 0.0f;
-    uint32_t pm = 0xffffffffu;
-    if (j < P.nu) {
-      w = __ldg(B.wn + j);
-      pm = __ldg(B.perm + j);
-    } else if (j < ntot) {
-      w = __ldg(B.bw + (j - P.nu));
-    }
-    q[it] = q40(w);
-    loc += q[it];
-    s_perm[threadIdx.x * NORM_ITEMS + it] = pm;
-  }
+  for (int it = 0; it < NORM_ITEMS; ++it) loc += q40(w[it]);
   unsigned long long inc = loc;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -1035,33 +1139,26 @@ __global__ void __launch_bounds__(RES_BLOCK) k_resample(KParams P, DevBufs B) {
   }
   if (lane == 31) s_wsum[warp] = inc;
   __syncthreads();
-  unsigned long long wbase = 0ull;
-  for (uint32_t w = 0; w < warp; ++w) wbase += s_wsum[w];
-  unsigned long long run = E + wbase + inc - loc;
+  unsigned long long run = E + inc - loc;
+  for (uint32_t k = 0; k < warp; ++k) run += s_wsum[k];
+  if (threadIdx.x == 0) s_lo = count_below(E, Wt, u, P.nu, inv_w);
 #pragma unroll
   for (int it = 0; it < NORM_ITEMS; ++it) {
-    run += q[it];
-    s_Q[threadIdx.x * NORM_ITEMS + it] = run;
+    run += q40(w[it]);
+    s_end[pad8(threadIdx.x * NORM_ITEMS + it)] = count_below(run, Wt, u, P.nu, inv_w);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    s_range[0] = outputs_below(E, Wt, u, P.nu);
-    s_range[1] = outputs_below(s_Q[NORM_TILE - 1], Wt, u, P.nu);
-  }
-  __syncthreads();
-  const uint32_t o_lo = s_range[0], o_hi = s_range[1];
+  const uint32_t o_lo = s_lo, o_hi = s_end[pad8(NORM_TILE - 1)];
   for (uint32_t i = o_lo + threadIdx.x; i < o_hi; i += RES_BLOCK) {
-    const U128 X = add_128_64(mul_64x64(i, Wt), u);
-    uint32_t lo = 0, hi = NORM_TILE - 1;  // smallest m with Q_m nu > X
+    uint32_t lo = 0, hi = NORM_TILE - 1;  // first source whose range ends after i
     while (lo < hi) {
       const uint32_t mid = (lo + hi) >> 1;
-      if (lt_128(X, mul_64x64(s_Q[mid], P.nu))) hi = mid; else lo = mid + 1;
+      if (s_end[pad8(mid)] > i) hi = mid; else lo = mid + 1;
     }
     const uint32_t j = base + lo;
     float x, y, vx, vy;
     if (j < P.nu) {
-      const uint32_t s = s_perm[lo];
-      x = __ldg(B.Ax + s); y = __ldg(B.Ay + s); vx = __ldg(B.Avx + s); vy = __ldg(B.Avy + s);
+      x = __ldg(B.ox + j); y = __ldg(B.oy + j); vx = __ldg(B.ovx + j); vy = __ldg(B.ovy + j);
     } else {
       const uint32_t b = P.nu_b ? min(j - P.nu, P.nu_b - 1u) : 0u;
       x = __ldg(B.bx + b); y = __ldg(B.by + b); vx = __ldg(B.bvx + b); vy = __ldg(B.bvy + b);

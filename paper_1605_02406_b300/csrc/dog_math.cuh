@@ -129,19 +129,53 @@ __device__ __forceinline__ void gauss2(uint32_t ra, uint32_t rb, float &n0, floa
 // round-to-nearest.  Moment terms (products of a cell-normalised weight with velocities):
 // two's-complement 64-bit, scale 2^40, truncation toward 0, saturated at +-2^62.
 // ------------------------------------------------------------------------------------
+// |t| * 2^40 truncated toward zero, from the float's bits with integer shifts only (the
+// hardware float -> 64-bit integer conversion runs on the FP64 pipe, 1/64 of the FP32 rate
+// on this GPU); saturates at 2^62.  Equal to the truncating conversion of t * 2^40.
+__device__ __forceinline__ unsigned long long fx40_mag(uint32_t bits) {
+  const int ex = (int)((bits >> 23) & 0xffu);
+  if (ex == 0) return 0ull;  // zero or subnormal: |t| 2^40 < 1
+  const unsigned long long m = (unsigned long long)((bits & 0x7fffffu) | 0x800000u);
+  const int sh = ex - 110;   // |t| 2^40 = m 2^(ex - 150 + 40)
+  if (sh >= 39) return 1ull << 62;
+  if (sh >= 0) return m << sh;
+  if (sh <= -24) return 0ull;
+  return m >> (-sh);
+}
 __device__ __forceinline__ unsigned long long q40(float w) {
-  return (w > 0.0f) ? __float2ull_rz(__fmul_rn(w, 0x1p40f)) : 0ull;
+  return (w > 0.0f) ? fx40_mag(__float_as_uint(w)) : 0ull;
+}
+// u64 -> float, round to nearest even, with integer operations only (equal to the hardware
+// conversion, which runs on the FP64 pipe)
+__device__ __forceinline__ float u64_to_f32_rn(unsigned long long x) {
+  if (x < (1ull << 24)) return (float)(uint32_t)x;  // exact
+  const int shift = 40 - __clzll(x);                  // bits beyond the 24 kept, >= 1
+  unsigned long long m = x >> shift;                  // 24 bits, leading bit at 23
+  const unsigned long long rem = x & ((1ull << shift) - 1ull), half = 1ull << (shift - 1);
+  int e = shift;
+  if (rem > half || (rem == half && (m & 1ull))) {
+    ++m;
+    if (m == (1ull << 24)) {
+      m >>= 1;
+      ++e;
+    }
+  }
+  return __uint_as_float(((uint32_t)(e + 150) << 23) | ((uint32_t)m & 0x7fffffu));
 }
 __device__ __forceinline__ float fx40_to_f(unsigned long long s) {
-  return __fmul_rn(__ull2float_rn(s), 0x1p-40f);
+  return __fmul_rn(u64_to_f32_rn(s), 0x1p-40f);
 }
 __device__ __forceinline__ unsigned long long q40s(float t) {
-  float v = __fmul_rn(t, 0x1p40f);
-  v = fminf(fmaxf(v, -0x1p62f), 0x1p62f);
-  return (unsigned long long)__float2ll_rz(v);
+  const uint32_t b = __float_as_uint(t);
+  const unsigned long long mag = fx40_mag(b);
+  return (b >> 31) ? 0ull - mag : mag;
 }
-__device__ __forceinline__ double fx40s_to_d(unsigned long long s) {
-  return __ll2double_rn((long long)s) * 0x1p-40;
+// signed fixed point (two's complement, scale 2^40) -> float with 32-bit operations: the
+// two halves are converted separately (at most one extra rounding)
+__device__ __forceinline__ float fx40s_to_f(unsigned long long s) {
+  const int hi = (int)(uint32_t)(s >> 32);
+  const uint32_t lo = (uint32_t)s;
+  return __fmul_rn(__fadd_rn(__fmul_rn((float)hi, 0x1p32f), (float)lo), 0x1p-40f);
 }
 
 // ------------------------------------------------------------------------------------
@@ -165,7 +199,7 @@ __device__ __forceinline__ bool lt_128(U128 a, U128 b) {
 // then bisection with exact 128-bit comparisons
 __device__ __forceinline__ uint32_t floor_muldiv(uint32_t a, unsigned long long b, unsigned long long d) {
   const U128 ab = mul_64x64(a, b);
-  const float est = __fmul_rn((float)a, __fdiv_rn(__ull2float_rn(b), __ull2float_rn(d)));
+  const float est = __fmul_rn((float)a, __fdiv_rn(u64_to_f32_rn(b), u64_to_f32_rn(d)));
   const uint32_t q = est >= (float)a ? a : (uint32_t)est;
   uint32_t lo = q > 16u ? q - 16u : 0u;
   uint32_t hi = (a - q) > 16u ? q + 16u : a;
