@@ -17,7 +17,7 @@ using namespace dog;
 
 namespace {
 
-constexpr int MAX_KERNELS = 12;
+constexpr int MAX_KERNELS = 13;
 constexpr int PROFILE_RING = 1024;
 
 struct Derived {
@@ -69,8 +69,9 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
   const size_t nu = p.num_particles, nb = p.num_birth, C = d.C;
   const bool record = (p.flags & DOG_RECORD) != 0;
   B->ctl = (DevCtl *)take(sizeof(DevCtl));
-  float **pf[] = {&B->Bx, &B->By, &B->Bvx, &B->Bvy, &B->Bw, &B->Ax, &B->Ay, &B->Avx, &B->Avy, &B->Aw,
-                  &B->ox, &B->oy, &B->ovx, &B->ovy, &B->ow, &B->wn};
+  float4 **ps[] = {&B->Bs, &B->As, &B->Os};
+  for (auto q : ps) *q = (float4 *)take(16 * nu);
+  float **pf[] = {&B->Bw, &B->Aw, &B->Ow, &B->wn};
   for (auto q : pf) *q = (float *)take(4 * nu);
   uint32_t **pu[] = {&B->key_pred, &B->key_sorted, &B->perm};
   for (auto q : pu) *q = (uint32_t *)take(4 * nu);
@@ -84,8 +85,8 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
     B->val_t1 = (uint32_t *)take(4 * nu);
   }
   B->rsrc = record ? (uint32_t *)take(4 * nu) : nullptr;
-  float **pb[] = {&B->bx, &B->by, &B->bvx, &B->bvy, &B->bw};
-  for (auto q : pb) *q = (float *)take(4 * (nb ? nb : 1));
+  B->bs = (float4 *)take(16 * (nb ? nb : 1));
+  B->bw = (float *)take(4 * (nb ? nb : 1));
   B->bcell = record ? (uint32_t *)take(4 * (nb ? nb : 1)) : nullptr;
   B->bassoc = record ? (uint32_t *)take(4 * (nb ? nb : 1)) : nullptr;
   float **pc[] = {&B->mF, &B->zO, &B->zF, &B->pA, &B->zv, &B->sgv, &B->mO, &B->rho_p, &B->rho_b,
@@ -100,6 +101,12 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
   const size_t CL = (size_t)d.tiles_cell * CELL_TILE;  // per-tile lists of birth cells
   B->bl_cell = (uint32_t *)take(4 * CL);
   B->bl_R = (unsigned long long *)take(8 * CL);
+  B->bl_first = (uint32_t *)take(4 * CL);
+  B->bl_n = (uint32_t *)take(4 * CL);
+  B->bl_nA = (uint32_t *)take(4 * CL);
+  B->bl_wA = (float *)take(4 * CL);
+  B->bl_wUA = (float *)take(4 * CL);
+  B->tile_first = (uint32_t *)take(4 * ((size_t)d.tiles_cell + 1));
   B->hist = (uint32_t *)take(4 * 2048 * (size_t)d.passes);
   B->lb_sort = (uint32_t *)take(4 * (size_t)d.passes * d.tiles_sort * d.radix);
   B->S_piece = (unsigned long long *)take(8 * C);
@@ -116,8 +123,8 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
 }
 
 const char *KNAMES[MAX_KERNELS] = {"k_tick", "k_predict", "k_sort_pass0", "k_sort_pass1", "k_sort_pass2",
-                                   "k_segsum", "k_cell", "k_scan_births", "k_birth", "k_normalise",
-                                   "k_scan_cdf", "k_resample"};
+                                   "k_segsum", "k_cell", "k_scan_births", "k_birth_prep", "k_birth",
+                                   "k_normalise", "k_scan_cdf", "k_resample"};
 
 }  // namespace
 
@@ -200,6 +207,9 @@ int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
   k_scan_tiles<<<1, SCAN_BLOCK, 0, st>>>(B.tile_q, B.tile_n, K.tiles_cell, B.tile_qin, B.tile_nin,
                                           &B.ctl->R_total, &B.ctl->n_birth_cells);
   ++k; mark();
+  if (radar) k_birth_prep<true><<<K.tiles_cell, CELL_BLOCK, 0, st>>>(K, B);
+  else k_birth_prep<false><<<K.tiles_cell, CELL_BLOCK, 0, st>>>(K, B);
+  ++k; mark();
   if (radar) k_birth<true><<<f->birth_grid, BIRTH_BLOCK, 0, st>>>(K, B);
   else k_birth<false><<<f->birth_grid, BIRTH_BLOCK, 0, st>>>(K, B);
   ++k; mark();
@@ -240,6 +250,32 @@ int reset_epochs(dog_filter *f) {
   DOG_CUDA(cudaMemsetAsync(B.A_piece, 0, 8 * (size_t)d.C, f->st));
   DOG_CUDA(cudaMemsetAsync(B.Mx, 0, 8 * 5 * (size_t)d.C, f->st));
   DOG_CUDA(cudaMemsetAsync(B.Mcnt, 0, 4 * (size_t)d.C, f->st));
+  return DOG_OK;
+}
+
+// Records (x, y, vx, vy) <-> four plain float arrays, staged through the sorted-copy buffer
+// Os (16 bytes per particle, idle between steps).  Records of newborn slots use the same
+// buffer when it is large enough, else strided copies.
+int unpack_records(dog_filter *f, const float4 *rec, size_t n, float *const dst[4], cudaMemcpyKind kd) {
+  if (n == 0) return DOG_OK;
+  if (n <= f->p.num_particles) {
+    float *scr = reinterpret_cast<float *>(f->B.Os);
+    k_unpack<<<1024, 256, 0, f->st>>>(rec, (uint32_t)n, scr);
+    DOG_CUDA(cudaGetLastError());
+    for (int k = 0; k < 4; ++k)
+      if (dst[k]) DOG_CUDA(cudaMemcpyAsync(dst[k], scr + k * n, 4 * n, kd, f->st));
+  } else {
+    for (int k = 0; k < 4; ++k)
+      if (dst[k])
+        DOG_CUDA(cudaMemcpy2DAsync(dst[k], 4, reinterpret_cast<const float *>(rec) + k, 16, 4, n, kd, f->st));
+  }
+  return DOG_OK;
+}
+int pack_records(dog_filter *f, float4 *rec, size_t n, const float *const src[4], cudaMemcpyKind kd) {
+  float *scr = reinterpret_cast<float *>(f->B.Os);
+  for (int k = 0; k < 4; ++k) DOG_CUDA(cudaMemcpyAsync(scr + k * n, src[k], 4 * n, kd, f->st));
+  k_pack<<<1024, 256, 0, f->st>>>(scr, (uint32_t)n, rec);
+  DOG_CUDA(cudaGetLastError());
   return DOG_OK;
 }
 
@@ -320,7 +356,7 @@ int dog_create(const dog_params *params, void *d_workspace, size_t workspace_byt
   K.tiles_seg = d.tiles_seg;
   K.tiles_cell = d.tiles_cell;
   K.tiles_norm = d.tiles_norm;
-  f->nk = 9 + d.passes;
+  f->nk = 10 + d.passes;
   f->profile = (params->flags & DOG_PROFILE) != 0;
   f->use_graph = !(params->flags & DOG_NO_GRAPH) && f->st != nullptr && !f->profile;
   int dev = 0, sms = 148;
@@ -458,10 +494,10 @@ int dog_get_state(dog_filter *f, const dog_state *out, int mem_kind, uint32_t *f
   if (mem_kind != DOG_HOST && mem_kind != DOG_DEVICE) return DOG_ERR_INVALID_ARG;
   const size_t n = 4 * (size_t)f->p.num_particles;
   const cudaMemcpyKind kd = kind_to(mem_kind);
-  float *dst[] = {out->x, out->y, out->vx, out->vy, out->w};
-  const float *src[] = {f->B.Bx, f->B.By, f->B.Bvx, f->B.Bvy, f->B.Bw};
-  for (int k = 0; k < 5; ++k)
-    if (dst[k]) DOG_CUDA(cudaMemcpyAsync(dst[k], src[k], n, kd, f->st));
+  float *const dst[4] = {out->x, out->y, out->vx, out->vy};
+  const int rc0 = unpack_records(f, f->B.Bs, f->p.num_particles, dst, kd);
+  if (rc0) return rc0;
+  if (out->w) DOG_CUDA(cudaMemcpyAsync(out->w, f->B.Bw, n, kd, f->st));
   if (out->m_free) DOG_CUDA(cudaMemcpyAsync(out->m_free, f->B.mF, 4 * (size_t)f->d.C, kd, f->st));
   const int rc = read_err(f);
   if (frame) *frame = f->frame;
@@ -474,9 +510,10 @@ int dog_set_state(dog_filter *f, const dog_state *in, int mem_kind, uint32_t fra
   if (mem_kind != DOG_HOST && mem_kind != DOG_DEVICE) return DOG_ERR_INVALID_ARG;
   const size_t n = 4 * (size_t)f->p.num_particles;
   const cudaMemcpyKind kd = kind_from(mem_kind);
-  const float *src[] = {in->x, in->y, in->vx, in->vy, in->w};
-  float *dst[] = {f->B.Bx, f->B.By, f->B.Bvx, f->B.Bvy, f->B.Bw};
-  for (int k = 0; k < 5; ++k) DOG_CUDA(cudaMemcpyAsync(dst[k], src[k], n, kd, f->st));
+  const float *const src[4] = {in->x, in->y, in->vx, in->vy};
+  const int rc0 = pack_records(f, f->B.Bs, f->p.num_particles, src, kd);
+  if (rc0) return rc0;
+  DOG_CUDA(cudaMemcpyAsync(f->B.Bw, in->w, n, kd, f->st));
   DOG_CUDA(cudaMemcpyAsync(f->B.mF, in->m_free, 4 * (size_t)f->d.C, kd, f->st));
   const int rc = reset_epochs(f);
   if (rc) return rc;
@@ -496,11 +533,14 @@ int dog_get_debug(dog_filter *f, int which, void *out, int mem_kind) {
   const void *src = nullptr;
   size_t bytes = 0;
   bool masked = false;
+  const float4 *rec = nullptr;  // component of (x, y, vx, vy) records
+  int comp = 0;
+  size_t nrec = 0;
   switch (which) {
-    case DOG_DBG_PRED_X: src = B.Ax; bytes = 4 * nu; break;
-    case DOG_DBG_PRED_Y: src = B.Ay; bytes = 4 * nu; break;
-    case DOG_DBG_PRED_VX: src = B.Avx; bytes = 4 * nu; break;
-    case DOG_DBG_PRED_VY: src = B.Avy; bytes = 4 * nu; break;
+    case DOG_DBG_PRED_X: rec = B.As; comp = 0; nrec = nu; break;
+    case DOG_DBG_PRED_Y: rec = B.As; comp = 1; nrec = nu; break;
+    case DOG_DBG_PRED_VX: rec = B.As; comp = 2; nrec = nu; break;
+    case DOG_DBG_PRED_VY: rec = B.As; comp = 3; nrec = nu; break;
     case DOG_DBG_PRED_W: src = B.Aw; bytes = 4 * nu; break;
     case DOG_DBG_KEY: src = B.key_pred; bytes = 4 * nu; break;
     case DOG_DBG_PERM: src = B.perm; bytes = 4 * nu; break;
@@ -512,10 +552,10 @@ int dog_get_debug(dog_filter *f, int which, void *out, int mem_kind) {
     case DOG_DBG_MU_A: src = B.muA; bytes = 4 * C; break;
     case DOG_DBG_MU_UA: src = B.muU; bytes = 4 * C; break;
     case DOG_DBG_W_NORM: src = B.wn; bytes = 4 * nu; break;
-    case DOG_DBG_BIRTH_X: src = B.bx; bytes = 4 * nb; break;
-    case DOG_DBG_BIRTH_Y: src = B.by; bytes = 4 * nb; break;
-    case DOG_DBG_BIRTH_VX: src = B.bvx; bytes = 4 * nb; break;
-    case DOG_DBG_BIRTH_VY: src = B.bvy; bytes = 4 * nb; break;
+    case DOG_DBG_BIRTH_X: rec = B.bs; comp = 0; nrec = nb; break;
+    case DOG_DBG_BIRTH_Y: rec = B.bs; comp = 1; nrec = nb; break;
+    case DOG_DBG_BIRTH_VX: rec = B.bs; comp = 2; nrec = nb; break;
+    case DOG_DBG_BIRTH_VY: rec = B.bs; comp = 3; nrec = nb; break;
     case DOG_DBG_BIRTH_W: src = B.bw; bytes = 4 * nb; break;
     case DOG_DBG_BIRTH_CELL: src = B.bcell; bytes = 4 * nb; break;
     case DOG_DBG_BIRTH_ASSOC: src = B.bassoc; bytes = 4 * nb; break;
@@ -531,6 +571,13 @@ int dog_get_debug(dog_filter *f, int which, void *out, int mem_kind) {
     DOG_CUDA(cudaMemcpy(&h, B.ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost));
     const unsigned long long v[4] = {h.frame, h.W_total, h.R_total, h.u_offset};
     DOG_CUDA(cudaMemcpy(out, v, sizeof(v), mem_kind == DOG_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+    return read_err(f);
+  }
+  if (rec) {
+    float *dst[4] = {nullptr, nullptr, nullptr, nullptr};
+    dst[comp] = (float *)out;
+    const int rc = unpack_records(f, rec, nrec, dst, kind_to(mem_kind));
+    if (rc) return rc;
     return read_err(f);
   }
   if (!masked) {
@@ -553,14 +600,14 @@ int dog_profile_read(dog_filter *f, float *ms, const char **names, int max, int 
   if (!f || !ms || max <= 0) return DOG_ERR_INVALID_ARG;
   if (!f->profile) return DOG_ERR_BAD_STATE;
   DOG_CUDA(cudaStreamSynchronize(f->st));
-  // kernel slots in launch order: tick, predict, sort passes, segsum, cell, birth scan, birth,
-  // normalise, CDF scan, resample
+  // kernel slots in launch order: tick, predict, sort passes, segsum, cell, birth scan, birth
+  // prep, birth, normalise, CDF scan, resample
   int slot_kind[MAX_KERNELS];
   int nk = 0;
   slot_kind[nk++] = 0;
   slot_kind[nk++] = 1;
   for (int p = 0; p < f->d.passes; ++p) slot_kind[nk++] = 2 + p;
-  for (int k = 5; k <= 11; ++k) slot_kind[nk++] = k;
+  for (int k = 5; k <= 12; ++k) slot_kind[nk++] = k;
   const int n = nk < max ? nk : max;
   for (int k = 0; k < n; ++k) ms[k] = 0.0f;
   for (int r = 0; r < f->ring_count; ++r) {

@@ -50,16 +50,14 @@ struct KParams {
 
 struct DevBufs {
   DevCtl *ctl;
-  // persistent posterior particles (B) and predicted particles (A)
-  float *Bx, *By, *Bvx, *Bvy, *Bw;
-  float *Ax, *Ay, *Avx, *Avy, *Aw;
+  // particle states are (x, y, vx, vy) records with the weight in a separate array:
+  // posterior (B), predicted (A), predicted in sorted cell order (O), newborn (b)
+  float4 *Bs, *As, *Os, *bs;
+  float *Bw, *Aw, *Ow, *bw;
   uint32_t *key_pred, *key_t0, *val_t0, *key_t1, *val_t1, *key_sorted, *perm;
-  float *ox, *oy, *ovx, *ovy, *ow;  // predicted particles in sorted (cell) order
   float *wn;
   uint32_t *rsrc;  // record only
-  // newborn particles
-  float *bx, *by, *bvx, *bvy, *bw;
-  uint32_t *bcell, *bassoc;  // record only
+  uint32_t *bcell, *bassoc;  // newborn cells and association flags (record only)
   // cells
   float *mF;
   float *zO, *zF, *pA, *zv, *sgv;
@@ -67,8 +65,11 @@ struct DevBufs {
   float *mpred, *muA, *muU, *paeff, *rinv;
   unsigned long long *S, *A;
   uint32_t *tag, *cstart, *cend;
-  uint32_t *bl_cell;
-  unsigned long long *bl_R;
+  uint32_t *bl_cell;               // [tiles_cell][1024] cells with newborn mass, per tile
+  unsigned long long *bl_R;         // [tiles_cell][1024] tile-local inclusive newborn mass
+  uint32_t *bl_first, *bl_n, *bl_nA;  // first slot, slots, associated slots of each entry
+  float *bl_wA, *bl_wUA;              // newborn weights of each entry
+  uint32_t *tile_first;               // [tiles_cell + 1] first slot of each cell tile
   // scratch of the sort and the tile scans
   uint32_t *hist;                  // [passes][2048] digit histograms
   uint32_t *lb_sort;               // [passes][tiles_sort][radix] look-back words

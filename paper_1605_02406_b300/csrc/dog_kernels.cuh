@@ -9,6 +9,7 @@
 //   k_cell        Alg. 3  occupancy prediction, DS update, newborn split, normalisers;
 //                          per-tile lists of cells with newborn mass
 //   k_scan_tiles          prefix of the tiles' newborn masses
+//   k_birth_prep  Alg. 5  slot range, associated share and weights of each birth cell
 //   k_birth       Alg. 5  newborn particles, slots proportional to the newborn mass
 //   k_normalise   Alg. 4/6 normalised persistent weights, velocity moments, tile sums of
 //                          the joint weights
@@ -42,13 +43,28 @@ __global__ void k_init(KParams P, DevBufs B) {
     const U4 r = philox(i, 0u, TAG_INIT, P.seed_lo, P.seed_hi);
     float n0, n1;
     gauss2(r.c, r.d, n0, n1);
-    B.Bx[i] = __fmul_rn(u01_co(r.a), gx);
-    B.By[i] = __fmul_rn(u01_co(r.b), gy);
-    B.Bvx[i] = __fmul_rn(P.sigma_B, n0);
-    B.Bvy[i] = __fmul_rn(P.sigma_B, n1);
+    B.Bs[i] = make_float4(__fmul_rn(u01_co(r.a), gx), __fmul_rn(u01_co(r.b), gy),
+                          __fmul_rn(P.sigma_B, n0), __fmul_rn(P.sigma_B, n1));
     B.Bw[i] = 0.0f;
   }
   for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < P.C; c += stride) B.mF[c] = 0.0f;
+}
+
+// ====================================================================================
+// record <-> plain arrays (state checkpoint and diagnostics; not on the per-frame path)
+// ====================================================================================
+__global__ void k_unpack(const float4 *__restrict__ rec, uint32_t n, float *__restrict__ out /* [4][n] */) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float4 r = rec[i];
+    out[i] = r.x;
+    out[n + i] = r.y;
+    out[2 * (size_t)n + i] = r.z;
+    out[3 * (size_t)n + i] = r.w;
+  }
+}
+__global__ void k_pack(const float *__restrict__ in /* [4][n] */, uint32_t n, float4 *__restrict__ rec) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    rec[i] = make_float4(in[i], in[n + i], in[2 * (size_t)n + i], in[3 * (size_t)n + i]);
 }
 
 // ====================================================================================
@@ -79,8 +95,8 @@ __global__ void k_validate(KParams P, DevBufs B, int radar) {
 constexpr int PRED_BLOCK = 256, PRED_ROUNDS = 4, PRED_TILE = PRED_BLOCK * 4 * PRED_ROUNDS;
 
 __device__ __forceinline__ void predict_one(const KParams &P, uint32_t i, uint32_t frame, float T,
-                                            float &x, float &y, float &vx, float &vy, float &w,
-                                            uint32_t &key) {
+                                            float4 &st, float &w, uint32_t &key) {
+  float &x = st.x, &y = st.y, &vx = st.z, &vy = st.w;
   const U4 r = philox(i, frame, TAG_PREDICT, P.seed_lo, P.seed_hi);
   float n0, n1, n2, n3;
   gauss2(r.a, r.b, n0, n1);
@@ -112,19 +128,16 @@ __global__ void __launch_bounds__(PRED_BLOCK) k_predict(KParams P, DevBufs B) {
     uint32_t key[4];
     bool valid[4];
     if (i0 + 4 <= P.nu) {
-      float4 x = *reinterpret_cast<const float4 *>(B.Bx + i0);
-      float4 y = *reinterpret_cast<const float4 *>(B.By + i0);
-      float4 vx = *reinterpret_cast<const float4 *>(B.Bvx + i0);
-      float4 vy = *reinterpret_cast<const float4 *>(B.Bvy + i0);
+      float4 s0 = B.Bs[i0], s1 = B.Bs[i0 + 1], s2 = B.Bs[i0 + 2], s3 = B.Bs[i0 + 3];
       float4 w = *reinterpret_cast<const float4 *>(B.Bw + i0);
-      predict_one(P, i0 + 0, frame, T, x.x, y.x, vx.x, vy.x, w.x, key[0]);
-      predict_one(P, i0 + 1, frame, T, x.y, y.y, vx.y, vy.y, w.y, key[1]);
-      predict_one(P, i0 + 2, frame, T, x.z, y.z, vx.z, vy.z, w.z, key[2]);
-      predict_one(P, i0 + 3, frame, T, x.w, y.w, vx.w, vy.w, w.w, key[3]);
-      *reinterpret_cast<float4 *>(B.Ax + i0) = x;
-      *reinterpret_cast<float4 *>(B.Ay + i0) = y;
-      *reinterpret_cast<float4 *>(B.Avx + i0) = vx;
-      *reinterpret_cast<float4 *>(B.Avy + i0) = vy;
+      predict_one(P, i0 + 0, frame, T, s0, w.x, key[0]);
+      predict_one(P, i0 + 1, frame, T, s1, w.y, key[1]);
+      predict_one(P, i0 + 2, frame, T, s2, w.z, key[2]);
+      predict_one(P, i0 + 3, frame, T, s3, w.w, key[3]);
+      B.As[i0] = s0;
+      B.As[i0 + 1] = s1;
+      B.As[i0 + 2] = s2;
+      B.As[i0 + 3] = s3;
       *reinterpret_cast<float4 *>(B.Aw + i0) = w;
       *reinterpret_cast<uint4 *>(B.key_pred + i0) = make_uint4(key[0], key[1], key[2], key[3]);
       valid[0] = valid[1] = valid[2] = valid[3] = true;
@@ -135,9 +148,11 @@ __global__ void __launch_bounds__(PRED_BLOCK) k_predict(KParams P, DevBufs B) {
         valid[k] = i < P.nu;
         key[k] = 0u;
         if (valid[k]) {
-          float x = B.Bx[i], y = B.By[i], vx = B.Bvx[i], vy = B.Bvy[i], w = B.Bw[i];
-          predict_one(P, i, frame, T, x, y, vx, vy, w, key[k]);
-          B.Ax[i] = x; B.Ay[i] = y; B.Avx[i] = vx; B.Avy[i] = vy; B.Aw[i] = w;
+          float4 s = B.Bs[i];
+          float w = B.Bw[i];
+          predict_one(P, i, frame, T, s, w, key[k]);
+          B.As[i] = s;
+          B.Aw[i] = w;
           B.key_pred[i] = key[k];
         }
       }
@@ -361,6 +376,9 @@ __global__ void __launch_bounds__(SORT_BLOCK, 2)
 // ====================================================================================
 constexpr int SEG_BLOCK = 256, SEG_ITEMS = 8, SEG_TILE = SEG_BLOCK * SEG_ITEMS;
 
+// shared-memory index padded by one element per 8 (blocked accesses hit distinct banks)
+__device__ __forceinline__ uint32_t pad8(uint32_t m) { return m + (m >> 3); }
+
 template <int N, typename V = unsigned long long>
 struct Seg {
   uint32_t f;  // a segment head lies in the covered range
@@ -476,21 +494,49 @@ __device__ __forceinline__ void store_run(float *p, uint32_t j0, uint32_t n, con
 // k_segsum: cell ranges (Alg. 2) and S_c = sum of q40(w) (Eq. DS_particle_sum_pred as an
 // exact fixed-point sum), plus A_c = sum of q40(g w) where the cell has a radar likelihood.
 // tag[c] = 2 frame (finished here) or 2 frame + 1 (pieces in the accumulators).  The
-// predicted state is gathered through the sort permutation into sorted order (ox..ow).
+// predicted state is gathered through the sort permutation into sorted order (Os, Ow) with
+// consecutive lanes on consecutive sorted positions (neighbouring particles mostly come
+// from neighbouring slots), and the fixed-point weights reach the blocked segmented scan
+// through shared memory.
 template <bool RADAR>
 __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
   constexpr int N = RADAR ? 2 : 1;
   __shared__ Seg<N> s_w[SEG_BLOCK / 32 + 1];
+  __shared__ unsigned long long s_q[N][SEG_TILE + SEG_TILE / 8];  // padded: m -> m + m/8
   const uint32_t tile = blockIdx.x, frame = B.ctl->frame;
-  const uint32_t j0 = tile * SEG_TILE + threadIdx.x * SEG_ITEMS;
-  const uint32_t last_valid = min(tile * SEG_TILE + SEG_TILE, P.nu) - 1u;
-  uint32_t key[SEG_ITEMS], idx[SEG_ITEMS];
+  const uint32_t base = tile * SEG_TILE;
+  const uint32_t last_valid = min(base + SEG_TILE, P.nu) - 1u;
+  // gather phase, warp-striped: position base + it*256 + threadIdx.x
+#pragma unroll
+  for (int it = 0; it < SEG_ITEMS; ++it) {
+    const uint32_t m = it * SEG_BLOCK + threadIdx.x;
+    const uint32_t j = base + m;
+    unsigned long long q = 0ull, gq = 0ull;
+    if (j < P.nu) {
+      const uint32_t i = __ldg(B.perm + j);
+      const float4 st = __ldg(B.As + i);
+      const float w = __ldg(B.Aw + i);
+      const float x = st.x, y = st.y, vx = st.z, vy = st.w;
+      B.Os[j] = st;
+      B.Ow[j] = w;
+      q = q40(w);
+      if constexpr (RADAR) {
+        const uint32_t c = __ldg(B.key_sorted + j);
+        if (__ldg(B.pA + c) > 0.0f)
+          gq = q40(__fmul_rn(radar_lik(P, x, y, vx, vy, __ldg(B.zv + c), __ldg(B.sgv + c)), w));
+      }
+    }
+    s_q[0][pad8(m)] = q;
+    if constexpr (RADAR) s_q[N - 1][pad8(m)] = gq;
+  }
+  __syncthreads();
+  // scan phase, blocked: a thread owns ITEMS consecutive positions
+  const uint32_t j0 = base + threadIdx.x * SEG_ITEMS;
+  uint32_t key[SEG_ITEMS];
   load_run<SEG_ITEMS>(B.key_sorted, j0, P.nu, key, 0xffffffffu);
-  load_run<SEG_ITEMS>(B.perm, j0, P.nu, idx, 0u);
   const uint32_t kprev = (j0 > 0 && j0 <= P.nu) ? __ldg(B.key_sorted + j0 - 1) : 0xfffffffeu;
   const uint32_t knext = (j0 + SEG_ITEMS < P.nu) ? __ldg(B.key_sorted + j0 + SEG_ITEMS) : 0xfffffffeu;
   unsigned long long v[SEG_ITEMS][N];
-  float sx[SEG_ITEMS], sy[SEG_ITEMS], svx[SEG_ITEMS], svy[SEG_ITEMS], sw[SEG_ITEMS];
   uint32_t head = 0, tail = 0;
   Seg<N> agg;
   agg.f = 0;
@@ -507,34 +553,13 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
     head |= (uint32_t)h << it;
     tail |= (uint32_t)t << it;
 #pragma unroll
-    for (int k = 0; k < N; ++k) v[it][k] = 0ull;
-    if (ok) {
-      const uint32_t i = idx[it];
-      sx[it] = __ldg(B.Ax + i);
-      sy[it] = __ldg(B.Ay + i);
-      svx[it] = __ldg(B.Avx + i);
-      svy[it] = __ldg(B.Avy + i);
-      sw[it] = __ldg(B.Aw + i);
-      v[it][0] = q40(sw[it]);
-      if constexpr (RADAR) {
-        const uint32_t c = key[it];
-        if (__ldg(B.pA + c) > 0.0f) {
-          const float g = radar_lik(P, sx[it], sy[it], svx[it], svy[it], __ldg(B.zv + c), __ldg(B.sgv + c));
-          v[it][N - 1] = q40(__fmul_rn(g, sw[it]));
-        }
-      }
-    }
+    for (int k = 0; k < N; ++k) v[it][k] = s_q[k][pad8(threadIdx.x * SEG_ITEMS + it)];
     Seg<N> e;
     e.f = h;
 #pragma unroll
     for (int k = 0; k < N; ++k) e.v[k] = v[it][k];
     agg = seg_combine(agg, e);
   }
-  store_run<SEG_ITEMS>(B.ox, j0, P.nu, sx);
-  store_run<SEG_ITEMS>(B.oy, j0, P.nu, sy);
-  store_run<SEG_ITEMS>(B.ovx, j0, P.nu, svx);
-  store_run<SEG_ITEMS>(B.ovy, j0, P.nu, svy);
-  store_run<SEG_ITEMS>(B.ow, j0, P.nu, sw);
   const Seg<N> ex = block_seg_excl(agg, s_w);
   unsigned long long run[N];
 #pragma unroll
@@ -782,9 +807,8 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
 // k_birth (Alg. 5): cell c owns the newborn slots [floor(nu_b R_{c-1}/R), floor(nu_b R_c/R))
 // of the fixed-point scan R of the newborn masses; nu_A = round(n p_A) of them form the
 // associated set (Eq. assoc_relation, assoc_sum), with weights Eq. weights_associated /
-// weights_unassociated.  One thread per slot finds its cell by bisection, first over the
-// cell tiles' inclusive totals, then in the tile's list (exact 128-bit comparisons of
-// nu_b R_incl against (slot + 1) R).
+// weights_unassociated.  The exact slot arithmetic is done once per birth cell
+// (k_birth_prep); each slot then only searches first-slot tables.
 // ====================================================================================
 constexpr int BIRTH_BLOCK = 256;
 
@@ -814,10 +838,7 @@ __device__ __forceinline__ void birth_init(const KParams &P, const DevBufs &B, u
     vx = __fmul_rn(P.sigma_B, n0);
     vy = __fmul_rn(P.sigma_B, n1);
   }
-  B.bx[slot] = x;
-  B.by[slot] = y;
-  B.bvx[slot] = vx;
-  B.bvy[slot] = vy;
+  B.bs[slot] = make_float4(x, y, vx, vy);
   B.bw[slot] = w;
   if (record) {
     B.bcell[slot] = c;
@@ -825,6 +846,50 @@ __device__ __forceinline__ void birth_init(const KParams &P, const DevBufs &B, u
   }
 }
 
+// k_birth_prep: per birth cell (list entry) its first slot floor(nu_b R_{c-1} / R), slot
+// count, associated count nu_A = round(n p_A) and the two newborn weights; per cell tile
+// its first slot.  One block per cell tile.
+template <bool RADAR>
+__global__ void __launch_bounds__(CELL_BLOCK) k_birth_prep(KParams P, DevBufs B) {
+  const unsigned long long R = B.ctl->R_total;
+  const uint32_t T = blockIdx.x;
+  const unsigned long long Tex = T > 0u ? B.tile_qin[T - 1u] : 0ull;
+  if (threadIdx.x == 0) {
+    B.tile_first[T] = R ? floor_muldiv(P.nu_b, Tex, R) : 0u;
+    if (T == P.tiles_cell - 1u) B.tile_first[T + 1u] = P.nu_b;
+  }
+  if (R == 0ull) return;
+  const uint32_t cnt = B.tile_n[T];
+  for (uint32_t e = threadIdx.x; e < cnt; e += CELL_BLOCK) {
+    const size_t pos = (size_t)T * CELL_TILE + e;
+    const uint32_t c = B.bl_cell[pos];
+    const unsigned long long Rin = Tex + B.bl_R[pos];
+    const unsigned long long Rex = Tex + (e > 0u ? B.bl_R[pos - 1] : 0ull);
+    const uint32_t first = floor_muldiv(P.nu_b, Rex, R);
+    const uint32_t last = floor_muldiv(P.nu_b, Rin, R);
+    const uint32_t n = last > first ? last - first : 0u;
+    const float rb = B.rho_b[c];
+    const float pA = RADAR ? B.pA[c] : 0.0f;
+    uint32_t nA = (uint32_t)__fadd_rn(__fmul_rn((float)n, pA), 0.5f);
+    if (nA > n) nA = n;
+    const uint32_t nUA = n - nA;
+    float wA = 0.0f, wUA = 0.0f;
+    if (nA > 0u && nUA > 0u) {
+      wA = __fdiv_rn(__fmul_rn(pA, rb), (float)nA);
+      wUA = __fdiv_rn(__fmul_rn(__fsub_rn(1.0f, pA), rb), (float)nUA);
+    } else if (n > 0u) {
+      wA = wUA = __fdiv_rn(rb, (float)n);
+    }
+    B.bl_first[pos] = first;
+    B.bl_n[pos] = n;
+    B.bl_nA[pos] = nA;
+    B.bl_wA[pos] = wA;
+    B.bl_wUA[pos] = wUA;
+  }
+}
+
+// k_birth: one thread per newborn slot; its cell tile and then its cell are found by
+// bisection over the first slots prepared by k_birth_prep.
 template <bool RADAR>
 __global__ void __launch_bounds__(BIRTH_BLOCK) k_birth(KParams P, DevBufs B) {
   const uint32_t frame = B.ctl->frame;
@@ -838,49 +903,30 @@ __global__ void __launch_bounds__(BIRTH_BLOCK) k_birth(KParams P, DevBufs B) {
     return;
   }
   for (uint32_t s = blockIdx.x * BIRTH_BLOCK + threadIdx.x; s < P.nu_b; s += stride) {
-    const U128 target = mul_64x64((unsigned long long)s + 1ull, R);
-    // the cell tile: first T with nu_b * Qincl_T >= (s + 1) R
+    // the cell tile: first T whose slots end after s (tile_first[T + 1] > s)
     uint32_t lo = 0, hi = P.tiles_cell - 1u;
     while (lo < hi) {
       const uint32_t mid = (lo + hi) >> 1;
-      if (lt_128(mul_64x64(P.nu_b, __ldg(B.tile_qin + mid)), target)) lo = mid + 1u; else hi = mid;
+      if (__ldg(B.tile_first + mid + 1u) > s) hi = mid; else lo = mid + 1u;
     }
-    const uint32_t T = lo;
-    const unsigned long long Tex = T > 0u ? __ldg(B.tile_qin + T - 1u) : 0ull;
-    const uint32_t cnt = __ldg(B.tile_n + T);
-    const uint32_t *cells = B.bl_cell + (size_t)T * CELL_TILE;
-    const unsigned long long *Rl = B.bl_R + (size_t)T * CELL_TILE;
-    // the cell within the tile's list
-    lo = 0;
-    hi = cnt > 0u ? cnt - 1u : 0u;
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (lt_128(mul_64x64(P.nu_b, Tex + __ldg(Rl + mid)), target)) lo = mid + 1u; else hi = mid;
+    const size_t tb = (size_t)lo * CELL_TILE;
+    // the cell: the last entry whose first slot is <= s
+    uint32_t a = 0, b = __ldg(B.tile_n + lo);
+    b = b > 0u ? b - 1u : 0u;
+    while (a < b) {
+      const uint32_t mid = (a + b + 1u) >> 1;
+      if (__ldg(B.bl_first + tb + mid) <= s) a = mid; else b = mid - 1u;
     }
-    const uint32_t c = __ldg(cells + lo);
-    const unsigned long long Rin = Tex + __ldg(Rl + lo);
-    const unsigned long long Rex = Tex + (lo > 0u ? __ldg(Rl + lo - 1u) : 0ull);
-    const uint32_t first = floor_muldiv(P.nu_b, Rex, R);
-    const uint32_t last = floor_muldiv(P.nu_b, Rin, R);
-    const uint32_t n = last > first ? last - first : 1u;  // n = 0 only on corrupted input
-    const uint32_t t = s >= first ? s - first : 0u;
-    const float rb = __ldg(B.rho_b + c);
-    float pA = 0.0f, zv = 0.0f, sg = 1.0f;
+    const size_t pos = tb + a;
+    const uint32_t c = __ldg(B.bl_cell + pos);
+    const uint32_t t = s - __ldg(B.bl_first + pos);
+    const bool assoc = t < __ldg(B.bl_nA + pos);
+    const float w = assoc ? __ldg(B.bl_wA + pos) : __ldg(B.bl_wUA + pos);
+    float zv = 0.0f, sg = 1.0f;
     if constexpr (RADAR) {
-      pA = __ldg(B.pA + c);
       zv = __ldg(B.zv + c);
       sg = __ldg(B.sgv + c);
     }
-    uint32_t nA = (uint32_t)__fadd_rn(__fmul_rn((float)n, pA), 0.5f);
-    if (nA > n) nA = n;
-    const uint32_t nUA = n - nA;
-    const bool assoc = t < nA;
-    float w;
-    if (nA > 0u && nUA > 0u)
-      w = assoc ? __fdiv_rn(__fmul_rn(pA, rb), (float)nA)
-                : __fdiv_rn(__fmul_rn(__fsub_rn(1.0f, pA), rb), (float)nUA);
-    else
-      w = __fdiv_rn(rb, (float)n);
     birth_init(P, B, s, c, assoc, w, zv, sg, frame, record);
   }
 }
@@ -938,9 +984,14 @@ __global__ void __launch_bounds__(NORM_BLOCK) k_normalise(KParams P, DevBufs B) 
   if (has_pers) {
     float ws[NORM_ITEMS];
     load_run<NORM_ITEMS>(B.key_sorted, j0, P.nu, key, 0xffffffffu);
-    load_runf<NORM_ITEMS>(B.ow, j0, P.nu, ws);
-    load_runf<NORM_ITEMS>(B.ovx, j0, P.nu, mvx);
-    load_runf<NORM_ITEMS>(B.ovy, j0, P.nu, mvy);
+    load_runf<NORM_ITEMS>(B.Ow, j0, P.nu, ws);
+    float4 st[NORM_ITEMS];
+#pragma unroll
+    for (int it = 0; it < NORM_ITEMS; ++it) {
+      st[it] = j0 + it < P.nu ? __ldg(B.Os + j0 + it) : make_float4(0.f, 0.f, 0.f, 0.f);
+      mvx[it] = st[it].z;
+      mvy[it] = st[it].w;
+    }
     const uint32_t kprev = (j0 > 0 && j0 <= P.nu) ? __ldg(B.key_sorted + j0 - 1) : 0xfffffffeu;
     const uint32_t knext = (j0 + NORM_ITEMS < P.nu) ? __ldg(B.key_sorted + j0 + NORM_ITEMS) : 0xfffffffeu;
     float wn_out[NORM_ITEMS];
@@ -963,7 +1014,7 @@ __global__ void __launch_bounds__(NORM_BLOCK) k_normalise(KParams P, DevBufs B) 
         float wn;
         const float pa = RADAR ? __ldg(B.paeff + c) : 0.0f;
         if (RADAR && pa > 0.0f) {
-          const float g = radar_lik(P, __ldg(B.ox + j), __ldg(B.oy + j), mvx[it], mvy[it],
+          const float g = radar_lik(P, st[it].x, st[it].y, mvx[it], mvy[it],
                                     __ldg(B.zv + c), __ldg(B.sgv + c));
           const float a = __fmul_rn(__fmul_rn(__fmul_rn(pa, __ldg(B.muA + c)), g), w);
           const float b = __fmul_rn(__fmul_rn(__fsub_rn(1.0f, pa), muU), w);
@@ -1052,7 +1103,6 @@ __global__ void __launch_bounds__(NORM_BLOCK) k_normalise(KParams P, DevBufs B) 
 // ====================================================================================
 constexpr int RES_BLOCK = 256;
 
-__device__ __forceinline__ uint32_t pad8(uint32_t m) { return m + (m >> 3); }
 
 __device__ __forceinline__ float u64_to_f32_approx(unsigned long long x) {
   return __fadd_rn(__fmul_rn((float)(uint32_t)(x >> 32), 0x1p32f), (float)(uint32_t)x);
@@ -1096,7 +1146,7 @@ __global__ void __launch_bounds__(RES_BLOCK) k_resample(KParams P, DevBufs B) {
   if ((P.flags & 0x2u) != 0u || Wt == 0ull) {
     // no resampling: the persistent particles carry over in sorted order
     for (uint32_t i = base + threadIdx.x; i < min(base + NORM_TILE, P.nu); i += RES_BLOCK) {
-      B.Bx[i] = B.ox[i]; B.By[i] = B.oy[i]; B.Bvx[i] = B.ovx[i]; B.Bvy[i] = B.ovy[i];
+      B.Bs[i] = B.Os[i];
       B.Bw[i] = B.wn[i];
       if (record) B.rsrc[i] = i;
     }
@@ -1156,14 +1206,15 @@ __global__ void __launch_bounds__(RES_BLOCK) k_resample(KParams P, DevBufs B) {
       if (s_end[pad8(mid)] > i) hi = mid; else lo = mid + 1;
     }
     const uint32_t j = base + lo;
-    float x, y, vx, vy;
+    float4 st;
     if (j < P.nu) {
-      x = __ldg(B.ox + j); y = __ldg(B.oy + j); vx = __ldg(B.ovx + j); vy = __ldg(B.ovy + j);
+      st = __ldg(B.Os + j);
     } else {
       const uint32_t b = P.nu_b ? min(j - P.nu, P.nu_b - 1u) : 0u;
-      x = __ldg(B.bx + b); y = __ldg(B.by + b); vx = __ldg(B.bvx + b); vy = __ldg(B.bvy + b);
+      st = __ldg(B.bs + b);
     }
-    B.Bx[i] = x; B.By[i] = y; B.Bvx[i] = vx; B.Bvy[i] = vy; B.Bw[i] = wnew;
+    B.Bs[i] = st;
+    B.Bw[i] = wnew;
     if (record) B.rsrc[i] = j;
   }
 }
