@@ -56,7 +56,8 @@ typedef enum dog_status {
 #define DOG_DEVICE 1
 
 /* Filter parameters (Table I of the paper gives typical values).  All POD; validated by
- * dog_workspace_bytes and dog_create.  Limits: 1 <= width, height; C = width*height <= 2^24;
+ * dog_workspace_bytes and dog_create.  Limits: 1 <= width, height; C = width*height < 2^24 (so
+ * the 2^-40 fixed-point total of all cell masses, at most C, stays below 2^64);
  * 1 <= num_particles < 2^25; num_birth < 2^25. */
 typedef struct dog_params {
   int32_t width, height;   /* grid cells                                             */

@@ -27,8 +27,8 @@
  *   (default)     FP64: the same steps in binary64 with libm transcendentals.
  * Both modes keep the 64-bit fixed-point weight sums that the method fixes (scale 2^40).
  *
- * Readings where the paper is silent are listed in DESIGN.md; each is marked "reading"
- * at the place it is applied below.
+ * Where the paper is silent or ambiguous, the reading taken is marked "reading" at the
+ * place it is applied below.
  */
 #include <math.h>
 #include <stdint.h>

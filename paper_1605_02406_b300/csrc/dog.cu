@@ -40,7 +40,8 @@ int check_params(const dog_params *p, Derived *d) {
     if (!(v >= 0.0f) || !std::isfinite(v)) return DOG_ERR_INVALID_ARG;
   if (!std::isfinite(p->sensor_x) || !std::isfinite(p->sensor_y)) return DOG_ERR_INVALID_ARG;
   const unsigned long long C = (unsigned long long)p->width * (unsigned long long)p->height;
-  if (C > (1ull << 24)) return DOG_ERR_UNSUPPORTED;
+  // C < 2^24 keeps the joint weight total (<= C cell masses of at most 1, scale 2^40) < 2^64
+  if (C >= (1ull << 24)) return DOG_ERR_UNSUPPORTED;
   if (p->num_particles >= (1u << 25) || p->num_birth >= (1u << 25)) return DOG_ERR_UNSUPPORTED;
   d->C = (uint32_t)C;
   int bits = 1;

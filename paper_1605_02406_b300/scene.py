@@ -7,8 +7,8 @@ meas_cell_array, Sect. VII) and, for single-frame tests, a posterior particle st
 
 The paper evaluates on recorded laser/radar logs that are not available; the workloads
 here stand in for them with the shapes of the paper's setting (Table I: 0.1 m cells,
-millions of particles, p_S = 0.99, sigma_B,v = 4 m/s) and the five configurations of this
-project's benchmark plan.
+millions of particles, p_S = 0.99, sigma_B,v = 4 m/s) at the workload sizes below: a
+small plain grid, the automotive-size grid and a lidar + radar fusion grid.
 
 Measurement grid model (inverse sensor model of a 2D scanner at the grid centre):
 beams at uniform angles are ray-cast against the scene (oriented rectangles plus a wall
@@ -31,15 +31,15 @@ COMMON = dict(p_S=0.99, p_B=0.02, alpha=0.9, sigma_pos=0.1, sigma_vel=2.0,
               sigma_birth_vel=4.0, occ_mass=0.9, free_mass=0.7, range_noise=0.1, dt=0.1)
 
 CONFIGS = {
-    1: dict(COMMON, name="plain 128x128 @0.5 m, 65,536 + 16,384 particles",
+    "plain_128": dict(COMMON, name="plain 128x128 @0.5 m, 65,536 + 16,384 particles",
             width=128, height=128, cell_size=0.5, nu=65536, nu_b=16384, frames=20,
             n_moving=4, moving_size=(2.0, 4.5), moving_speed=(0.0, 15.0), n_static=0,
             beams=1080),
-    2: dict(COMMON, name="automotive 1024x1024 @0.1 m, 4,194,304 + 1,048,576 particles",
+    "automotive_1024": dict(COMMON, name="automotive 1024x1024 @0.1 m, 4,194,304 + 1,048,576 particles",
             width=1024, height=1024, cell_size=0.1, nu=4194304, nu_b=1048576, frames=100,
             n_moving=30, moving_side=(1.0, 5.0), moving_speed=(0.0, 20.0), n_static=200,
             static_side=(0.5, 3.0), beams=2160),
-    5: dict(COMMON, name="fusion 2048x2048 @0.1 m, 16,777,216 + 4,194,304 particles, lidar + radar",
+    "fusion_2048": dict(COMMON, name="fusion 2048x2048 @0.1 m, 16,777,216 + 4,194,304 particles, lidar + radar",
             width=2048, height=2048, cell_size=0.1, nu=16777216, nu_b=4194304, frames=100,
             n_moving=30, moving_side=(1.0, 5.0), moving_speed=(0.0, 20.0), n_static=200,
             static_side=(0.5, 3.0), beams=4320, radar_detections=64, radar_sigma_r=0.3,

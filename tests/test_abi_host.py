@@ -43,28 +43,30 @@ def test_error_strings(lib):
 
 
 def test_workspace_bytes_and_validation(lib):
-    cfg = scene.CONFIGS[2]
+    cfg = scene.CONFIGS["automotive_1024"]
     p = N.make_params(scene.filter_params(cfg))
     n = N.dog_workspace_bytes(p)
     # every particle array, the sort buffers and the cell arrays fit, and nothing absurd
     assert 4 * 16 * cfg["nu"] < n < 8 * 64 * cfg["nu"] + 256 * cfg["width"] * cfg["height"]
-    small = N.make_params(scene.filter_params(scene.CONFIGS[1]))
+    small = N.make_params(scene.filter_params(scene.CONFIGS["plain_128"]))
     assert N.dog_workspace_bytes(small) < n
     bad = N.make_params(dict(scene.filter_params(cfg), p_S=1.5))
     with pytest.raises(N.DogError) as e:
         N.dog_workspace_bytes(bad)
     assert e.value.code == -1
-    huge = N.make_params(dict(scene.filter_params(cfg), width=8192, height=4096))
-    with pytest.raises(N.DogError) as e:
-        N.dog_workspace_bytes(huge)
-    assert e.value.code == -7
+    for w, h in [(8192, 4096), (4096, 4096)]:  # C = 2^25, and C = 2^24 just past the limit
+        huge = N.make_params(dict(scene.filter_params(cfg), width=w, height=h))
+        with pytest.raises(N.DogError) as e:
+            N.dog_workspace_bytes(huge)
+        assert e.value.code == -7
+    assert N.dog_workspace_bytes(N.make_params(dict(scene.filter_params(cfg), width=4095, height=4096))) > 0
     zero = N.make_params(dict(scene.filter_params(cfg), nu=0))
     with pytest.raises(N.DogError):
         N.dog_workspace_bytes(zero)
 
 
 def test_create_rejects_small_or_unaligned_workspace(lib):
-    p = N.make_params(scene.filter_params(scene.CONFIGS[1]))
+    p = N.make_params(scene.filter_params(scene.CONFIGS["plain_128"]))
     n = N.dog_workspace_bytes(p)
     h = C.c_void_p()
     assert lib.dog_create(C.byref(p), C.c_void_p(256), n - 1, None, C.byref(h)) == -2

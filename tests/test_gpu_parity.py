@@ -1,8 +1,17 @@
 """GPU parity: the CUDA path (through the C ABI) against the oracle's FP32 mirror on the
 same seeded inputs.  Integer and index results (cell keys, sort order, cell ranges,
 fixed-point sums, newborn slots, resample sources) and every FP32 mass, weight and particle
-state are compared bit for bit; velocity moments within the tolerance derived in the design doc
-(mean: 1e-5 (1 + |mean|); variance and covariance: 1e-5 (1 + E[v^2])).
+state are compared bit for bit; velocity moments within a tolerance derived from the
+kernel's arithmetic:
+
+The kernel sums the terms u v, u v^2, u vx vy (u = w'/rho_p, Eq. mean_x, var_x, covar_xy)
+in binary32 over a binary tree of depth <= 11 inside a 2048-particle tile, joins the pieces
+of a cell spread over tiles in 2^-40 fixed point, and forms u with one rounded product by a
+rounded reciprocal; the oracle sums the same terms in binary64.  Each partial sum is
+therefore off by at most (11 + 3) 2^-24 of the sum of |terms| plus 2^-40 per piece, i.e.
+|err(mean)| <= 14 * 2^-24 * E_u|v| + 1e-11 <= 9e-7 sqrt(E_u[v^2]).  The tolerances below
+are that bound with an order of magnitude of headroom:
+mean: 1e-5 (1 + sqrt(E[v^2])); variance and covariance: 1e-5 (1 + E[v^2]).
 """
 import numpy as np
 import pytest
@@ -41,7 +50,7 @@ def assert_bits(name, got, ref):
 def moment_tolerance(ref):
     ev2x = ref["var_vx"].astype(np.float64) + ref["mean_vx"].astype(np.float64) ** 2
     ev2y = ref["var_vy"].astype(np.float64) + ref["mean_vy"].astype(np.float64) ** 2
-    return {"mean_vx": 1e-5 * (1 + np.abs(ref["mean_vx"])), "mean_vy": 1e-5 * (1 + np.abs(ref["mean_vy"])),
+    return {"mean_vx": 1e-5 * (1 + np.sqrt(ev2x)), "mean_vy": 1e-5 * (1 + np.sqrt(ev2y)),
             "var_vx": 1e-5 * (1 + ev2x), "var_vy": 1e-5 * (1 + ev2y),
             "cov_vxy": 1e-5 * (1 + np.sqrt(ev2x * ev2y))}
 
@@ -137,7 +146,7 @@ def test_radar_frames():
 
 def test_config1_scene_from_initial_state():
     """The 128x128 plain workload from its initial state, 20 frames, every frame compared."""
-    cfg = scene.CONFIGS[1]
+    cfg = scene.CONFIGS["plain_128"]
     p = scene.filter_params(cfg, flags=RECORD)
     grids = scene.frame_sequence(cfg, cfg["frames"], 1001)
     run_pair(p, cfg["frames"], grids)
@@ -172,7 +181,7 @@ def test_edge_cases(case):
 
 
 def test_checkpoint_resume_is_bit_exact():
-    cfg = scene.CONFIGS[1]
+    cfg = scene.CONFIGS["plain_128"]
     p = scene.filter_params(cfg)
     grids = scene.frame_sequence(cfg, 16, 1001)
     a = _gpu(p)
@@ -197,7 +206,7 @@ def test_checkpoint_resume_is_bit_exact():
 
 
 def test_runs_are_deterministic():
-    cfg = scene.CONFIGS[1]
+    cfg = scene.CONFIGS["plain_128"]
     p = scene.filter_params(cfg)
     grids = scene.frame_sequence(cfg, 6, 1001)
     outs = []
@@ -241,7 +250,7 @@ def test_invalid_measurement_grid_is_rejected():
 def test_full_size_automotive_frames():
     """The 1024x1024, 4,194,304 + 1,048,576 particle workload in the launch configuration
     bench.py times (CUDA graph), three frames against the oracle, everything compared."""
-    cfg = scene.CONFIGS[2]
+    cfg = scene.CONFIGS["automotive_1024"]
     p = scene.filter_params(cfg, flags=RECORD)
     grids = scene.frame_sequence(cfg, 3, 1002)
     run_pair(p, 3, grids)

@@ -53,8 +53,8 @@ def _noalloc(keys_np, num_cells):
 
 def test_noalloc_assignment_matches_dog_step_twice():
     cases = [
-        dict(scene.filter_params(scene.CONFIGS[1])),                        # 65,536 particles, 128x128
-        dict(scene.filter_params(scene.CONFIGS[1]), width=300, height=200,  # ragged, other size
+        dict(scene.filter_params(scene.CONFIGS["plain_128"])),                        # 65,536 particles, 128x128
+        dict(scene.filter_params(scene.CONFIGS["plain_128"]), width=300, height=200,  # ragged, other size
              nu=3 * 4096 + 777, nu_b=1000, cell_size=0.3),
     ]
     for seed, p in enumerate(cases):
