@@ -19,8 +19,8 @@
  *   - Arrays are SoA; cell arrays have C = width * height entries in row-major order
  *     (cell index = row * width + col, row = floor(y / cell_size), col = floor(x / cell_size),
  *     grid origin at the corner (0, 0)).
- *   - Errors detected on the device (an input that fails validation, a bounded wait that
- *     ran out) are latched in the filter and returned by the next synchronising call
+ *   - Errors detected on the device (an input that fails validation, an internal
+ *     consistency check) are latched in the filter and returned by the next synchronising call
  *     (dog_get_cells, dog_get_state, dog_get_debug, dog_sync), which clears them.  While an
  *     error is latched, the results of the frames that follow are void.
  */
@@ -39,7 +39,7 @@ typedef enum dog_status {
   DOG_ERR_INVALID_ARG = -1,         /* bad pointer, size or parameter                   */
   DOG_ERR_WORKSPACE_TOO_SMALL = -2, /* workspace smaller than dog_workspace_bytes        */
   DOG_ERR_CUDA = -3,                /* a CUDA runtime call failed                        */
-  DOG_ERR_TIMEOUT = -4,             /* a device-side bounded wait gave up; results void  */
+  DOG_ERR_DEVICE = -4,              /* a device-side consistency check failed; void      */
   DOG_ERR_INPUT = -5,               /* measurement grid / state outside its domain       */
   DOG_ERR_BAD_STATE = -6,           /* call not valid in the filter's current state      */
   DOG_ERR_UNSUPPORTED = -7          /* size beyond the supported maximum                 */

@@ -17,7 +17,7 @@ using namespace dog;
 
 namespace {
 
-constexpr int MAX_KERNELS = 13;
+constexpr int MAX_KERNELS = 18;
 constexpr int PROFILE_RING = 1024;
 
 struct Derived {
@@ -109,7 +109,7 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
   B->bl_wUA = (float *)take(4 * CL);
   B->tile_first = (uint32_t *)take(4 * ((size_t)d.tiles_cell + 1));
   B->hist = (uint32_t *)take(4 * 2048 * (size_t)d.passes);
-  B->lb_sort = (uint32_t *)take(4 * (size_t)d.passes * d.tiles_sort * d.radix);
+  B->dcnt = (uint32_t *)take(4 * (size_t)d.passes * d.tiles_sort * d.radix);
   B->S_piece = (unsigned long long *)take(8 * C);
   B->A_piece = (unsigned long long *)take(8 * C);
   B->Mx = (unsigned long long *)take(8 * 5 * C);
@@ -123,7 +123,9 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
   return (off + 255) & ~(size_t)255;
 }
 
-const char *KNAMES[MAX_KERNELS] = {"k_tick", "k_predict", "k_sort_pass0", "k_sort_pass1", "k_sort_pass2",
+const char *KNAMES[MAX_KERNELS] = {"k_tick", "k_predict", "k_sort_offsets0", "k_sort_pass0",
+                                   "k_sort_count1", "k_sort_offsets1", "k_sort_pass1",
+                                   "k_sort_count2", "k_sort_offsets2", "k_sort_pass2",
                                    "k_segsum", "k_cell", "k_scan_births", "k_birth_prep", "k_birth",
                                    "k_normalise", "k_scan_cdf", "k_resample"};
 
@@ -194,6 +196,12 @@ int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
       kout = B.key_t1;
       vout = B.val_t1;
     }
+    if (p > 0) {
+      k_sort_count<<<K.tiles_sort, COUNT_BLOCK, 4u * K.radix, st>>>(K, B, kin, p);
+      ++k; mark();
+    }
+    k_sort_offsets<<<K.radix, OFF_BLOCK, 0, st>>>(K, B, p);
+    ++k; mark();
     k_sort_pass<<<K.tiles_sort, SORT_BLOCK, ssm, st>>>(K, B, kin, vin, kout, vout, p);
     kin = kout;
     vin = vout;
@@ -234,19 +242,17 @@ int read_err(dog_filter *f) {
     DOG_CUDA(cudaMemcpyAsync(&f->B.ctl->err, &zero, 4, cudaMemcpyHostToDevice, f->st));
     DOG_CUDA(cudaStreamSynchronize(f->st));
     if (h.err & ERR_INPUT) return DOG_ERR_INPUT;
-    return DOG_ERR_TIMEOUT;
+    return DOG_ERR_DEVICE;
   }
   return DOG_OK;
 }
 
-// zero the sort's look-back words, the cell tags and the piece accumulators (needed
-// whenever the frame counter is set to a value earlier frames may have used, and to drop
-// whatever a failed frame left behind)
+// zero the cell tags and the piece accumulators (needed whenever the frame counter is set
+// to a value earlier frames may have used, and to drop whatever a failed frame left behind)
 int reset_epochs(dog_filter *f) {
   const Derived &d = f->d;
   DevBufs &B = f->B;
   DOG_CUDA(cudaMemsetAsync(B.tag, 0, 4 * (size_t)d.C, f->st));
-  DOG_CUDA(cudaMemsetAsync(B.lb_sort, 0, 4 * (size_t)d.passes * d.tiles_sort * d.radix, f->st));
   DOG_CUDA(cudaMemsetAsync(B.S_piece, 0, 8 * (size_t)d.C, f->st));
   DOG_CUDA(cudaMemsetAsync(B.A_piece, 0, 8 * (size_t)d.C, f->st));
   DOG_CUDA(cudaMemsetAsync(B.Mx, 0, 8 * 5 * (size_t)d.C, f->st));
@@ -293,7 +299,7 @@ const char *dog_error_string(int code) {
     case DOG_ERR_INVALID_ARG: return "invalid argument";
     case DOG_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
     case DOG_ERR_CUDA: return "CUDA runtime error";
-    case DOG_ERR_TIMEOUT: return "device-side bounded wait timed out";
+    case DOG_ERR_DEVICE: return "device-side consistency check failed";
     case DOG_ERR_INPUT: return "input outside its domain";
     case DOG_ERR_BAD_STATE: return "call not valid in the current state";
     case DOG_ERR_UNSUPPORTED: return "size beyond the supported maximum";
@@ -357,7 +363,7 @@ int dog_create(const dog_params *params, void *d_workspace, size_t workspace_byt
   K.tiles_seg = d.tiles_seg;
   K.tiles_cell = d.tiles_cell;
   K.tiles_norm = d.tiles_norm;
-  f->nk = 10 + d.passes;
+  f->nk = 9 + 3 * d.passes;
   f->profile = (params->flags & DOG_PROFILE) != 0;
   f->use_graph = !(params->flags & DOG_NO_GRAPH) && f->st != nullptr && !f->profile;
   int dev = 0, sms = 148;
@@ -607,8 +613,14 @@ int dog_profile_read(dog_filter *f, float *ms, const char **names, int max, int 
   int nk = 0;
   slot_kind[nk++] = 0;
   slot_kind[nk++] = 1;
-  for (int p = 0; p < f->d.passes; ++p) slot_kind[nk++] = 2 + p;
-  for (int k = 5; k <= 12; ++k) slot_kind[nk++] = k;
+  slot_kind[nk++] = 2;
+  slot_kind[nk++] = 3;
+  for (int p = 1; p < f->d.passes; ++p) {
+    slot_kind[nk++] = 1 + 3 * p;
+    slot_kind[nk++] = 2 + 3 * p;
+    slot_kind[nk++] = 3 + 3 * p;
+  }
+  for (int k = 10; k <= 17; ++k) slot_kind[nk++] = k;
   const int n = nk < max ? nk : max;
   for (int k = 0; k < n; ++k) ms[k] = 0.0f;
   for (int r = 0; r < f->ring_count; ++r) {
@@ -648,33 +660,35 @@ constexpr uint32_t NA_MAX_CELLS = 1u << 22;  // cells per call (keys of at most 
 constexpr uint32_t NA_TILES = NA_MAX_N / SORT_TILE;
 constexpr size_t NA_CTL = 256;
 constexpr size_t NA_HIST = 2 * 2048 * 4;
-constexpr size_t NA_LB = (size_t)2 * NA_TILES * 2048 * 4;
+constexpr size_t NA_DCNT = (size_t)2 * NA_TILES * 2048 * 4;
 constexpr size_t NA_ARR = (size_t)NA_MAX_N * 4;
-constexpr size_t NA_BYTES = NA_CTL + NA_HIST + NA_LB + 3 * NA_ARR;  // 8,405,248 bytes
+constexpr size_t NA_BYTES = NA_CTL + NA_HIST + NA_DCNT + 3 * NA_ARR;  // 8,405,248 bytes
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
-// digit histograms of all passes for caller-provided keys
-__global__ void k_na_hist(const uint32_t *__restrict__ keys, uint32_t n, int passes, int dbits,
-                          uint32_t radix, uint32_t *hist) {
+// digit histograms of all passes for caller-provided keys; block t counts the keys of sort
+// tile t and writes that tile's first-pass digit counts
+__global__ void k_na_hist(const uint32_t *__restrict__ keys, KParams K, DevBufs B) {
   extern __shared__ uint32_t sh[];
-  const uint32_t nh = (uint32_t)passes * radix;
+  const uint32_t nh = (uint32_t)K.passes * K.radix;
   for (uint32_t k = threadIdx.x; k < nh; k += blockDim.x) sh[k] = 0u;
   __syncthreads();
-  const uint32_t mask = radix - 1u;
-  for (uint32_t b = blockIdx.x * blockDim.x; b < n; b += gridDim.x * blockDim.x) {
-    const uint32_t i = b + threadIdx.x;
-    const bool ok = i < n;
+  const uint32_t mask = K.radix - 1u;
+  for (uint32_t i = blockIdx.x * SORT_TILE + threadIdx.x; i < (blockIdx.x + 1u) * SORT_TILE;
+       i += blockDim.x) {
+    const bool ok = i < K.nu;
     const uint32_t key = ok ? keys[i] : 0u;
-    for (int p = 0; p < passes; ++p) {
-      const uint32_t d = ok ? ((key >> (p * dbits)) & mask) : 0xffffffffu;
+    for (int p = 0; p < K.passes; ++p) {
+      const uint32_t d = ok ? ((key >> (p * K.dbits)) & mask) : 0xffffffffu;
       const uint32_t peers = __match_any_sync(FULL, d);
-      if (ok && (peers & lanemask_lt()) == 0u) atomicAdd(&sh[p * radix + d], (uint32_t)__popc(peers));
+      if (ok && (peers & lanemask_lt()) == 0u) atomicAdd(&sh[p * K.radix + d], (uint32_t)__popc(peers));
     }
   }
   __syncthreads();
   for (uint32_t k = threadIdx.x; k < nh; k += blockDim.x)
-    if (sh[k]) atomicAdd(&hist[(k / radix) * 2048u + (k % radix)], sh[k]);
+    if (sh[k]) atomicAdd(&B.hist[(k / K.radix) * 2048u + (k % K.radix)], sh[k]);
+  for (uint32_t d = threadIdx.x; d < K.radix; d += blockDim.x)
+    B.dcnt[(size_t)d * K.tiles_sort + blockIdx.x] = sh[d];
 }
 
 // half-open range of each cell in the sorted order (keys outside [0, num_cells) are skipped)
@@ -740,21 +754,21 @@ extern "C" int dog_assign_cells_noalloc(const uint32_t *d_keys, uint32_t n, uint
   DevBufs B{};
   B.ctl = (DevCtl *)base;
   B.hist = (uint32_t *)(base + NA_CTL);
-  B.lb_sort = (uint32_t *)(base + NA_CTL + NA_HIST);
-  uint32_t *key_t0 = (uint32_t *)(base + NA_CTL + NA_HIST + NA_LB);
+  B.dcnt = (uint32_t *)(base + NA_CTL + NA_HIST);
+  uint32_t *key_t0 = (uint32_t *)(base + NA_CTL + NA_HIST + NA_DCNT);
   uint32_t *val_t0 = key_t0 + NA_MAX_N;
   uint32_t *key_sorted = val_t0 + NA_MAX_N;
-  // the look-back status words of this call's tiles must start at zero: the array keeps
-  // whatever the previous call (possibly of another size) left in it
-  DOG_CUDA(cudaMemsetAsync(B.lb_sort, 0, 4 * (size_t)K.passes * K.tiles_sort * K.radix, st));
+  // every array of the scratch is rewritten before it is read: the histogram by k_tick, the
+  // per-tile digit counts by k_na_hist (first pass) and k_sort_count (later passes)
   k_tick<<<1, 256, 0, st>>>(B, 2048 * K.passes);
-  const uint32_t hgrid = (n + 255) / 256 < 1024u ? (n + 255) / 256 : 1024u;
-  k_na_hist<<<hgrid, 256, 4u * K.passes * K.radix, st>>>(d_keys, n, K.passes, K.dbits, K.radix, B.hist);
+  k_na_hist<<<K.tiles_sort, 256, 4u * K.passes * K.radix, st>>>(d_keys, K, B);
   const size_t ssm = sort_smem_bytes(K.radix);
   const uint32_t *kin = d_keys, *vin = nullptr;
   for (int p = 0; p < K.passes; ++p) {
     uint32_t *kout = (p == K.passes - 1) ? key_sorted : key_t0;
     uint32_t *vout = (p == K.passes - 1) ? d_perm : val_t0;
+    if (p > 0) k_sort_count<<<K.tiles_sort, COUNT_BLOCK, 4u * K.radix, st>>>(K, B, kin, p);
+    k_sort_offsets<<<K.radix, OFF_BLOCK, 0, st>>>(K, B, p);
     k_sort_pass<<<K.tiles_sort, SORT_BLOCK, ssm, st>>>(K, B, kin, vin, kout, vout, p);
     kin = kout;
     vin = vout;

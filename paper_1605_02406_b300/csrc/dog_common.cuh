@@ -9,20 +9,7 @@ namespace dog {
 constexpr uint32_t FULL = 0xffffffffu;
 
 // error bits latched in DevCtl::err
-enum : uint32_t {
-  ERR_TIMEOUT_SORT = 1u, ERR_INPUT = 16u, ERR_INTERNAL = 32u
-};
-
-// dynamic tile counters of the sort passes (reset every frame by k_tick)
-enum : int { CTR_SORT0 = 0, CTR_SORT1, CTR_SORT2, CTR_COUNT = 8 };
-
-// look-back status: (epoch << 2) | state
-enum : uint32_t { ST_NONE = 0, ST_AGG = 1, ST_INCL = 2 };
-
-// spin bound of the sort's device-wide wait: 2^20 polls with a short sleep (about a second),
-// after which the waiter latches an error bit and proceeds; a waiter that sees an error
-// already latched gives up at once, so a failed frame drains quickly.
-constexpr int SPIN_LIMIT = 1 << 20;
+enum : uint32_t { ERR_INPUT = 16u, ERR_INTERNAL = 32u };
 
 struct DevCtl {
   uint32_t frame;          // incremented by k_tick at the start of every step
@@ -32,7 +19,6 @@ struct DevCtl {
   unsigned long long R_total;
   unsigned long long W_total;
   unsigned long long u_offset;
-  unsigned long long ctr[CTR_COUNT];
   uint32_t pad[8];
 };
 
@@ -72,7 +58,8 @@ struct DevBufs {
   uint32_t *tile_first;               // [tiles_cell + 1] first slot of each cell tile
   // scratch of the sort and the tile scans
   uint32_t *hist;                  // [passes][2048] digit histograms
-  uint32_t *lb_sort;               // [passes][tiles_sort][radix] look-back words
+  uint32_t *dcnt;                  // [passes][tiles_sort][radix] digit counts of each sort
+                                   // tile, turned into global output offsets in place
   unsigned long long *S_piece, *A_piece;  // [C] pieces of cells spread over several tiles
   unsigned long long *Mx;          // [5][C] moment pieces
   uint32_t *Mcnt;                  // [C] pieces counted in so far

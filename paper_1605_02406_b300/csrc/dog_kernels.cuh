@@ -4,7 +4,8 @@
 //   k_tick        frame counter, reset of per-frame counters and digit histograms
 //   k_predict     Alg. 1  B -> A: constant-velocity prediction with Philox process noise,
 //                          persistence weight, cell index; digit histograms for the sort
-//   k_sort_pass   Alg. 2  onesweep LSD radix pass(es) of (cell index, particle index)
+//   k_sort_count / k_sort_offsets / k_sort_pass
+//                 Alg. 2  LSD radix passes of (cell index, particle index), reduce-then-scan
 //   k_segsum      Alg. 2/3 cell ranges and exact fixed-point per-cell sums of w (and g w)
 //   k_cell        Alg. 3  occupancy prediction, DS update, newborn split, normalisers;
 //                          per-tile lists of cells with newborn mass
@@ -15,8 +16,8 @@
 //                          the joint weights
 //   k_scan_tiles          CDF of the joint weights over tiles
 //   k_resample    Alg. 7  systematic resampling A + newborns -> B
-// No kernel waits for another block of the same launch except the sort passes, whose
-// digit offsets come from a bounded decoupled look-back.
+// No block waits for another block of the same launch: every cross-block dependency is a
+// kernel boundary.
 #pragma once
 #include "dog_common.cuh"
 #include "dog_math.cuh"
@@ -28,7 +29,6 @@ namespace dog {
 // ====================================================================================
 __global__ void k_tick(DevBufs B, int n_hist) {
   for (int i = threadIdx.x; i < n_hist; i += blockDim.x) B.hist[i] = 0u;
-  if (threadIdx.x < CTR_COUNT) B.ctl->ctr[threadIdx.x] = 0ull;
   if (threadIdx.x == 0) B.ctl->frame += 1u;
 }
 
@@ -173,28 +173,33 @@ __global__ void __launch_bounds__(PRED_BLOCK) k_predict(KParams P, DevBufs B) {
     const uint32_t v = sh_hist[k];
     if (v) atomicAdd(&B.hist[(k / P.radix) * 2048u + (k % P.radix)], v);
   }
+  // this block's keys are tile blockIdx.x of the first sort pass: its first-pass digit counts
+  for (uint32_t d = threadIdx.x; d < P.radix; d += PRED_BLOCK)
+    B.dcnt[(size_t)d * P.tiles_sort + blockIdx.x] = sh_hist[d];
 }
 
 // ====================================================================================
-// k_sort_pass (Alg. 2, sort): one onesweep LSD radix pass (Adinets & Merrill, 2022) of
-// (cell index, particle index) pairs on a digit of up to 11 bits.  A tile of 4096 keys is
-// ranked stably in shared memory (per-warp histograms with match.any), its digit counts
-// are published immediately, the global digit offsets come from a bounded decoupled
-// look-back over earlier tiles, and the tile is scattered through shared memory so that
-// equal digits leave as contiguous runs.
+// Sort (Alg. 2): LSD radix sort of (cell index, particle index) pairs on digits of up to 11
+// bits, reduce-then-scan: every pass works on fixed tiles of 4096 pairs, and the output
+// offset of each (digit, tile) is known before the pass starts, so no block waits for
+// another.
+//   - digit counts per tile, stored digit-major ([pass][digit][tile]): k_predict writes the
+//     first pass's (its blocks are that pass's tiles); k_sort_count counts a later pass's
+//     tiles in the output of the pass before;
+//   - k_sort_offsets turns one pass's counts into global offsets, in place: start of the
+//     digit (prefix of the digit histogram) + the digit's count in all earlier tiles;
+//   - k_sort_pass ranks its tile stably in shared memory (warp-private digit counters with
+//     match.any) and writes each digit's run contiguously at its offset.
 // ====================================================================================
 constexpr int SORT_BLOCK = 512, SORT_ITEMS = 8, SORT_WARPS = SORT_BLOCK / 32,
               SORT_TILE = SORT_BLOCK * SORT_ITEMS;
+static_assert(PRED_TILE == SORT_TILE, "k_predict's blocks are the first sort pass's tiles");
 
 __host__ __device__ constexpr size_t sort_smem_bytes(uint32_t radix) {
   // ranking: per-warp u16 histograms, later reused for the staged keys and values
   return ((size_t)SORT_WARPS * radix * 2 > (size_t)SORT_TILE * 8 ? (size_t)SORT_WARPS * radix * 2
                                                                   : (size_t)SORT_TILE * 8) +
-         (size_t)4 * radix * 4 + 128;
-}
-
-__device__ __forceinline__ uint32_t pack_digit(uint32_t ep5, uint32_t st, uint32_t cnt) {
-  return (ep5 << 27) | (st << 25) | cnt;
+         (size_t)3 * radix * 4 + 128;
 }
 
 // exclusive scan of n <= 2048 values in shared memory by SORT_BLOCK threads
@@ -213,13 +218,16 @@ __device__ void block_excl_scan_u32(const uint32_t *in, uint32_t *out, uint32_t 
   }
   if (lane == 31) s_warp[warp] = inc;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t run = 0;
-    for (int w = 0; w < SORT_WARPS; ++w) {
-      const uint32_t t = s_warp[w];
-      s_warp[w] = run;
-      run += t;
+  if (warp == 0) {  // exclusive scan of the SORT_WARPS warp totals
+    const uint32_t v = lane < (uint32_t)SORT_WARPS ? s_warp[lane] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < SORT_WARPS; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(FULL, x, o);
+      if (lane >= (uint32_t)o) x += t;
     }
+    __syncwarp();
+    if (lane < (uint32_t)SORT_WARPS) s_warp[lane] = x - v;
   }
   __syncthreads();
   uint32_t run = s_warp[warp] + inc - loc;
@@ -232,32 +240,126 @@ __device__ void block_excl_scan_u32(const uint32_t *in, uint32_t *out, uint32_t 
   __syncthreads();
 }
 
+// k_sort_count: digit counts of one pass's tiles (block t counts keys [4096 t, 4096 t + 4096)
+// of the pass's input)
+constexpr int COUNT_BLOCK = 256;
+
+__global__ void __launch_bounds__(COUNT_BLOCK) k_sort_count(KParams P, DevBufs B,
+                                                            const uint32_t *__restrict__ keys, int pass) {
+  extern __shared__ uint32_t sh_cnt[];  // [radix]
+  const uint32_t radix = P.radix, mask = radix - 1u;
+  const int shift = pass * P.dbits;
+  for (uint32_t d = threadIdx.x; d < radix; d += COUNT_BLOCK) sh_cnt[d] = 0u;
+  __syncthreads();
+  const uint32_t base = blockIdx.x * SORT_TILE;
+  constexpr int N = SORT_TILE / COUNT_BLOCK;
+  uint32_t k[N];  // all loads in flight before the first count
+#pragma unroll
+  for (int it = 0; it < N; ++it) {
+    const uint32_t i = base + it * COUNT_BLOCK + threadIdx.x;
+    k[it] = i < P.nu ? __ldg(keys + i) : 0xffffffffu;
+  }
+#pragma unroll
+  for (int it = 0; it < N; ++it)
+    if (k[it] != 0xffffffffu) atomicAdd(&sh_cnt[(k[it] >> shift) & mask], 1u);
+  __syncthreads();
+  uint32_t *col = B.dcnt + (size_t)pass * radix * P.tiles_sort;
+  for (uint32_t d = threadIdx.x; d < radix; d += COUNT_BLOCK)
+    col[(size_t)d * P.tiles_sort + blockIdx.x] = sh_cnt[d];
+}
+
+// k_sort_offsets: for one pass, counts[d][t] -> (sum of the histogram below digit d) +
+// sum_{t' < t} counts[d][t'], in place.  One block per digit; thread k owns a contiguous run
+// of tiles, and the block scans the runs' totals.
+constexpr int OFF_BLOCK = 256, OFF_WARPS = OFF_BLOCK / 32, OFF_PER = 8;
+
+__global__ void __launch_bounds__(OFF_BLOCK) k_sort_offsets(KParams P, DevBufs B, int pass) {
+  __shared__ uint32_t s_h[OFF_WARPS], s_t[OFF_WARPS];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t d = blockIdx.x;
+  const uint32_t T = P.tiles_sort;
+  const uint32_t *hist = B.hist + pass * 2048u;
+  uint32_t *M = B.dcnt + ((size_t)pass * P.radix + d) * T;
+  const uint32_t per = (T + OFF_BLOCK - 1) / OFF_BLOCK;  // tiles per thread
+  const uint32_t t0 = threadIdx.x * per;
+  // this thread's share of the histogram below d, and the total of its tiles
+  uint32_t hsum = 0, tsum = 0;
+  for (uint32_t e = threadIdx.x; e < d; e += OFF_BLOCK) hsum += __ldg(hist + e);
+  for (uint32_t j0 = 0; j0 < per; j0 += OFF_PER) {
+    uint32_t c[OFF_PER];
+#pragma unroll
+    for (int j = 0; j < OFF_PER; ++j) {
+      const uint32_t t = t0 + j0 + j;
+      c[j] = (j0 + j < per && t < T) ? M[t] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < OFF_PER; ++j) tsum += c[j];
+  }
+  // block: total of hsum, exclusive prefix of tsum
+  uint32_t tinc = tsum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    hsum += __shfl_xor_sync(FULL, hsum, o);
+    const uint32_t y = __shfl_up_sync(FULL, tinc, o);
+    if (lane >= (uint32_t)o) tinc += y;
+  }
+  if (lane == 31) {
+    s_h[warp] = hsum;
+    s_t[warp] = tinc;
+  }
+  __syncthreads();
+  uint32_t run = tinc - tsum;
+  for (uint32_t w = 0; w < OFF_WARPS; ++w) {
+    run += s_h[w];
+    if (w < warp) run += s_t[w];
+  }
+  for (uint32_t j0 = 0; j0 < per; j0 += OFF_PER) {
+    uint32_t c[OFF_PER];
+#pragma unroll
+    for (int j = 0; j < OFF_PER; ++j) {
+      const uint32_t t = t0 + j0 + j;
+      c[j] = (j0 + j < per && t < T) ? M[t] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < OFF_PER; ++j) {
+      const uint32_t t = t0 + j0 + j;
+      if (j0 + j < per && t < T) M[t] = run;
+      run += c[j];
+    }
+  }
+}
+
 __global__ void __launch_bounds__(SORT_BLOCK, 2)
     k_sort_pass(KParams P, DevBufs B, const uint32_t *__restrict__ keys_in,
                 const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
                 uint32_t *__restrict__ vals_out, int pass) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t radix = P.radix;
-  const size_t big = sort_smem_bytes(radix) - (size_t)4 * radix * 4 - 128;
+  const size_t big = sort_smem_bytes(radix) - (size_t)3 * radix * 4 - 128;
   uint16_t *s_whist = reinterpret_cast<uint16_t *>(smem);      // [warps][radix]
   uint32_t *s_keys = reinterpret_cast<uint32_t *>(smem);       // [tile] (after ranking)
   uint32_t *s_vals = s_keys + SORT_TILE;                       // [tile]
   uint32_t *s_cnt = reinterpret_cast<uint32_t *>(smem + big);  // [radix]
   uint32_t *s_excl = s_cnt + radix;
   uint32_t *s_base = s_excl + radix;
-  uint32_t *s_gst = s_base + radix;
-  uint32_t *s_misc = s_gst + radix;  // [32]: tile id, warp sums
+  uint32_t *s_misc = s_base + radix;  // [32]: warp sums
 
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t tile = blockIdx.x;
   const int shift = pass * P.dbits;
   const uint32_t mask = radix - 1u;
-  if (tid == 0) s_misc[0] = (uint32_t)atomicAdd(&B.ctl->ctr[CTR_SORT0 + pass], 1ull);
+  // global output offset of this tile's digits (radix <= 2048)
+  constexpr int DPT = (2048 + SORT_BLOCK - 1) / SORT_BLOCK;  // digits per thread, at most
+  const uint32_t *off = B.dcnt + (size_t)pass * radix * P.tiles_sort + tile;
+  uint32_t offr[DPT];
+#pragma unroll
+  for (int j = 0; j < DPT; ++j) {
+    const uint32_t d = tid + j * SORT_BLOCK;
+    offr[j] = d < radix ? __ldg(off + (size_t)d * P.tiles_sort) : 0u;
+  }
   for (uint32_t k = tid; k < SORT_WARPS * radix / 2; k += SORT_BLOCK)
     reinterpret_cast<uint32_t *>(s_whist)[k] = 0u;
   __syncthreads();
-  const uint32_t tile = s_misc[0];
-  const uint32_t ep5 = B.ctl->frame & 31u;
-  uint32_t *lb = B.lb_sort + ((size_t)pass * P.tiles_sort + tile) * radix;
 
   // load: warp w covers positions [w*256, w*256+256) of the tile, item k at k*32 + lane
   uint32_t key[SORT_ITEMS], val[SORT_ITEMS];
@@ -283,8 +385,11 @@ __global__ void __launch_bounds__(SORT_BLOCK, 2)
     rk[k] = pre + __popc(peers & lt);
   }
   __syncthreads();
-  // per digit: exclusive offsets of the warps, tile count, publish the tile aggregate
-  for (uint32_t d = tid; d < radix; d += SORT_BLOCK) {
+  // per digit: exclusive offsets of the warps and the tile's count
+#pragma unroll
+  for (int j = 0; j < DPT; ++j) {
+    const uint32_t d = tid + j * SORT_BLOCK;
+    if (d >= radix) break;
     uint32_t run = 0;
     for (int w = 0; w < SORT_WARPS; ++w) {
       const uint32_t c = s_whist[w * radix + d];
@@ -292,14 +397,10 @@ __global__ void __launch_bounds__(SORT_BLOCK, 2)
       run += c;
     }
     s_cnt[d] = run;
-    st_volatile(lb + d, pack_digit(ep5, tile == 0 ? ST_INCL : ST_AGG, run));
+    s_base[d] = offr[j];
   }
-  // global digit starts (exclusive scan of this pass's histogram)
   __syncthreads();
-  for (uint32_t d = tid; d < radix; d += SORT_BLOCK) s_base[d] = B.hist[pass * 2048u + d];
-  __syncthreads();
-  block_excl_scan_u32(s_base, s_gst, radix, s_misc + 1);
-  block_excl_scan_u32(s_cnt, s_excl, radix, s_misc + 1);
+  block_excl_scan_u32(s_cnt, s_excl, radix, s_misc);
   // tile-local sorted position of each key
   uint32_t lpos[SORT_ITEMS];
 #pragma unroll
@@ -307,50 +408,12 @@ __global__ void __launch_bounds__(SORT_BLOCK, 2)
     const uint32_t d = (key[k] >> shift) & mask;
     lpos[k] = s_excl[d] + s_whist[warp * radix + d] + rk[k];
   }
+  for (uint32_t d = tid; d < radix; d += SORT_BLOCK) s_base[d] -= s_excl[d];
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < SORT_ITEMS; ++k) {
     s_keys[lpos[k]] = key[k];
     s_vals[lpos[k]] = val[k];
-  }
-  // decoupled look-back per digit, eight predecessors per round trip
-  const uint32_t *lb_pass = B.lb_sort + (size_t)pass * P.tiles_sort * radix;
-  for (uint32_t d = tid; d < radix; d += SORT_BLOCK) {
-    uint32_t excl = 0;
-    if (tile > 0) {
-      long long t = (long long)tile - 1;
-      int spins = 0;
-      while (t >= 0) {
-        uint32_t w[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          w[k] = (t - k >= 0) ? ld_volatile(lb_pass + (size_t)(t - k) * radix + d)
-                              : pack_digit(ep5, ST_INCL, 0u);
-        int k = 0;
-        bool done = false;
-        for (; k < 8; ++k) {
-          const uint32_t st = (w[k] >> 25) & 3u;
-          if ((w[k] >> 27) != ep5 || st == ST_NONE) break;  // not published yet
-          excl += w[k] & 0x1ffffffu;
-          if (st == ST_INCL) {
-            done = true;
-            break;
-          }
-        }
-        if (done) break;
-        t -= k;
-        if (k == 0) {
-          if (++spins > SPIN_LIMIT) {
-            atomicOr(&B.ctl->err, ERR_TIMEOUT_SORT);
-            break;
-          }
-          if ((spins & 255) == 0 && ld_volatile(&B.ctl->err) != 0u) break;
-          __nanosleep(32);
-        }
-      }
-      st_volatile(lb + d, pack_digit(ep5, ST_INCL, (excl + s_cnt[d]) & 0x1ffffffu));
-    }
-    s_base[d] = s_gst[d] + excl - s_excl[d];
   }
   __syncthreads();
   // scatter: runs of equal digits are contiguous in shared memory and in the output

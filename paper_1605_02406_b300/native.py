@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, "libdog.so")
 
 DOG_OK = 0
 DOG_ERR = {-1: "DOG_ERR_INVALID_ARG", -2: "DOG_ERR_WORKSPACE_TOO_SMALL", -3: "DOG_ERR_CUDA",
-           -4: "DOG_ERR_TIMEOUT", -5: "DOG_ERR_INPUT", -6: "DOG_ERR_BAD_STATE",
+           -4: "DOG_ERR_DEVICE", -5: "DOG_ERR_INPUT", -6: "DOG_ERR_BAD_STATE",
            -7: "DOG_ERR_UNSUPPORTED"}
 DOG_NO_RESAMPLE, DOG_RECORD, DOG_NO_GRAPH, DOG_PROFILE = 0x2, 0x4, 0x8, 0x10
 DOG_HOST, DOG_DEVICE = 0, 1
