@@ -118,9 +118,13 @@ int dog_create(const dog_params *params, void *d_workspace, size_t workspace_byt
 
 /* Copy a measurement grid into the filter (Sect. VII: same dimensions as the map); it is
  * used by every following dog_step until replaced.  mem_kind says where the caller's arrays
- * live.  DOG_HOST: validated on the host (DOG_ERR_INPUT on violation, nothing copied) and
- * the call returns after the copy; DOG_DEVICE: copied and validated on the filter's stream
- * (asynchronous; a violation is latched and reported as DOG_ERR_INPUT). */
+ * live.  The grid is copied and validated on the device (m_occ, m_free in [0, 1] with
+ * m_occ + m_free <= 1; p_A in [0, 1]; sigma_vr > 0 where p_A > 0; z_vr finite).
+ * DOG_HOST: the call waits for the copy (the caller may then reuse its arrays) and returns
+ * DOG_ERR_INPUT on a violation, after which dog_step refuses (DOG_ERR_BAD_STATE) until a
+ * valid grid is set; it also returns any error latched by earlier frames.  DOG_DEVICE:
+ * asynchronous; a violation is latched and reported as DOG_ERR_INPUT by the next
+ * synchronising call. */
 int dog_set_measurement_grid(dog_filter *f, const dog_meas_grid *grid, int mem_kind);
 
 /* One recursion of the filter with time step dt (s): Alg. 1-7 of Sect. VII.

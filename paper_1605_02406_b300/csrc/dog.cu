@@ -213,8 +213,8 @@ int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
   if (radar) k_cell<true><<<K.tiles_cell, CELL_BLOCK, 0, st>>>(K, B);
   else k_cell<false><<<K.tiles_cell, CELL_BLOCK, 0, st>>>(K, B);
   ++k; mark();
-  k_scan_tiles<<<1, SCAN_BLOCK, 0, st>>>(B.tile_q, B.tile_n, K.tiles_cell, B.tile_qin, B.tile_nin,
-                                          &B.ctl->R_total, &B.ctl->n_birth_cells);
+  k_scan_tiles<false><<<1, SCAN_BLOCK, 0, st>>>(B.tile_q, B.tile_n, K.tiles_cell, B.tile_qin, B.tile_nin,
+                                                 &B.ctl->R_total, &B.ctl->n_birth_cells, K, B.ctl);
   ++k; mark();
   if (radar) k_birth_prep<true><<<K.tiles_cell, CELL_BLOCK, 0, st>>>(K, B);
   else k_birth_prep<false><<<K.tiles_cell, CELL_BLOCK, 0, st>>>(K, B);
@@ -225,8 +225,8 @@ int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
   if (radar) k_normalise<true><<<K.tiles_norm, NORM_BLOCK, 0, st>>>(K, B);
   else k_normalise<false><<<K.tiles_norm, NORM_BLOCK, 0, st>>>(K, B);
   ++k; mark();
-  k_scan_tiles<<<1, SCAN_BLOCK, 0, st>>>(B.cdf_tile, nullptr, K.tiles_norm, B.cdf_incl, nullptr,
-                                          &B.ctl->W_total, nullptr);
+  k_scan_tiles<true><<<1, SCAN_BLOCK, 0, st>>>(B.cdf_tile, nullptr, K.tiles_norm, B.cdf_incl, nullptr,
+                                                &B.ctl->W_total, nullptr, K, B.ctl);
   ++k; mark();
   k_resample<<<K.tiles_norm, RES_BLOCK, 0, st>>>(K, B);
   ++k; mark();
@@ -408,18 +408,6 @@ int dog_set_measurement_grid(dog_filter *f, const dog_meas_grid *g, int mem_kind
   const bool radar = g->p_A != nullptr;
   if (radar && (!g->z_vr || !g->sigma_vr)) return DOG_ERR_INVALID_ARG;
   const size_t C = f->d.C;
-  if (mem_kind == DOG_HOST) {
-    for (size_t c = 0; c < C; ++c) {
-      const float a = g->m_occ[c], b = g->m_free[c];
-      if (!(a >= 0.0f && a <= 1.0f && b >= 0.0f && b <= 1.0f && a + b <= 1.000001f)) return DOG_ERR_INPUT;
-      if (radar) {
-        const float pa = g->p_A[c];
-        if (!(pa >= 0.0f && pa <= 1.0f)) return DOG_ERR_INPUT;
-        if (pa > 0.0f && !(g->sigma_vr[c] > 0.0f)) return DOG_ERR_INPUT;
-        if (!std::isfinite(g->z_vr[c])) return DOG_ERR_INPUT;
-      }
-    }
-  }
   const cudaMemcpyKind kd = kind_from(mem_kind);
   DOG_CUDA(cudaMemcpyAsync(f->B.zO, g->m_occ, 4 * C, kd, f->st));
   DOG_CUDA(cudaMemcpyAsync(f->B.zF, g->m_free, 4 * C, kd, f->st));
@@ -428,15 +416,17 @@ int dog_set_measurement_grid(dog_filter *f, const dog_meas_grid *g, int mem_kind
     DOG_CUDA(cudaMemcpyAsync(f->B.zv, g->z_vr, 4 * C, kd, f->st));
     DOG_CUDA(cudaMemcpyAsync(f->B.sgv, g->sigma_vr, 4 * C, kd, f->st));
   }
-  if (mem_kind == DOG_DEVICE) {
-    k_validate<<<256, 256, 0, f->st>>>(f->K, f->B, radar ? 1 : 0);
-    DOG_CUDA(cudaGetLastError());
-  } else {
-    DOG_CUDA(cudaStreamSynchronize(f->st));  // the caller may reuse its host arrays
-  }
-  f->has_grid = true;
+  k_validate<<<256, 256, 0, f->st>>>(f->K, f->B, radar ? 1 : 0);
+  DOG_CUDA(cudaGetLastError());
   f->radar = radar;
-  return DOG_OK;
+  if (mem_kind == DOG_DEVICE) {  // asynchronous: a violation is reported by the next sync
+    f->has_grid = true;
+    return DOG_OK;
+  }
+  // host arrays: wait for the copy (the caller may reuse them) and report the validation
+  const int rc = read_err(f);
+  f->has_grid = rc == DOG_OK;
+  return rc;
 }
 
 int dog_step(dog_filter *f, float dt) {

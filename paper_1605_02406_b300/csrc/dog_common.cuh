@@ -18,8 +18,10 @@ struct DevCtl {
   uint32_t n_birth_cells;  // written by the newborn-mass tile scan
   unsigned long long R_total;
   unsigned long long W_total;
-  unsigned long long u_offset;
-  uint32_t pad[8];
+  unsigned long long u_offset;  // systematic resampling offset u in [0, W_total)
+  float w_new;                   // resampled weight (W_total 2^-40) / nu
+  float inv_w;                   // 1 / W_total (binary32 estimate for the source ranges)
+  uint32_t pad[6];
 };
 
 struct KParams {

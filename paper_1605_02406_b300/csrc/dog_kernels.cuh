@@ -569,24 +569,41 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
   const uint32_t tile = blockIdx.x, frame = B.ctl->frame;
   const uint32_t base = tile * SEG_TILE;
   const uint32_t last_valid = min(base + SEG_TILE, P.nu) - 1u;
-  // gather phase, warp-striped: position base + it*256 + threadIdx.x
+  // gather phase, warp-striped: position base + it*256 + threadIdx.x.  All permutation
+  // loads are issued, then all record loads, then the stores, so that a thread keeps
+  // SEG_ITEMS independent gathers in flight.
+  uint32_t gi[SEG_ITEMS];
+#pragma unroll
+  for (int it = 0; it < SEG_ITEMS; ++it) {
+    const uint32_t j = base + it * SEG_BLOCK + threadIdx.x;
+    gi[it] = j < P.nu ? __ldg(B.perm + j) : 0xffffffffu;
+  }
+  float4 st[SEG_ITEMS];
+  float w[SEG_ITEMS];
+#pragma unroll
+  for (int it = 0; it < SEG_ITEMS; ++it) {
+    st[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+    w[it] = 0.0f;
+    if (gi[it] != 0xffffffffu) {
+      st[it] = __ldg(B.As + gi[it]);
+      w[it] = __ldg(B.Aw + gi[it]);
+    }
+  }
 #pragma unroll
   for (int it = 0; it < SEG_ITEMS; ++it) {
     const uint32_t m = it * SEG_BLOCK + threadIdx.x;
     const uint32_t j = base + m;
     unsigned long long q = 0ull, gq = 0ull;
     if (j < P.nu) {
-      const uint32_t i = __ldg(B.perm + j);
-      const float4 st = __ldg(B.As + i);
-      const float w = __ldg(B.Aw + i);
-      const float x = st.x, y = st.y, vx = st.z, vy = st.w;
-      B.Os[j] = st;
-      B.Ow[j] = w;
-      q = q40(w);
+      B.Os[j] = st[it];
+      B.Ow[j] = w[it];
+      q = q40(w[it]);
       if constexpr (RADAR) {
         const uint32_t c = __ldg(B.key_sorted + j);
         if (__ldg(B.pA + c) > 0.0f)
-          gq = q40(__fmul_rn(radar_lik(P, x, y, vx, vy, __ldg(B.zv + c), __ldg(B.sgv + c)), w));
+          gq = q40(__fmul_rn(radar_lik(P, st[it].x, st[it].y, st[it].z, st[it].w, __ldg(B.zv + c),
+                                       __ldg(B.sgv + c)),
+                             w[it]));
       }
     }
     s_q[0][pad8(m)] = q;
@@ -663,10 +680,32 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
 // ====================================================================================
 constexpr int SCAN_BLOCK = 1024;
 
+__device__ __forceinline__ float u64_to_f32_approx(unsigned long long x) {
+  return __fadd_rn(__fmul_rn((float)(uint32_t)(x >> 32), 0x1p32f), (float)(uint32_t)x);
+}
+
+// once per frame, after the CDF total W is known (Alg. 7): the uniform offset
+// u = floor(r64 W / 2^64) from one Philox draw, the resampled weight (W 2^-40) / nu rounded
+// once from binary64, and a binary32 1/W for the source-range estimates
+__device__ void resample_setup(const KParams &P, DevCtl *ctl, unsigned long long Wt) {
+  if ((P.flags & 0x2u) != 0u || Wt == 0ull) {
+    ctl->u_offset = 0ull;
+    ctl->w_new = 0.0f;
+    ctl->inv_w = 0.0f;
+    return;
+  }
+  const U4 r = philox(0u, ctl->frame, TAG_RESAMPLE, P.seed_lo, P.seed_hi);
+  const unsigned long long r64 = ((unsigned long long)r.a << 32) | r.b;
+  ctl->u_offset = __umul64hi(r64, Wt);
+  ctl->w_new = (float)((__ull2double_rn(Wt) * 0x1p-40) / (double)P.nu);
+  ctl->inv_w = __fdiv_rn(1.0f, u64_to_f32_approx(Wt));
+}
+
+template <bool SETUP>
 __global__ void __launch_bounds__(SCAN_BLOCK)
     k_scan_tiles(const unsigned long long *__restrict__ q, const uint32_t *__restrict__ n, uint32_t count,
                  unsigned long long *q_incl, uint32_t *n_incl, unsigned long long *q_total,
-                 uint32_t *n_total) {
+                 uint32_t *n_total, KParams P, DevCtl *ctl) {
   __shared__ unsigned long long s_q[SCAN_BLOCK / 32];
   __shared__ uint32_t s_n[SCAN_BLOCK / 32];
   const uint32_t per = (count + SCAN_BLOCK - 1) / SCAN_BLOCK;
@@ -708,6 +747,7 @@ __global__ void __launch_bounds__(SCAN_BLOCK)
     }
     *q_total = rq;
     if (n_total) *n_total = rn;
+    if constexpr (SETUP) resample_setup(P, ctl, rq);
   }
   __syncthreads();
   unsigned long long rq = s_q[warp] + iq - lq;
@@ -1157,19 +1197,17 @@ __global__ void __launch_bounds__(NORM_BLOCK) k_normalise(KParams P, DevBufs B) 
 
 // ====================================================================================
 // k_resample (Alg. 7, systematic): with joint inclusive fixed-point CDF Q, total W and one
-// uniform offset u in [0, W), output i takes the first source j with Q_j * nu > i W + u
-// (i.e. Q_j > floor((i W + u) / nu)).  A block takes a tile of sources; each source's
-// output range ends at count(Q_j) = #{i : i W + u < Q_j nu}, found from a float estimate
-// and exact 128-bit corrections.  Each output of the tile finds its source by bisection
-// over those ends (u32, shared memory) and copies the source's state from the sorted copy
-// with the equal weight W / nu (Eq. resampledParticleWeights).
+// uniform offset u in [0, W), output i takes the first source j with Q_j * nu > i W + u.
+// A block takes a tile of 2048 sources (8 consecutive per thread).  A thread finds its
+// first output i = #{i : i W + u < E nu} (E = CDF before its first source) from a binary32
+// estimate corrected in exact 128-bit arithmetic, then walks its sources in order with the
+// running value i W + u, handing each output to the source whose Q_j nu first exceeds it --
+// the definition itself, one comparison per output.  The source of each output goes to
+// shared memory, and the block then copies the records in output order (coalesced), with
+// the equal weight W 2^-40 / nu (Eq. resampledParticleWeights).
 // ====================================================================================
 constexpr int RES_BLOCK = 256;
 
-
-__device__ __forceinline__ float u64_to_f32_approx(unsigned long long x) {
-  return __fadd_rn(__fmul_rn((float)(uint32_t)(x >> 32), 0x1p32f), (float)(uint32_t)x);
-}
 
 // #{i in [0, nu) : i W + u < X nu}, exactly
 __device__ __forceinline__ uint32_t count_below(unsigned long long X, unsigned long long Wt,
@@ -1197,11 +1235,27 @@ __device__ __forceinline__ uint32_t count_below(unsigned long long X, unsigned l
   return i;
 }
 
-__global__ void __launch_bounds__(RES_BLOCK) k_resample(KParams P, DevBufs B) {
-  __shared__ uint32_t s_end[NORM_TILE + NORM_TILE / 8];  // output range end of each source
+constexpr int RES_OUT = 8192;  // outputs of a block staged in shared memory
+
+__device__ __forceinline__ void resample_copy(const KParams &P, const DevBufs &B, uint32_t i, uint32_t j,
+                                              float wnew, bool record) {
+  float4 st;
+  if (j < P.nu) {
+    st = __ldg(B.Os + j);
+  } else {
+    const uint32_t b = P.nu_b ? min(j - P.nu, P.nu_b - 1u) : 0u;
+    st = __ldg(B.bs + b);
+  }
+  B.Bs[i] = st;
+  B.Bw[i] = wnew;
+  if (record) B.rsrc[i] = j;
+}
+
+__global__ void __launch_bounds__(RES_BLOCK, 4) k_resample(KParams P, DevBufs B) {
+  __shared__ uint32_t s_src[RES_OUT];  // source of output o_lo + k
   __shared__ unsigned long long s_wsum[RES_BLOCK / 32];
-  __shared__ uint32_t s_lo;
-  const uint32_t tile = blockIdx.x, frame = B.ctl->frame;
+  __shared__ uint32_t s_lo, s_hi;
+  const uint32_t tile = blockIdx.x;
   const uint32_t base = tile * NORM_TILE, ntot = P.nu + P.nu_b;
   const bool record = (P.flags & 0x4u) != 0u;
   const unsigned long long Wt = B.ctl->W_total;
@@ -1213,22 +1267,11 @@ __global__ void __launch_bounds__(RES_BLOCK) k_resample(KParams P, DevBufs B) {
       B.Bw[i] = B.wn[i];
       if (record) B.rsrc[i] = i;
     }
-    if (tile == 0 && threadIdx.x == 0) {
-      B.ctl->W_total = Wt;
-      B.ctl->u_offset = 0ull;
-    }
     return;
   }
-  const U4 r = philox(0u, frame, TAG_RESAMPLE, P.seed_lo, P.seed_hi);
-  const unsigned long long r64 = ((unsigned long long)r.a << 32) | r.b;
-  const unsigned long long u = __umul64hi(r64, Wt);
-  const float wnew = (float)((__ull2double_rn(Wt) * 0x1p-40) / (double)P.nu);
-  const float inv_w = __fdiv_rn(1.0f, u64_to_f32_approx(Wt));
-  if (tile == 0 && threadIdx.x == 0) {
-    B.ctl->W_total = Wt;
-    B.ctl->u_offset = u;
-  }
-  // the tile's quantised weights -> inclusive CDF -> end of each source's output range
+  const unsigned long long u = B.ctl->u_offset;
+  const float wnew = B.ctl->w_new, inv_w = B.ctl->inv_w;
+  // the thread's quantised weights and the CDF before its first source
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t j0 = base + threadIdx.x * NORM_ITEMS;
   float w[NORM_ITEMS];
@@ -1241,9 +1284,12 @@ __global__ void __launch_bounds__(RES_BLOCK) k_resample(KParams P, DevBufs B) {
       w[it] = j < P.nu ? __ldg(B.wn + j) : (j < ntot ? __ldg(B.bw + (j - P.nu)) : 0.0f);
     }
   }
-  unsigned long long loc = 0ull;
+  unsigned long long q[NORM_ITEMS], loc = 0ull;
 #pragma unroll
-  for (int it = 0; it < NORM_ITEMS; ++it) loc += q40(w[it]);
+  for (int it = 0; it < NORM_ITEMS; ++it) {
+    q[it] = q40(w[it]);
+    loc += q[it];
+  }
   unsigned long long inc = loc;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -1252,33 +1298,53 @@ __global__ void __launch_bounds__(RES_BLOCK) k_resample(KParams P, DevBufs B) {
   }
   if (lane == 31) s_wsum[warp] = inc;
   __syncthreads();
-  unsigned long long run = E + inc - loc;
-  for (uint32_t k = 0; k < warp; ++k) run += s_wsum[k];
-  if (threadIdx.x == 0) s_lo = count_below(E, Wt, u, P.nu, inv_w);
+  unsigned long long Q = E + inc - loc;
+  for (uint32_t k = 0; k < warp; ++k) Q += s_wsum[k];
+  // first output of this thread, then the walk over its sources
+  uint32_t i = count_below(Q, Wt, u, P.nu, inv_w);
+  if (threadIdx.x == 0) s_lo = i;
+  __syncthreads();
+  const uint32_t o_lo = s_lo;
+  U128 acc = add_128_64(mul_64x64(i, Wt), u);  // i W + u
 #pragma unroll
   for (int it = 0; it < NORM_ITEMS; ++it) {
-    run += q40(w[it]);
-    s_end[pad8(threadIdx.x * NORM_ITEMS + it)] = count_below(run, Wt, u, P.nu, inv_w);
+    Q += q[it];
+    const U128 lim = mul_64x64(Q, P.nu);
+    const uint32_t j = j0 + it;
+    while (i < P.nu && lt_128(acc, lim)) {
+      if (i - o_lo < (uint32_t)RES_OUT) s_src[i - o_lo] = j;
+      else resample_copy(P, B, i, j, wnew, record);  // beyond the staging buffer
+      ++i;
+      acc = add_128_64(acc, Wt);
+    }
   }
+  if (threadIdx.x == RES_BLOCK - 1) s_hi = i;
   __syncthreads();
-  const uint32_t o_lo = s_lo, o_hi = s_end[pad8(NORM_TILE - 1)];
-  for (uint32_t i = o_lo + threadIdx.x; i < o_hi; i += RES_BLOCK) {
-    uint32_t lo = 0, hi = NORM_TILE - 1;  // first source whose range ends after i
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (s_end[pad8(mid)] > i) hi = mid; else lo = mid + 1;
+  // copy in output order, RES_UNROLL independent gathers in flight per thread
+  constexpr int RES_UNROLL = 8;
+  const uint32_t o_hi = min(s_hi, o_lo + (uint32_t)RES_OUT);
+  for (uint32_t k0 = o_lo; k0 < o_hi; k0 += RES_BLOCK * RES_UNROLL) {
+    uint32_t src[RES_UNROLL];
+    float4 st[RES_UNROLL];
+#pragma unroll
+    for (int r = 0; r < RES_UNROLL; ++r) {
+      const uint32_t k = k0 + r * RES_BLOCK + threadIdx.x;
+      src[r] = k < o_hi ? s_src[k - o_lo] : 0xffffffffu;
     }
-    const uint32_t j = base + lo;
-    float4 st;
-    if (j < P.nu) {
-      st = __ldg(B.Os + j);
-    } else {
-      const uint32_t b = P.nu_b ? min(j - P.nu, P.nu_b - 1u) : 0u;
-      st = __ldg(B.bs + b);
+#pragma unroll
+    for (int r = 0; r < RES_UNROLL; ++r) {
+      const uint32_t j = src[r];
+      if (j == 0xffffffffu) continue;
+      st[r] = j < P.nu ? __ldg(B.Os + j) : __ldg(B.bs + (P.nu_b ? min(j - P.nu, P.nu_b - 1u) : 0u));
     }
-    B.Bs[i] = st;
-    B.Bw[i] = wnew;
-    if (record) B.rsrc[i] = j;
+#pragma unroll
+    for (int r = 0; r < RES_UNROLL; ++r) {
+      const uint32_t k = k0 + r * RES_BLOCK + threadIdx.x;
+      if (src[r] == 0xffffffffu) continue;
+      B.Bs[k] = st[r];
+      B.Bw[k] = wnew;
+      if (record) B.rsrc[k] = src[r];
+    }
   }
 }
 
