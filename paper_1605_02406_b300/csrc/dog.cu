@@ -102,12 +102,12 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
   const size_t CL = (size_t)d.tiles_cell * CELL_TILE;  // per-tile lists of birth cells
   B->bl_cell = (uint32_t *)take(4 * CL);
   B->bl_R = (unsigned long long *)take(8 * CL);
-  B->bl_first = (uint32_t *)take(4 * CL);
-  B->bl_n = (uint32_t *)take(4 * CL);
+  B->bl_first = (uint32_t *)take(4 * (CL + 1));
+  B->bl_gcell = (uint32_t *)take(4 * CL);
   B->bl_nA = (uint32_t *)take(4 * CL);
   B->bl_wA = (float *)take(4 * CL);
   B->bl_wUA = (float *)take(4 * CL);
-  B->tile_first = (uint32_t *)take(4 * ((size_t)d.tiles_cell + 1));
+  B->birth_block_entry = (uint32_t *)take(4 * ((nb + BIRTH_SLOTS - 1) / BIRTH_SLOTS + 1));
   B->hist = (uint32_t *)take(4 * 2048 * (size_t)d.passes);
   B->dcnt = (uint32_t *)take(4 * (size_t)d.passes * d.tiles_sort * d.radix);
   B->S_piece = (unsigned long long *)take(8 * C);
@@ -369,7 +369,8 @@ int dog_create(const dog_params *params, void *d_workspace, size_t workspace_byt
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  f->birth_grid = sms * 4;
+  f->birth_grid = (int)((params->num_birth + BIRTH_SLOTS - 1) / BIRTH_SLOTS);
+  if (f->birth_grid < 1) f->birth_grid = 1;
   const size_t ssm = sort_smem_bytes(d.radix);
   cudaError_t e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
   if (e == cudaSuccess) e = cudaMemsetAsync(f->ws, 0, need, f->st);

@@ -55,9 +55,11 @@ struct DevBufs {
   uint32_t *tag, *cstart, *cend;
   uint32_t *bl_cell;               // [tiles_cell][1024] cells with newborn mass, per tile
   unsigned long long *bl_R;         // [tiles_cell][1024] tile-local inclusive newborn mass
-  uint32_t *bl_first, *bl_n, *bl_nA;  // first slot, slots, associated slots of each entry
-  float *bl_wA, *bl_wUA;              // newborn weights of each entry
-  uint32_t *tile_first;               // [tiles_cell + 1] first slot of each cell tile
+  // all birth cells in cell order (entry G): first slot ([n + 1], last = nu_b), cell,
+  // associated slots and the two newborn weights
+  uint32_t *bl_first, *bl_gcell, *bl_nA;
+  float *bl_wA, *bl_wUA;
+  uint32_t *birth_block_entry;        // [ceil(nu_b / 2048)] entry owning each slot block's first slot
   // scratch of the sort and the tile scans
   uint32_t *hist;                  // [passes][2048] digit histograms
   uint32_t *dcnt;                  // [passes][tiles_sort][radix] digit counts of each sort

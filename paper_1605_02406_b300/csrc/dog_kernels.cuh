@@ -808,25 +808,44 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
   bool has[CELL_ITEMS];
   unsigned long long wq = 0ull;  // running sums of this warp, in cell order
   uint32_t wn = 0u;
+  // all loads of the thread's cells first (independent, in flight together)
+  uint32_t tgs[CELL_ITEMS];
+  float mFs[CELL_ITEMS], zOs[CELL_ITEMS], zFs[CELL_ITEMS];
+  unsigned long long Ss[CELL_ITEMS];
+#pragma unroll
+  for (int it = 0; it < CELL_ITEMS; ++it) {
+    const uint32_t c = tile * CELL_TILE + warp * (32 * CELL_ITEMS) + it * 32 + lane;
+    const bool in = c < P.C;
+    tgs[it] = in ? B.tag[c] : 0u;
+    mFs[it] = in ? B.mF[c] : 0.0f;
+    zOs[it] = in ? B.zO[c] : 0.0f;
+    zFs[it] = in ? B.zF[c] : 0.0f;
+  }
+#pragma unroll
+  for (int it = 0; it < CELL_ITEMS; ++it) {
+    const uint32_t c = tile * CELL_TILE + warp * (32 * CELL_ITEMS) + it * 32 + lane;
+    const bool occ = c < P.C && (tgs[it] >> 1) == frame;
+    Ss[it] = 0ull;
+    if (occ && (tgs[it] & 1u)) {
+      Ss[it] = atomicExch(B.S_piece + c, 0ull);  // all pieces are in; clear for the next frame
+      B.S[c] = Ss[it];
+    } else if (occ) {
+      Ss[it] = B.S[c];
+    }
+  }
 #pragma unroll
   for (int it = 0; it < CELL_ITEMS; ++it) {
     const uint32_t c = tile * CELL_TILE + warp * (32 * CELL_ITEMS) + it * 32 + lane;
     unsigned long long qb = 0ull;
     if (c < P.C) {
-      const uint32_t tg = B.tag[c];
+      const uint32_t tg = tgs[it];
       const bool occ = (tg >> 1) == frame;
       const bool cross = occ && (tg & 1u);
-      unsigned long long S = 0ull;
-      if (cross) {
-        S = atomicExch(B.S_piece + c, 0ull);  // all pieces are in; clear for the next frame
-        B.S[c] = S;
-      } else if (occ) {
-        S = B.S[c];
-      }
+      const unsigned long long S = Ss[it];
       const float Sf = fx40_to_f(S);
       const float mp = fminf(Sf, 1.0f);
       float mO, mF, rb;
-      cell_update(P, mp, B.mF[c], B.zO[c], B.zF[c], mO, mF, rb);
+      cell_update(P, mp, mFs[it], zOs[it], zFs[it], mO, mF, rb);
       const float rp = __fsub_rn(mO, rb);
       B.mpred[c] = mp;
       B.mO[c] = mO;
@@ -949,19 +968,21 @@ __device__ __forceinline__ void birth_init(const KParams &P, const DevBufs &B, u
   }
 }
 
-// k_birth_prep: per birth cell (list entry) its first slot floor(nu_b R_{c-1} / R), slot
-// count, associated count nu_A = round(n p_A) and the two newborn weights; per cell tile
-// its first slot.  One block per cell tile.
+// k_birth_prep: per birth cell (list entry) its first slot floor(nu_b R_{c-1} / R), the
+// associated count nu_A = round(n p_A) and the two newborn weights, written to one list in
+// cell order (entry G = birth cells of earlier tiles + position in the tile); and, for each
+// block of BIRTH_SLOTS slots, the entry that owns the block's first slot.  One block per
+// cell tile.
+constexpr int BIRTH_SLOTS = 2048, BIRTH_CACHE = 2048;
+
 template <bool RADAR>
 __global__ void __launch_bounds__(CELL_BLOCK) k_birth_prep(KParams P, DevBufs B) {
   const unsigned long long R = B.ctl->R_total;
+  if (R == 0ull) return;
   const uint32_t T = blockIdx.x;
   const unsigned long long Tex = T > 0u ? B.tile_qin[T - 1u] : 0ull;
-  if (threadIdx.x == 0) {
-    B.tile_first[T] = R ? floor_muldiv(P.nu_b, Tex, R) : 0u;
-    if (T == P.tiles_cell - 1u) B.tile_first[T + 1u] = P.nu_b;
-  }
-  if (R == 0ull) return;
+  const uint32_t G0 = T > 0u ? B.tile_nin[T - 1u] : 0u;
+  if (T == P.tiles_cell - 1u && threadIdx.x == 0) B.bl_first[B.tile_nin[T]] = P.nu_b;  // sentinel
   const uint32_t cnt = B.tile_n[T];
   for (uint32_t e = threadIdx.x; e < cnt; e += CELL_BLOCK) {
     const size_t pos = (size_t)T * CELL_TILE + e;
@@ -983,54 +1004,91 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_birth_prep(KParams P, DevBufs B)
     } else if (n > 0u) {
       wA = wUA = __fdiv_rn(rb, (float)n);
     }
-    B.bl_first[pos] = first;
-    B.bl_n[pos] = n;
-    B.bl_nA[pos] = nA;
-    B.bl_wA[pos] = wA;
-    B.bl_wUA[pos] = wUA;
+    const uint32_t G = G0 + e;
+    B.bl_first[G] = first;
+    B.bl_gcell[G] = c;
+    B.bl_nA[G] = nA;
+    B.bl_wA[G] = wA;
+    B.bl_wUA[G] = wUA;
+    // slot blocks whose first slot lies in [first, last)
+    for (uint32_t blk = (first + BIRTH_SLOTS - 1u) / BIRTH_SLOTS; blk * BIRTH_SLOTS < last; ++blk)
+      B.birth_block_entry[blk] = G;
   }
 }
 
-// k_birth: one thread per newborn slot; its cell tile and then its cell are found by
-// bisection over the first slots prepared by k_birth_prep.
+// k_birth: a block makes the newborns of BIRTH_SLOTS consecutive slots.  It starts from the
+// entry that owns its first slot, caches the first slots of the following entries in shared
+// memory, and each slot finds its entry (the last one whose first slot is <= the slot) by
+// bisection there.
 template <bool RADAR>
 __global__ void __launch_bounds__(BIRTH_BLOCK) k_birth(KParams P, DevBufs B) {
+  __shared__ uint32_t s_first[BIRTH_CACHE + 1];
   const uint32_t frame = B.ctl->frame;
   const unsigned long long R = B.ctl->R_total;
   const bool record = (P.flags & 0x4u) != 0u;
-  const uint32_t stride = gridDim.x * BIRTH_BLOCK;
+  const uint32_t s0 = blockIdx.x * BIRTH_SLOTS;
+  const uint32_t s1 = min(s0 + BIRTH_SLOTS, P.nu_b);
+  if (s0 >= s1) return;  // block-uniform (no newborn slots at all)
   if (R == 0ull) {
     // no newborn mass anywhere: weight 0, cell = slot mod C
-    for (uint32_t s = blockIdx.x * BIRTH_BLOCK + threadIdx.x; s < P.nu_b; s += stride)
+    for (uint32_t s = s0 + threadIdx.x; s < s1; s += BIRTH_BLOCK)
       birth_init(P, B, s, s % P.C, false, 0.0f, 0.0f, 1.0f, frame, record);
     return;
   }
-  for (uint32_t s = blockIdx.x * BIRTH_BLOCK + threadIdx.x; s < P.nu_b; s += stride) {
-    // the cell tile: first T whose slots end after s (tile_first[T + 1] > s)
-    uint32_t lo = 0, hi = P.tiles_cell - 1u;
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (__ldg(B.tile_first + mid + 1u) > s) hi = mid; else lo = mid + 1u;
+  const uint32_t nE = B.ctl->n_birth_cells;
+  const uint32_t G0 = B.birth_block_entry[blockIdx.x];
+  const uint32_t ncache = min((uint32_t)BIRTH_CACHE, nE - G0);  // entries G0 .. G0 + ncache - 1
+  for (uint32_t k = threadIdx.x; k <= ncache; k += BIRTH_BLOCK) s_first[k] = __ldg(B.bl_first + G0 + k);
+  __syncthreads();
+  const uint32_t cached_end = s_first[ncache];  // first slot after the cached entries
+  // entry of each of the thread's slots, then all entry gathers, then the draws
+  constexpr int PER = BIRTH_SLOTS / BIRTH_BLOCK;
+  uint32_t G[PER];
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const uint32_t s = s0 + r * BIRTH_BLOCK + threadIdx.x;
+    G[r] = 0u;
+    if (s >= s1) continue;
+    if (s < cached_end) {
+      uint32_t a = 0, b = ncache - 1u;
+      while (a < b) {
+        const uint32_t mid = (a + b + 1u) >> 1;
+        if (s_first[mid] <= s) a = mid; else b = mid - 1u;
+      }
+      G[r] = G0 + a;
+    } else {  // beyond the cache (many entries without slots in this block): global bisection
+      uint32_t a = G0 + ncache, b = nE - 1u;
+      while (a < b) {
+        const uint32_t mid = (a + b + 1u) >> 1;
+        if (__ldg(B.bl_first + mid) <= s) a = mid; else b = mid - 1u;
+      }
+      G[r] = a;
     }
-    const size_t tb = (size_t)lo * CELL_TILE;
-    // the cell: the last entry whose first slot is <= s
-    uint32_t a = 0, b = __ldg(B.tile_n + lo);
-    b = b > 0u ? b - 1u : 0u;
-    while (a < b) {
-      const uint32_t mid = (a + b + 1u) >> 1;
-      if (__ldg(B.bl_first + tb + mid) <= s) a = mid; else b = mid - 1u;
-    }
-    const size_t pos = tb + a;
-    const uint32_t c = __ldg(B.bl_cell + pos);
-    const uint32_t t = s - __ldg(B.bl_first + pos);
-    const bool assoc = t < __ldg(B.bl_nA + pos);
-    const float w = assoc ? __ldg(B.bl_wA + pos) : __ldg(B.bl_wUA + pos);
-    float zv = 0.0f, sg = 1.0f;
+  }
+  uint32_t cell[PER];
+  bool assoc[PER];
+  float wb[PER], zv[PER], sg[PER];
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const uint32_t s = s0 + r * BIRTH_BLOCK + threadIdx.x;
+    cell[r] = 0u;
+    assoc[r] = false;
+    wb[r] = 0.0f;
+    zv[r] = 0.0f;
+    sg[r] = 1.0f;
+    if (s >= s1) continue;
+    cell[r] = __ldg(B.bl_gcell + G[r]);
+    assoc[r] = s - __ldg(B.bl_first + G[r]) < __ldg(B.bl_nA + G[r]);
+    wb[r] = assoc[r] ? __ldg(B.bl_wA + G[r]) : __ldg(B.bl_wUA + G[r]);
     if constexpr (RADAR) {
-      zv = __ldg(B.zv + c);
-      sg = __ldg(B.sgv + c);
+      zv[r] = __ldg(B.zv + cell[r]);
+      sg[r] = __ldg(B.sgv + cell[r]);
     }
-    birth_init(P, B, s, c, assoc, w, zv, sg, frame, record);
+  }
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const uint32_t s = s0 + r * BIRTH_BLOCK + threadIdx.x;
+    if (s < s1) birth_init(P, B, s, cell[r], assoc[r], wb[r], zv[r], sg[r], frame, record);
   }
 }
 
@@ -1068,7 +1126,7 @@ __device__ __forceinline__ void moments_store(const DevBufs &B, uint32_t c, cons
 }
 
 template <bool RADAR>
-__global__ void __launch_bounds__(NORM_BLOCK) k_normalise(KParams P, DevBufs B) {
+__global__ void __launch_bounds__(NORM_BLOCK, 4) k_normalise(KParams P, DevBufs B) {
   __shared__ Seg<5, float> s_w[NORM_BLOCK / 32 + 1];
   __shared__ unsigned long long s_red[NORM_BLOCK / 32];
   const uint32_t tile = blockIdx.x;
@@ -1097,6 +1155,14 @@ __global__ void __launch_bounds__(NORM_BLOCK) k_normalise(KParams P, DevBufs B) 
     }
     const uint32_t kprev = (j0 > 0 && j0 <= P.nu) ? __ldg(B.key_sorted + j0 - 1) : 0xfffffffeu;
     const uint32_t knext = (j0 + NORM_ITEMS < P.nu) ? __ldg(B.key_sorted + j0 + NORM_ITEMS) : 0xfffffffeu;
+    // per-cell factors of all items before any arithmetic (independent loads in flight)
+    float cmu[NORM_ITEMS], crinv[NORM_ITEMS];
+#pragma unroll
+    for (int it = 0; it < NORM_ITEMS; ++it) {
+      const bool ok = j0 + it < P.nu;
+      cmu[it] = ok ? __ldg(B.muU + key[it]) : 0.0f;
+      crinv[it] = ok ? __ldg(B.rinv + key[it]) : 0.0f;
+    }
     float wn_out[NORM_ITEMS];
 #pragma unroll
     for (int it = 0; it < NORM_ITEMS; ++it) {
@@ -1113,7 +1179,7 @@ __global__ void __launch_bounds__(NORM_BLOCK) k_normalise(KParams P, DevBufs B) 
       if (ok) {
         const uint32_t c = key[it];
         const float w = ws[it];
-        const float muU = __ldg(B.muU + c);
+        const float muU = cmu[it];
         float wn;
         const float pa = RADAR ? __ldg(B.paeff + c) : 0.0f;
         if (RADAR && pa > 0.0f) {
@@ -1127,7 +1193,7 @@ __global__ void __launch_bounds__(NORM_BLOCK) k_normalise(KParams P, DevBufs B) 
         }
         wn_out[it] = wn;
         qsum += q40(wn);
-        mu[it] = __fmul_rn(wn, __ldg(B.rinv + c));
+        mu[it] = __fmul_rn(wn, crinv[it]);
       }
       Seg<5, float> e;
       e.f = h;
