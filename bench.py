@@ -39,7 +39,7 @@ CFG_ID = "automotive_1024"
 # algorithmic bytes per launch of each kernel: (bytes per persistent particle, per newborn
 # slot, per cell): the unique bytes each kernel must move, one read or write per datum
 ALG_BYTES = {
-    "k_predict": (44, 0, 0),      # read state 16 + weight 4; write both + cell index 4
+    "k_predict": (44, 0, 0),      # read source index 4 + its record 16; write record, w, key
     "k_sort_pass0": (12, 0, 0),   # read cell index 4; write (index, particle) pair 8
     "k_sort_pass1": (16, 0, 0),   # read pair 8; write pair 8
     "k_sort_pass2": (16, 0, 0),
@@ -47,7 +47,7 @@ ALG_BYTES = {
     "k_cell": (0, 0, 60),         # read S 8, tag 4, m_F 4, z_O 4, z_F 4; write 9 cell fields
     "k_birth": (0, 20, 0),        # write newborn state 16 + weight 4
     "k_normalise": (28, 4, 0),    # read key 4, w 4, state 16, write w' 4; newborn w 4
-    "k_resample": (40, 4, 0),     # read w' 4, selected state 16; write state 16 + weight 4
+    "k_resample": (8, 4, 0),      # read w' 4; write the source index 4; newborn w 4
     "k_tick": (0, 0, 0),
 }
 

@@ -47,7 +47,7 @@ typedef enum dog_status {
 
 /* dog_params.flags */
 #define DOG_NO_RESAMPLE 0x2u /* keep the normalised persistent particles (test mode)     */
-#define DOG_RECORD 0x4u      /* also keep newborn cells/flags and resample sources       */
+#define DOG_RECORD 0x4u      /* also keep the cell and set of every newborn slot         */
 #define DOG_NO_GRAPH 0x8u    /* issue kernels one by one instead of a captured graph     */
 #define DOG_PROFILE 0x10u    /* time each kernel with CUDA events (dog_profile_read)      */
 
@@ -159,7 +159,7 @@ int dog_sync(dog_filter *f);
  *   DOG_DBG_BIRTH_X..BIRTH_W float [nu_b] newborn particles (Alg. 5)
  *   DOG_DBG_BIRTH_CELL       u32   [nu_b] (DOG_RECORD only)
  *   DOG_DBG_BIRTH_ASSOC      u32   [nu_b] 1 = associated set (DOG_RECORD only)
- *   DOG_DBG_RESAMPLE_SRC     u32   [nu]  joint source index of each output (DOG_RECORD)
+ *   DOG_DBG_RESAMPLE_SRC     u32   [nu]  joint source index of each posterior particle
  *   DOG_DBG_SCALARS          u64   [4]   frame, total weight, total birth mass, offset u
  * Errors: INVALID_ARG (unknown which), BAD_STATE (needs DOG_RECORD). */
 enum {

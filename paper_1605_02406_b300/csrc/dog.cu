@@ -70,8 +70,10 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
   const size_t nu = p.num_particles, nb = p.num_birth, C = d.C;
   const bool record = (p.flags & DOG_RECORD) != 0;
   B->ctl = (DevCtl *)take(sizeof(DevCtl));
-  float4 **ps[] = {&B->Bs, &B->As, &B->Os};
+  float4 **ps[] = {&B->As, &B->Os};
   for (auto q : ps) *q = (float4 *)take(16 * nu);
+  B->Bsrc = (uint32_t *)take(4 * nu);
+  B->stage = (float4 *)take(16 * (nu > nb ? nu : nb));
   float **pf[] = {&B->Bw, &B->Aw, &B->Ow, &B->wn};
   for (auto q : pf) *q = (float *)take(4 * nu);
   uint32_t **pu[] = {&B->key_pred, &B->key_sorted, &B->perm};
@@ -85,7 +87,6 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
     B->key_t1 = (uint32_t *)take(4 * nu);
     B->val_t1 = (uint32_t *)take(4 * nu);
   }
-  B->rsrc = record ? (uint32_t *)take(4 * nu) : nullptr;
   B->bs = (float4 *)take(16 * (nb ? nb : 1));
   B->bw = (float *)take(4 * (nb ? nb : 1));
   B->bcell = record ? (uint32_t *)take(4 * (nb ? nb : 1)) : nullptr;
@@ -260,26 +261,19 @@ int reset_epochs(dog_filter *f) {
   return DOG_OK;
 }
 
-// Records (x, y, vx, vy) <-> four plain float arrays, staged through the sorted-copy buffer
-// Os (16 bytes per particle, idle between steps).  Records of newborn slots use the same
-// buffer when it is large enough, else strided copies.
+// Records (x, y, vx, vy) <-> four plain float arrays, through the staging buffer
+// (16 bytes per particle or newborn slot).
 int unpack_records(dog_filter *f, const float4 *rec, size_t n, float *const dst[4], cudaMemcpyKind kd) {
   if (n == 0) return DOG_OK;
-  if (n <= f->p.num_particles) {
-    float *scr = reinterpret_cast<float *>(f->B.Os);
-    k_unpack<<<1024, 256, 0, f->st>>>(rec, (uint32_t)n, scr);
-    DOG_CUDA(cudaGetLastError());
-    for (int k = 0; k < 4; ++k)
-      if (dst[k]) DOG_CUDA(cudaMemcpyAsync(dst[k], scr + k * n, 4 * n, kd, f->st));
-  } else {
-    for (int k = 0; k < 4; ++k)
-      if (dst[k])
-        DOG_CUDA(cudaMemcpy2DAsync(dst[k], 4, reinterpret_cast<const float *>(rec) + k, 16, 4, n, kd, f->st));
-  }
+  float *scr = reinterpret_cast<float *>(f->B.stage);
+  k_unpack<<<1024, 256, 0, f->st>>>(rec, (uint32_t)n, scr);
+  DOG_CUDA(cudaGetLastError());
+  for (int k = 0; k < 4; ++k)
+    if (dst[k]) DOG_CUDA(cudaMemcpyAsync(dst[k], scr + k * n, 4 * n, kd, f->st));
   return DOG_OK;
 }
 int pack_records(dog_filter *f, float4 *rec, size_t n, const float *const src[4], cudaMemcpyKind kd) {
-  float *scr = reinterpret_cast<float *>(f->B.Os);
+  float *scr = reinterpret_cast<float *>(f->B.stage);
   for (int k = 0; k < 4; ++k) DOG_CUDA(cudaMemcpyAsync(scr + k * n, src[k], 4 * n, kd, f->st));
   k_pack<<<1024, 256, 0, f->st>>>(scr, (uint32_t)n, rec);
   DOG_CUDA(cudaGetLastError());
@@ -493,9 +487,14 @@ int dog_get_state(dog_filter *f, const dog_state *out, int mem_kind, uint32_t *f
   const size_t n = 4 * (size_t)f->p.num_particles;
   const cudaMemcpyKind kd = kind_to(mem_kind);
   float *const dst[4] = {out->x, out->y, out->vx, out->vy};
-  const int rc0 = unpack_records(f, f->B.Bs, f->p.num_particles, dst, kd);
-  if (rc0) return rc0;
-  if (out->w) DOG_CUDA(cudaMemcpyAsync(out->w, f->B.Bw, n, kd, f->st));
+  // posterior as plain arrays in the staging buffer (x, y, vx, vy) and Aw (weights; both
+  // idle between steps)
+  float *scr = reinterpret_cast<float *>(f->B.stage);
+  k_gather_posterior<<<1024, 256, 0, f->st>>>(f->K, f->B, scr, f->B.Aw);
+  DOG_CUDA(cudaGetLastError());
+  for (int k = 0; k < 4; ++k)
+    if (dst[k]) DOG_CUDA(cudaMemcpyAsync(dst[k], scr + k * (size_t)f->p.num_particles, n, kd, f->st));
+  if (out->w) DOG_CUDA(cudaMemcpyAsync(out->w, f->B.Aw, n, kd, f->st));
   if (out->m_free) DOG_CUDA(cudaMemcpyAsync(out->m_free, f->B.mF, 4 * (size_t)f->d.C, kd, f->st));
   const int rc = read_err(f);
   if (frame) *frame = f->frame;
@@ -509,9 +508,12 @@ int dog_set_state(dog_filter *f, const dog_state *in, int mem_kind, uint32_t fra
   const size_t n = 4 * (size_t)f->p.num_particles;
   const cudaMemcpyKind kd = kind_from(mem_kind);
   const float *const src[4] = {in->x, in->y, in->vx, in->vy};
-  const int rc0 = pack_records(f, f->B.Bs, f->p.num_particles, src, kd);
+  // the restored posterior is held directly: records in Os, weights in Bw
+  const int rc0 = pack_records(f, f->B.Os, f->p.num_particles, src, kd);
   if (rc0) return rc0;
   DOG_CUDA(cudaMemcpyAsync(f->B.Bw, in->w, n, kd, f->st));
+  const uint32_t direct = POST_DIRECT;
+  DOG_CUDA(cudaMemcpyAsync(&f->B.ctl->post_mode, &direct, 4, cudaMemcpyHostToDevice, f->st));
   DOG_CUDA(cudaMemcpyAsync(f->B.mF, in->m_free, 4 * (size_t)f->d.C, kd, f->st));
   const int rc = reset_epochs(f);
   if (rc) return rc;
@@ -557,11 +559,11 @@ int dog_get_debug(dog_filter *f, int which, void *out, int mem_kind) {
     case DOG_DBG_BIRTH_W: src = B.bw; bytes = 4 * nb; break;
     case DOG_DBG_BIRTH_CELL: src = B.bcell; bytes = 4 * nb; break;
     case DOG_DBG_BIRTH_ASSOC: src = B.bassoc; bytes = 4 * nb; break;
-    case DOG_DBG_RESAMPLE_SRC: src = B.rsrc; bytes = 4 * nu; break;
+    case DOG_DBG_RESAMPLE_SRC: src = B.Bsrc; bytes = 4 * nu; break;
     case DOG_DBG_SCALARS: break;
     default: return DOG_ERR_INVALID_ARG;
   }
-  if ((which == DOG_DBG_BIRTH_CELL || which == DOG_DBG_BIRTH_ASSOC || which == DOG_DBG_RESAMPLE_SRC) && !record)
+  if ((which == DOG_DBG_BIRTH_CELL || which == DOG_DBG_BIRTH_ASSOC) && !record)
     return DOG_ERR_BAD_STATE;
   DOG_CUDA(cudaStreamSynchronize(f->st));
   if (which == DOG_DBG_SCALARS) {

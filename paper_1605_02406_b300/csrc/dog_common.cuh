@@ -21,8 +21,17 @@ struct DevCtl {
   unsigned long long u_offset;  // systematic resampling offset u in [0, W_total)
   float w_new;                   // resampled weight (W_total 2^-40) / nu
   float inv_w;                   // 1 / W_total (binary32 estimate for the source ranges)
-  uint32_t pad[6];
+  uint32_t post_mode;            // posterior held as POST_RESAMPLED or POST_DIRECT
+  uint32_t pad[5];
 };
+
+// How the posterior particles are held between frames:
+//   POST_RESAMPLED: particle i is the record of joint source Bsrc[i] (the sorted copy Os
+//                   for a persistent source, the newborn records bs for a newborn one) and
+//                   every weight is DevCtl::w_new;
+//   POST_DIRECT:    particle i is Os[i] with weight Bw[i] (initial state, a restored
+//                   checkpoint, or a frame without resampling).
+enum : uint32_t { POST_RESAMPLED = 0, POST_DIRECT = 1 };
 
 struct KParams {
   int W, H;
@@ -39,12 +48,14 @@ struct KParams {
 struct DevBufs {
   DevCtl *ctl;
   // particle states are (x, y, vx, vy) records with the weight in a separate array:
-  // posterior (B), predicted (A), predicted in sorted cell order (O), newborn (b)
-  float4 *Bs, *As, *Os, *bs;
+  // predicted (A), predicted in sorted cell order (O), newborn (b); the posterior is
+  // Bsrc / Bw over O and b (see post_mode)
+  float4 *As, *Os, *bs;
   float *Bw, *Aw, *Ow, *bw;
+  uint32_t *Bsrc;  // [nu] joint source of each posterior particle
+  float4 *stage;   // [max(nu, nu_b)] staging for checkpoints and diagnostics
   uint32_t *key_pred, *key_t0, *val_t0, *key_t1, *val_t1, *key_sorted, *perm;
   float *wn;
-  uint32_t *rsrc;  // record only
   uint32_t *bcell, *bassoc;  // newborn cells and association flags (record only)
   // cells
   float *mF;

@@ -43,11 +43,34 @@ __global__ void k_init(KParams P, DevBufs B) {
     const U4 r = philox(i, 0u, TAG_INIT, P.seed_lo, P.seed_hi);
     float n0, n1;
     gauss2(r.c, r.d, n0, n1);
-    B.Bs[i] = make_float4(__fmul_rn(u01_co(r.a), gx), __fmul_rn(u01_co(r.b), gy),
+    B.Os[i] = make_float4(__fmul_rn(u01_co(r.a), gx), __fmul_rn(u01_co(r.b), gy),
                           __fmul_rn(P.sigma_B, n0), __fmul_rn(P.sigma_B, n1));
     B.Bw[i] = 0.0f;
   }
   for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < P.C; c += stride) B.mF[c] = 0.0f;
+  if (blockIdx.x == 0 && threadIdx.x == 0) B.ctl->post_mode = POST_DIRECT;
+}
+
+// posterior particle i (record and weight) under either post_mode
+__device__ __forceinline__ float4 posterior_record(const KParams &P, const DevBufs &B, uint32_t mode,
+                                                   uint32_t i) {
+  if (mode == POST_DIRECT) return __ldg(B.Os + i);
+  const uint32_t j = __ldg(B.Bsrc + i);
+  return j < P.nu ? __ldg(B.Os + j) : __ldg(B.bs + (j - P.nu));
+}
+
+// posterior state as plain arrays: out[0..3][i] = x, y, vx, vy and w[i] (checkpoints)
+__global__ void k_gather_posterior(KParams P, DevBufs B, float *__restrict__ out, float *__restrict__ w) {
+  const uint32_t mode = B.ctl->post_mode;
+  const float wn = B.ctl->w_new;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P.nu; i += gridDim.x * blockDim.x) {
+    const float4 r = posterior_record(P, B, mode, i);
+    out[i] = r.x;
+    out[P.nu + i] = r.y;
+    out[2 * (size_t)P.nu + i] = r.z;
+    out[3 * (size_t)P.nu + i] = r.w;
+    w[i] = mode == POST_DIRECT ? B.Bw[i] : wn;
+  }
 }
 
 // ====================================================================================
@@ -122,14 +145,26 @@ __global__ void __launch_bounds__(PRED_BLOCK) k_predict(KParams P, DevBufs B) {
   __syncthreads();
   const uint32_t frame = B.ctl->frame;
   const float T = B.ctl->dt;
+  const uint32_t mode = B.ctl->post_mode;
+  const float w_res = B.ctl->w_new;
   const uint32_t mask = P.radix - 1u;
   for (int rnd = 0; rnd < PRED_ROUNDS; ++rnd) {
     const uint32_t i0 = blockIdx.x * PRED_TILE + (uint32_t)rnd * (PRED_BLOCK * 4) + threadIdx.x * 4;
     uint32_t key[4];
     bool valid[4];
     if (i0 + 4 <= P.nu) {
-      float4 s0 = B.Bs[i0], s1 = B.Bs[i0 + 1], s2 = B.Bs[i0 + 2], s3 = B.Bs[i0 + 3];
-      float4 w = *reinterpret_cast<const float4 *>(B.Bw + i0);
+      float4 s0, s1, s2, s3, w;
+      if (mode == POST_DIRECT) {
+        s0 = B.Os[i0]; s1 = B.Os[i0 + 1]; s2 = B.Os[i0 + 2]; s3 = B.Os[i0 + 3];
+        w = *reinterpret_cast<const float4 *>(B.Bw + i0);
+      } else {  // the records of the four particles' sources; equal weights
+        const uint4 j = *reinterpret_cast<const uint4 *>(B.Bsrc + i0);
+        s0 = j.x < P.nu ? B.Os[j.x] : B.bs[j.x - P.nu];
+        s1 = j.y < P.nu ? B.Os[j.y] : B.bs[j.y - P.nu];
+        s2 = j.z < P.nu ? B.Os[j.z] : B.bs[j.z - P.nu];
+        s3 = j.w < P.nu ? B.Os[j.w] : B.bs[j.w - P.nu];
+        w = make_float4(w_res, w_res, w_res, w_res);
+      }
       predict_one(P, i0 + 0, frame, T, s0, w.x, key[0]);
       predict_one(P, i0 + 1, frame, T, s1, w.y, key[1]);
       predict_one(P, i0 + 2, frame, T, s2, w.z, key[2]);
@@ -148,8 +183,8 @@ __global__ void __launch_bounds__(PRED_BLOCK) k_predict(KParams P, DevBufs B) {
         valid[k] = i < P.nu;
         key[k] = 0u;
         if (valid[k]) {
-          float4 s = B.Bs[i];
-          float w = B.Bw[i];
+          float4 s = posterior_record(P, B, mode, i);
+          float w = mode == POST_DIRECT ? B.Bw[i] : w_res;
           predict_one(P, i, frame, T, s, w, key[k]);
           B.As[i] = s;
           B.Aw[i] = w;
@@ -692,8 +727,10 @@ __device__ void resample_setup(const KParams &P, DevCtl *ctl, unsigned long long
     ctl->u_offset = 0ull;
     ctl->w_new = 0.0f;
     ctl->inv_w = 0.0f;
+    ctl->post_mode = POST_DIRECT;
     return;
   }
+  ctl->post_mode = POST_RESAMPLED;
   const U4 r = philox(0u, ctl->frame, TAG_RESAMPLE, P.seed_lo, P.seed_hi);
   const unsigned long long r64 = ((unsigned long long)r.a << 32) | r.b;
   ctl->u_offset = __umul64hi(r64, Wt);
@@ -1269,8 +1306,9 @@ __global__ void __launch_bounds__(NORM_BLOCK, 4) k_normalise(KParams P, DevBufs 
 // estimate corrected in exact 128-bit arithmetic, then walks its sources in order with the
 // running value i W + u, handing each output to the source whose Q_j nu first exceeds it --
 // the definition itself, one comparison per output.  The source of each output goes to
-// shared memory, and the block then copies the records in output order (coalesced), with
-// the equal weight W 2^-40 / nu (Eq. resampledParticleWeights).
+// shared memory and then to Bsrc in output order (coalesced): posterior particle i is the
+// record of source Bsrc[i] with the equal weight W 2^-40 / nu (Eq.
+// resampledParticleWeights), which the next prediction reads through the index.
 // ====================================================================================
 constexpr int RES_BLOCK = 256;
 
@@ -1303,40 +1341,24 @@ __device__ __forceinline__ uint32_t count_below(unsigned long long X, unsigned l
 
 constexpr int RES_OUT = 8192;  // outputs of a block staged in shared memory
 
-__device__ __forceinline__ void resample_copy(const KParams &P, const DevBufs &B, uint32_t i, uint32_t j,
-                                              float wnew, bool record) {
-  float4 st;
-  if (j < P.nu) {
-    st = __ldg(B.Os + j);
-  } else {
-    const uint32_t b = P.nu_b ? min(j - P.nu, P.nu_b - 1u) : 0u;
-    st = __ldg(B.bs + b);
-  }
-  B.Bs[i] = st;
-  B.Bw[i] = wnew;
-  if (record) B.rsrc[i] = j;
-}
-
 __global__ void __launch_bounds__(RES_BLOCK, 4) k_resample(KParams P, DevBufs B) {
   __shared__ uint32_t s_src[RES_OUT];  // source of output o_lo + k
   __shared__ unsigned long long s_wsum[RES_BLOCK / 32];
   __shared__ uint32_t s_lo, s_hi;
   const uint32_t tile = blockIdx.x;
   const uint32_t base = tile * NORM_TILE, ntot = P.nu + P.nu_b;
-  const bool record = (P.flags & 0x4u) != 0u;
   const unsigned long long Wt = B.ctl->W_total;
   const unsigned long long E = tile > 0 ? B.cdf_incl[tile - 1] : 0ull;
   if ((P.flags & 0x2u) != 0u || Wt == 0ull) {
-    // no resampling: the persistent particles carry over in sorted order
+    // no resampling: the persistent particles carry over in sorted order (POST_DIRECT)
     for (uint32_t i = base + threadIdx.x; i < min(base + NORM_TILE, P.nu); i += RES_BLOCK) {
-      B.Bs[i] = B.Os[i];
       B.Bw[i] = B.wn[i];
-      if (record) B.rsrc[i] = i;
+      B.Bsrc[i] = i;
     }
     return;
   }
   const unsigned long long u = B.ctl->u_offset;
-  const float wnew = B.ctl->w_new, inv_w = B.ctl->inv_w;
+  const float inv_w = B.ctl->inv_w;
   // the thread's quantised weights and the CDF before its first source
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t j0 = base + threadIdx.x * NORM_ITEMS;
@@ -1379,39 +1401,16 @@ __global__ void __launch_bounds__(RES_BLOCK, 4) k_resample(KParams P, DevBufs B)
     const uint32_t j = j0 + it;
     while (i < P.nu && lt_128(acc, lim)) {
       if (i - o_lo < (uint32_t)RES_OUT) s_src[i - o_lo] = j;
-      else resample_copy(P, B, i, j, wnew, record);  // beyond the staging buffer
+      else B.Bsrc[i] = j;  // beyond the staging buffer
       ++i;
       acc = add_128_64(acc, Wt);
     }
   }
   if (threadIdx.x == RES_BLOCK - 1) s_hi = i;
   __syncthreads();
-  // copy in output order, RES_UNROLL independent gathers in flight per thread
-  constexpr int RES_UNROLL = 8;
+  // sources in output order (coalesced)
   const uint32_t o_hi = min(s_hi, o_lo + (uint32_t)RES_OUT);
-  for (uint32_t k0 = o_lo; k0 < o_hi; k0 += RES_BLOCK * RES_UNROLL) {
-    uint32_t src[RES_UNROLL];
-    float4 st[RES_UNROLL];
-#pragma unroll
-    for (int r = 0; r < RES_UNROLL; ++r) {
-      const uint32_t k = k0 + r * RES_BLOCK + threadIdx.x;
-      src[r] = k < o_hi ? s_src[k - o_lo] : 0xffffffffu;
-    }
-#pragma unroll
-    for (int r = 0; r < RES_UNROLL; ++r) {
-      const uint32_t j = src[r];
-      if (j == 0xffffffffu) continue;
-      st[r] = j < P.nu ? __ldg(B.Os + j) : __ldg(B.bs + (P.nu_b ? min(j - P.nu, P.nu_b - 1u) : 0u));
-    }
-#pragma unroll
-    for (int r = 0; r < RES_UNROLL; ++r) {
-      const uint32_t k = k0 + r * RES_BLOCK + threadIdx.x;
-      if (src[r] == 0xffffffffu) continue;
-      B.Bs[k] = st[r];
-      B.Bw[k] = wnew;
-      if (record) B.rsrc[k] = src[r];
-    }
-  }
+  for (uint32_t k = o_lo + threadIdx.x; k < o_hi; k += RES_BLOCK) B.Bsrc[k] = s_src[k - o_lo];
 }
 
 }  // namespace dog
