@@ -209,7 +209,7 @@ int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
     ++k; mark();
   }
   if (radar) k_segsum<true><<<K.tiles_seg, SEG_BLOCK, 0, st>>>(K, B);
-  else k_segsum<false><<<K.tiles_seg, SEG_BLOCK, 0, st>>>(K, B);
+  else k_segsum_lidar<<<K.tiles_seg, SEG_BLOCK, 0, st>>>(K, B);
   ++k; mark();
   if (radar) k_cell<true><<<K.tiles_cell, CELL_BLOCK, 0, st>>>(K, B);
   else k_cell<false><<<K.tiles_cell, CELL_BLOCK, 0, st>>>(K, B);
@@ -224,7 +224,7 @@ int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
   else k_birth<false><<<f->birth_grid, BIRTH_BLOCK, 0, st>>>(K, B);
   ++k; mark();
   if (radar) k_normalise<true><<<K.tiles_norm, NORM_BLOCK, 0, st>>>(K, B);
-  else k_normalise<false><<<K.tiles_norm, NORM_BLOCK, 0, st>>>(K, B);
+  else k_normalise_lidar<<<K.tiles_norm, NORM_BLOCK, 0, st>>>(K, B);
   ++k; mark();
   k_scan_tiles<true><<<1, SCAN_BLOCK, 0, st>>>(B.cdf_tile, nullptr, K.tiles_norm, B.cdf_incl, nullptr,
                                                 &B.ctl->W_total, nullptr, K, B.ctl);

@@ -502,36 +502,69 @@ __device__ __forceinline__ Seg<N, V> seg_shfl_up(const Seg<N, V> &a, int o) {
   return r;
 }
 
-// Block-wide exclusive segmented scan of per-thread aggregates (SEG_BLOCK threads).
 template <int N, typename V>
-__device__ Seg<N, V> block_seg_excl(const Seg<N, V> &x, Seg<N, V> *s_w /* [SEG_BLOCK/32 + 1] */) {
+__device__ __forceinline__ Seg<N, V> seg_zero(const Seg<N, V> &) {
+  Seg<N, V> r;
+  r.f = 0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.v[k] = V(0);
+  return r;
+}
+
+// a fixed-point weight sum and five binary32 moment sums under one head flag
+struct SegQM {
+  uint32_t f;
+  unsigned long long q;
+  float m[5];
+};
+__device__ __forceinline__ SegQM seg_combine(const SegQM &a, const SegQM &b) {
+  SegQM r;
+  r.f = a.f | b.f;
+  r.q = b.f ? b.q : a.q + b.q;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) r.m[k] = b.f ? b.m[k] : __fadd_rn(a.m[k], b.m[k]);
+  return r;
+}
+__device__ __forceinline__ SegQM seg_shfl_up(const SegQM &a, int o) {
+  SegQM r;
+  r.f = __shfl_up_sync(FULL, a.f, o);
+  r.q = __shfl_up_sync(FULL, a.q, o);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) r.m[k] = __shfl_up_sync(FULL, a.m[k], o);
+  return r;
+}
+__device__ __forceinline__ SegQM seg_zero(const SegQM &) {
+  SegQM r;
+  r.f = 0;
+  r.q = 0ull;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) r.m[k] = 0.0f;
+  return r;
+}
+
+// Block-wide exclusive segmented scan of per-thread aggregates (SEG_BLOCK threads).
+template <typename S>
+__device__ S block_seg_excl(const S &x, S *s_w /* [SEG_BLOCK/32 + 1] */) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Seg<N, V> inc = x;
+  S inc = x;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const Seg<N, V> t = seg_shfl_up(inc, o);
+    const S t = seg_shfl_up(inc, o);
     if (lane >= o) inc = seg_combine(t, inc);
   }
   if (lane == 31) s_w[warp] = inc;
   __syncthreads();
   if (threadIdx.x == 0) {
-    Seg<N, V> run;
-    run.f = 0;
-#pragma unroll
-    for (int k = 0; k < N; ++k) run.v[k] = V(0);
+    S run = seg_zero(x);
     for (int w = 0; w < SEG_BLOCK / 32; ++w) {
-      const Seg<N, V> t = s_w[w];
+      const S t = s_w[w];
       s_w[w] = run;
       run = seg_combine(run, t);
     }
   }
   __syncthreads();
-  Seg<N, V> prev = seg_shfl_up(inc, 1);
-  if (lane == 0) {
-    prev.f = 0;
-#pragma unroll
-    for (int k = 0; k < N; ++k) prev.v[k] = V(0);
-  }
+  S prev = seg_shfl_up(inc, 1);
+  if (lane == 0) prev = seg_zero(x);
   return seg_combine(s_w[warp], prev);
 }
 
@@ -587,6 +620,39 @@ __device__ __forceinline__ void store_run(float *p, uint32_t j0, uint32_t n, con
     for (int k = 0; k < ITEMS; ++k)
       if (j0 + k < n) p[j0 + k] = v[k];
   }
+}
+
+// moment terms of one particle: u v_x, u v_y, u v_x^2, u v_y^2, u v_x v_y (u = w'/rho_p)
+__device__ __forceinline__ void moment_terms(float u, float vx, float vy, float (&m)[5]) {
+  const float mx = __fmul_rn(u, vx), my = __fmul_rn(u, vy);
+  m[0] = mx;
+  m[1] = my;
+  m[2] = __fmul_rn(mx, vx);
+  m[3] = __fmul_rn(my, vy);
+  m[4] = __fmul_rn(mx, vy);
+}
+
+// Eq. mean_x, var_x, covar_xy from the cell's sums of u v, u v^2, u vx vy
+__device__ __forceinline__ void moments_store(const DevBufs &B, uint32_t c, const float (&m)[5]) {
+  const float mx = m[0], my = m[1];
+  B.mean_x[c] = mx;
+  B.mean_y[c] = my;
+  B.var_x[c] = fmaxf(__fsub_rn(m[2], __fmul_rn(mx, mx)), 0.0f);
+  B.var_y[c] = fmaxf(__fsub_rn(m[3], __fmul_rn(my, my)), 0.0f);
+  B.cov[c] = __fsub_rn(m[4], __fmul_rn(mx, my));
+}
+
+// moments from the sums of w v, w v^2, w vx vy over a cell and its weight sum S (2^-40
+// fixed point): the cell-normalised weight is w / S
+__device__ __forceinline__ void moments_from_sums(const DevBufs &B, uint32_t c, const float (&m)[5],
+                                                  unsigned long long S) {
+  float u[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  if (S != 0ull) {
+    const float inv = __fdiv_rn(1.0f, fx40_to_f(S));
+#pragma unroll
+    for (int k = 0; k < 5; ++k) u[k] = __fmul_rn(m[k], inv);
+  }
+  moments_store(B, c, u);
 }
 
 // k_segsum: cell ranges (Alg. 2) and S_c = sum of q40(w) (Eq. DS_particle_sum_pred as an
@@ -704,6 +770,112 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
     } else if (j == last_valid) {
       atomicAdd(B.S_piece + c, run[0]);
       if constexpr (RADAR) atomicAdd(B.A_piece + c, run[N - 1]);
+    }
+  }
+}
+
+// k_segsum_lidar: k_segsum for a filter without radar likelihood (g == 1), which also sums
+// the velocity moments of Eq. mean_x, var_x, covar_xy.  With g == 1 the normalised weight
+// is w' = (rho_p / S_c) w, so the weight each moment uses, w' / rho_p, equals w / S_c: the
+// moments follow from the predicted weights here, one pass earlier than the normalisation.
+// w v, w v^2, w vx vy are summed per cell in binary32 by the same block-wide segmented
+// scan; a cell inside the tile is finished here, a cell spread over tiles adds its pieces
+// in exact 2^-40 fixed point and k_cell finishes it.
+__global__ void __launch_bounds__(SEG_BLOCK, 4) k_segsum_lidar(KParams P, DevBufs B) {
+  __shared__ SegQM s_wqm[SEG_BLOCK / 32 + 1];
+  __shared__ float s_x[3][SEG_TILE + SEG_TILE / 8];  // w, vx, vy in tile order (padded)
+  const uint32_t tile = blockIdx.x, frame = B.ctl->frame;
+  const uint32_t base = tile * SEG_TILE;
+  const uint32_t last_valid = min(base + SEG_TILE, P.nu) - 1u;
+  // gather phase, warp-striped, all loads in flight before the stores
+  uint32_t gi[SEG_ITEMS];
+#pragma unroll
+  for (int it = 0; it < SEG_ITEMS; ++it) {
+    const uint32_t j = base + it * SEG_BLOCK + threadIdx.x;
+    gi[it] = j < P.nu ? __ldg(B.perm + j) : 0xffffffffu;
+  }
+  float4 st[SEG_ITEMS];
+  float w[SEG_ITEMS];
+#pragma unroll
+  for (int it = 0; it < SEG_ITEMS; ++it) {
+    st[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+    w[it] = 0.0f;
+    if (gi[it] != 0xffffffffu) {
+      st[it] = __ldg(B.As + gi[it]);
+      w[it] = __ldg(B.Aw + gi[it]);
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < SEG_ITEMS; ++it) {
+    const uint32_t m = it * SEG_BLOCK + threadIdx.x;
+    const uint32_t j = base + m;
+    if (j < P.nu) {
+      B.Os[j] = st[it];
+      B.Ow[j] = w[it];
+    }
+    s_x[0][pad8(m)] = w[it];
+    s_x[1][pad8(m)] = st[it].z;
+    s_x[2][pad8(m)] = st[it].w;
+  }
+  __syncthreads();
+  // scan phase, blocked: a thread owns ITEMS consecutive positions
+  const uint32_t j0 = base + threadIdx.x * SEG_ITEMS;
+  uint32_t key[SEG_ITEMS];
+  load_run<SEG_ITEMS>(B.key_sorted, j0, P.nu, key, 0xffffffffu);
+  const uint32_t kprev = (j0 > 0 && j0 <= P.nu) ? __ldg(B.key_sorted + j0 - 1) : 0xfffffffeu;
+  const uint32_t knext = (j0 + SEG_ITEMS < P.nu) ? __ldg(B.key_sorted + j0 + SEG_ITEMS) : 0xfffffffeu;
+  uint32_t head = 0, tail = 0;
+  SegQM agg;
+  agg = seg_zero(agg);
+#pragma unroll
+  for (int it = 0; it < SEG_ITEMS; ++it) {
+    const uint32_t j = j0 + it;
+    const bool ok = j < P.nu;
+    const uint32_t kp = it == 0 ? kprev : key[it - 1];
+    const uint32_t kn = it == SEG_ITEMS - 1 ? knext : key[it + 1];
+    const bool h = ok && (j == 0 || key[it] != kp);
+    const bool t = ok && (j == P.nu - 1 || key[it] != kn);
+    head |= (uint32_t)h << it;
+    tail |= (uint32_t)t << it;
+    const uint32_t m = pad8(threadIdx.x * SEG_ITEMS + it);
+    SegQM e;
+    e.f = h;
+    e.q = q40(s_x[0][m]);
+    moment_terms(s_x[0][m], s_x[1][m], s_x[2][m], e.m);
+    agg = seg_combine(agg, e);
+  }
+  const SegQM ex = block_seg_excl(agg, s_wqm);
+  unsigned long long rq = ex.q;
+  float rm[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) rm[k] = ex.m[k];
+  bool seen = ex.f != 0;  // the current segment's head lies in this tile
+  const size_t Cs = P.C;
+#pragma unroll
+  for (int it = 0; it < SEG_ITEMS; ++it) {
+    const uint32_t j = j0 + it;
+    if (j >= P.nu) break;
+    const bool h = (head >> it) & 1u, t = (tail >> it) & 1u;
+    const uint32_t m = pad8(threadIdx.x * SEG_ITEMS + it);
+    const unsigned long long q = q40(s_x[0][m]);
+    float mt[5];
+    moment_terms(s_x[0][m], s_x[1][m], s_x[2][m], mt);
+    rq = h ? q : rq + q;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) rm[k] = h ? mt[k] : __fadd_rn(rm[k], mt[k]);
+    seen |= h;
+    const uint32_t c = key[it];
+    if (h) B.cstart[c] = j;
+    if (t) B.cend[c] = j + 1;
+    if (t && seen) {  // the whole cell lies in this tile
+      B.S[c] = rq;
+      B.tag[c] = frame << 1;
+      moments_from_sums(B, c, rm, rq);
+    } else if (t || j == last_valid) {  // a piece of a cell spread over several tiles
+      atomicAdd(B.S_piece + c, rq);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) atomicAdd(B.Mx + k * Cs + c, q40s(rm[k]));
+      if (t) B.tag[c] = (frame << 1) | 1u;
     }
   }
 }
@@ -908,6 +1080,17 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
         B.paeff[c] = pa;
       }
       B.muA[c] = muA;
+      if constexpr (!RADAR) {  // moments of the lidar filter (see k_segsum_lidar)
+        if (cross) {
+          float mm[5];
+#pragma unroll
+          for (int k = 0; k < 5; ++k) mm[k] = fx40s_to_f(atomicExch(B.Mx + (size_t)k * P.C + c, 0ull));
+          moments_from_sums(B, c, mm, rp > 0.0f ? S : 0ull);
+        } else if (occ && !(rp > 0.0f)) {
+          const float z[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+          moments_store(B, c, z);
+        }
+      }
       if (!occ) {
         B.mean_x[c] = 0.0f; B.mean_y[c] = 0.0f; B.var_x[c] = 0.0f; B.var_y[c] = 0.0f; B.cov[c] = 0.0f;
       }
@@ -1142,26 +1325,6 @@ __global__ void __launch_bounds__(BIRTH_BLOCK) k_birth(KParams P, DevBufs B) {
 // ====================================================================================
 constexpr int NORM_BLOCK = 256, NORM_ITEMS = 8, NORM_TILE = NORM_BLOCK * NORM_ITEMS;
 
-// moment terms of one particle: u v_x, u v_y, u v_x^2, u v_y^2, u v_x v_y (u = w'/rho_p)
-__device__ __forceinline__ void moment_terms(float u, float vx, float vy, float (&m)[5]) {
-  const float mx = __fmul_rn(u, vx), my = __fmul_rn(u, vy);
-  m[0] = mx;
-  m[1] = my;
-  m[2] = __fmul_rn(mx, vx);
-  m[3] = __fmul_rn(my, vy);
-  m[4] = __fmul_rn(mx, vy);
-}
-
-// Eq. mean_x, var_x, covar_xy from the cell's sums of u v, u v^2, u vx vy
-__device__ __forceinline__ void moments_store(const DevBufs &B, uint32_t c, const float (&m)[5]) {
-  const float mx = m[0], my = m[1];
-  B.mean_x[c] = mx;
-  B.mean_y[c] = my;
-  B.var_x[c] = fmaxf(__fsub_rn(m[2], __fmul_rn(mx, mx)), 0.0f);
-  B.var_y[c] = fmaxf(__fsub_rn(m[3], __fmul_rn(my, my)), 0.0f);
-  B.cov[c] = __fsub_rn(m[4], __fmul_rn(mx, my));
-}
-
 template <bool RADAR>
 __global__ void __launch_bounds__(NORM_BLOCK, 4) k_normalise(KParams P, DevBufs B) {
   __shared__ Seg<5, float> s_w[NORM_BLOCK / 32 + 1];
@@ -1295,6 +1458,46 @@ __global__ void __launch_bounds__(NORM_BLOCK, 4) k_normalise(KParams P, DevBufs 
       if (__ldg(B.rho_p + c) > 0.0f) moments_store(B, c, tot);
       else { float z[5] = {0.f, 0.f, 0.f, 0.f, 0.f}; moments_store(B, c, z); }
     }
+  }
+}
+
+// k_normalise_lidar: the lidar filter's normalisation (Eq. DSnormalization with g == 1:
+// w' = mu_UA w, Alg. 4) and the tile sums of the joint quantised weights; its moments
+// were summed in k_segsum_lidar.
+__global__ void __launch_bounds__(NORM_BLOCK) k_normalise_lidar(KParams P, DevBufs B) {
+  __shared__ unsigned long long s_red[NORM_BLOCK / 32];
+  const uint32_t tile = blockIdx.x;
+  const uint32_t ntot = P.nu + P.nu_b;
+  const uint32_t j0 = tile * NORM_TILE + threadIdx.x * NORM_ITEMS;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long qsum = 0ull;
+  if (tile * NORM_TILE < P.nu) {  // block-uniform
+    uint32_t key[NORM_ITEMS];
+    float ws[NORM_ITEMS], cmu[NORM_ITEMS], wn[NORM_ITEMS];
+    load_run<NORM_ITEMS>(B.key_sorted, j0, P.nu, key, 0xffffffffu);
+    load_runf<NORM_ITEMS>(B.Ow, j0, P.nu, ws);
+#pragma unroll
+    for (int it = 0; it < NORM_ITEMS; ++it) cmu[it] = j0 + it < P.nu ? __ldg(B.muU + key[it]) : 0.0f;
+#pragma unroll
+    for (int it = 0; it < NORM_ITEMS; ++it) {
+      wn[it] = __fmul_rn(cmu[it], ws[it]);
+      qsum += q40(wn[it]);
+    }
+    store_run<NORM_ITEMS>(B.wn, j0, P.nu, wn);
+  }
+#pragma unroll
+  for (int it = 0; it < NORM_ITEMS; ++it) {
+    const uint32_t j = j0 + it;
+    if (j >= P.nu && j < ntot) qsum += q40(__ldg(B.bw + (j - P.nu)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) qsum += __shfl_xor_sync(FULL, qsum, o);
+  if (lane == 0) s_red[warp] = qsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tsum = 0ull;
+    for (int w = 0; w < NORM_BLOCK / 32; ++w) tsum += s_red[w];
+    B.cdf_tile[tile] = tsum;
   }
 }
 

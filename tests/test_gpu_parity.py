@@ -4,13 +4,15 @@ fixed-point sums, newborn slots, resample sources) and every FP32 mass, weight a
 state are compared bit for bit; velocity moments within a tolerance derived from the
 kernel's arithmetic:
 
-The kernel sums the terms u v, u v^2, u vx vy (u = w'/rho_p, Eq. mean_x, var_x, covar_xy)
-in binary32 over a binary tree of depth <= 11 inside a 2048-particle tile, joins the pieces
-of a cell spread over tiles in 2^-40 fixed point, and forms u with one rounded product by a
-rounded reciprocal; the oracle sums the same terms in binary64.  Each partial sum is
-therefore off by at most (11 + 3) 2^-24 of the sum of |terms| plus 2^-40 per piece, i.e.
-|err(mean)| <= 14 * 2^-24 * E_u|v| + 1e-11 <= 9e-7 sqrt(E_u[v^2]).  The tolerances below
-are that bound with an order of magnitude of headroom:
+The kernel sums the terms w v, w v^2, w vx vy (Eq. mean_x, var_x, covar_xy; for the lidar
+filter w'/rho_p = w/S_c exactly, so it uses the predicted weights w and divides by the
+fixed-point S_c; with a radar likelihood it sums u v, ... with u = w' (1/rho_p)) in binary32
+over a binary tree of depth <= 11 inside a 2048-particle tile, joins the pieces of a cell
+spread over tiles in 2^-40 fixed point, and scales by one rounded reciprocal; the oracle
+sums w' v, ... in binary64 from its binary32 w' (one more rounding per term).  Each
+normalised sum is therefore off by at most (11 + 4) 2^-24 of the sum of |terms| plus 2^-40
+per piece, i.e. |err(mean)| <= 15 * 2^-24 * E|v| + 1e-11 <= 9e-7 sqrt(E[v^2]).  The
+tolerances below are that bound with an order of magnitude of headroom:
 mean: 1e-5 (1 + sqrt(E[v^2])); variance and covariance: 1e-5 (1 + E[v^2]).
 """
 import numpy as np
