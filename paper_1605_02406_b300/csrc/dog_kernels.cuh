@@ -192,15 +192,22 @@ __global__ void __launch_bounds__(PRED_BLOCK) k_predict(KParams P, DevBufs B) {
         }
       }
     }
-    // digit histograms: one shared-memory add per distinct digit per warp
+    // digit histograms: the thread's four consecutive particles mostly share a cell (the
+    // posterior is in cell order), so runs of equal digits are added with one atomic each
+    for (int p = 0; p < P.passes; ++p) {
+      uint32_t cur = 0xffffffffu, cnt = 0u;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      for (int p = 0; p < P.passes; ++p) {
-        const uint32_t d = valid[k] ? ((key[k] >> (p * P.dbits)) & mask) : 0xffffffffu;
-        const uint32_t peers = __match_any_sync(FULL, d);
-        if (d != 0xffffffffu && (peers & lanemask_lt()) == 0u)
-          atomicAdd(&sh_hist[p * P.radix + d], (uint32_t)__popc(peers));
+      for (int k = 0; k < 4; ++k) {
+        if (!valid[k]) continue;
+        const uint32_t d = (key[k] >> (p * P.dbits)) & mask;
+        if (d != cur) {
+          if (cnt) atomicAdd(&sh_hist[p * P.radix + cur], cnt);
+          cur = d;
+          cnt = 0u;
+        }
+        ++cnt;
       }
+      if (cnt) atomicAdd(&sh_hist[p * P.radix + cur], cnt);
     }
   }
   __syncthreads();
