@@ -46,7 +46,7 @@ ALG_BYTES = {
     "k_segsum": (48, 0, 0),       # read key 4 + perm 4 + gathered state 20; write sorted copy 20
     "k_cell": (0, 0, 60),         # read S 8, tag 4, m_F 4, z_O 4, z_F 4; write 9 cell fields
     "k_birth": (0, 20, 0),        # write newborn state 16 + weight 4
-    "k_normalise": (28, 4, 0),    # read key 4, w 4, state 16, write w' 4; newborn w 4
+    "k_normalise": (12, 4, 0),    # lidar: read key 4, w 4, write w' 4; newborn w 4
     "k_resample": (8, 4, 0),      # read w' 4; write the source index 4; newborn w 4
     "k_tick": (0, 0, 0),
 }

@@ -77,13 +77,15 @@ def traffic(path: str) -> dict:
     per = collections.defaultdict(list)
     sort_pass = None
     for _, (k, v) in sorted(acc.items()):
+        k = k.replace("_lidar", "")  # the lidar variants report under the step's kernel names
         if k == "k_predict":
             sort_pass = 0
-        elif k == "k_sort_pass":
-            if sort_pass is None:  # capture began between passes: pass unknown
+        elif k in ("k_sort_count", "k_sort_offsets", "k_sort_pass"):
+            if sort_pass is None:  # capture began inside the sort: pass unknown
                 continue
-            k = f"k_sort_pass{sort_pass}"
-            sort_pass += 1
+            k = f"{k}{sort_pass}"
+            if k.startswith("k_sort_pass"):
+                sort_pass += 1
         per[k].append(v)
     return {k: sum(v) / len(v) for k, v in per.items()}
 
