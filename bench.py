@@ -173,6 +173,53 @@ def run_reference(args) -> None:
     }), flush=True)
 
 
+def batched_latency(frames: int, warmup: int, dt: float = 0.1) -> dict:
+    """p50/p99 GPU time of one frame of the 64-filter batched workload (uneven grids and
+    particle counts), stepped by a plain loop of dog_step calls vs one dog_batch_step."""
+    import torch
+
+    from paper_1605_02406_b300.filter import DogBatch, DogFilter
+    cfgs = scene.batched_configs(64)
+    shared = torch.cuda.Stream()
+    filters = []
+    for k, c in enumerate(cfgs):
+        f = DogFilter(scene.filter_params(c, seed=100 + k), stream=shared)
+        g = scene.frame_sequence(c, 1, 2000 + k)[0]
+        f.set_measurement_grid(**{kk: torch.tensor(v, device="cuda") for kk, v in g.items()})
+        filters.append(f)
+    batch = DogBatch(filters)
+    dts = [dt] * len(filters)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * frames)]
+
+    def run(step):
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        for k in range(frames):
+            ev[2 * k].record(shared)
+            step()
+            ev[2 * k + 1].record(shared)
+        torch.cuda.synchronize()
+        return [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(frames)]
+
+    def plain():
+        for f in filters:
+            f.step(dt)
+
+    t_plain = run(plain)
+    t_batch = run(lambda: batch.step(dts))
+    nu_total = sum(int(c["nu"]) for c in cfgs)
+    batch.close()
+    for f in filters:
+        f.close()
+    return {"workload": "batched: 64 filters, sides 256-1024 at 0.1 m, 2^18-2^22 particles each "
+                        f"({nu_total:,} in total)",
+            "frames": frames,
+            "plain_p50": float(np.percentile(t_plain, 50)), "plain_p99": float(np.percentile(t_plain, 99)),
+            "batched_p50": float(np.percentile(t_batch, 50)), "batched_p99": float(np.percentile(t_batch, 99)),
+            "batched_particle_updates_per_s": nu_total / (float(np.median(t_batch)) * 1e-3)}
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -180,6 +227,7 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-filter latency run")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -307,6 +355,9 @@ def main() -> None:
         if world > 1:
             dist.destroy_process_group()
         return
+    batched = {"workload": None}
+    if not args.no_batched:
+        batched = batched_latency(frames=min(args.steps, 50), warmup=args.warmup)
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_oracle_rate(scene.filter_params(cfg), grids[:8])
@@ -320,9 +371,8 @@ def main() -> None:
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (particle state 168 MB); no flush",
                    "launch": "CUDA graph per step"},
-        "latency_ms": {"plain_p50": float(np.percentile(per_step, 50)),
-                       "plain_p99": float(np.percentile(per_step, 99)),
-                       "batched_p50": None, "batched_p99": None},
+        "latency_ms": dict(batched, step_p50=float(np.percentile(per_step, 50)),
+                           step_p99=float(np.percentile(per_step, 99))),
         "e2e": {"value": e2e_value, "unit": "particle-updates/s",
                 "h2d_bytes_per_step": 2 * 4 * C, "d2h_bytes_per_step": 3 * 4 * C},
         "gpu_launches": launches,

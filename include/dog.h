@@ -208,8 +208,37 @@ int dog_assign_cells_noalloc(const uint32_t *d_keys, uint32_t n, uint32_t num_ce
  * the stream has drained). */
 void dog_destroy(dog_filter *f);
 
+/* ---- Batched stepping (no counterpart in the paper: a way to run many independent
+ * filters per frame).  A batch advances n filters by one frame each with a single CUDA-graph
+ * launch whose n parallel branches are the filters' own frame sequences, so small filters
+ * overlap on the GPU and the host issues one launch instead of n.  Every filter of a batch
+ * must have been created on the same non-NULL stream; the batch launches on that stream, so
+ * each filter's other calls (grids, cells, state) stay ordered with the batched frames.
+ * Filters created with DOG_PROFILE cannot be batched.  A filter may belong to several
+ * batches and may still be stepped alone with dog_step; the caller must not destroy a
+ * filter before the batches that hold it. */
+typedef struct dog_batch dog_batch;
+
+/* Create a batch over filters[0..n) (n >= 1, pointers kept, not owned).
+ * Errors: INVALID_ARG (NULL, n < 1, different or NULL streams, a profiling filter), CUDA. */
+int dog_batch_create(dog_filter *const *filters, int n, dog_batch **out);
+
+/* One frame of every filter of the batch, with time steps dt[0..n) (host array, s).  Each
+ * filter needs a measurement grid, as for dog_step.  Asynchronous; results equal n calls of
+ * dog_step bit for bit.  The graph is captured on the first call and again whenever a
+ * filter's grid switched between lidar and lidar + radar.
+ * Errors: INVALID_ARG (dt out of domain), BAD_STATE (a filter without grid), CUDA. */
+int dog_batch_step(dog_batch *b, const float *dt);
+
+/* Release the batch (waits for its stream); the filters stay. */
+void dog_batch_destroy(dog_batch *b);
+
 /* Static description of a dog_status. */
 const char *dog_error_string(int code);
+
+/* The CUDA runtime's description of the last CUDA failure that made a call of this thread
+ * return DOG_ERR_CUDA ("" if none); static storage. */
+const char *dog_last_cuda_error(void);
 
 #ifdef __cplusplus
 }

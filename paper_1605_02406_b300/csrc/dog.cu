@@ -156,8 +156,11 @@ struct dog_filter {
 
 namespace {
 
+thread_local const char *t_last_cuda_error = "";
+
 int cuda_fail(cudaError_t e) {
   if (e == cudaSuccess) return DOG_OK;
+  t_last_cuda_error = cudaGetErrorString(e);
   (void)cudaGetLastError();
   return DOG_ERR_CUDA;
 }
@@ -287,6 +290,8 @@ cudaMemcpyKind kind_from(int mem) { return mem == DOG_DEVICE ? cudaMemcpyDeviceT
 
 extern "C" {
 
+const char *dog_last_cuda_error(void) { return t_last_cuda_error; }
+
 const char *dog_error_string(int code) {
   switch (code) {
     case DOG_OK: return "ok";
@@ -365,8 +370,9 @@ int dog_create(const dog_params *params, void *d_workspace, size_t workspace_byt
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   f->birth_grid = (int)((params->num_birth + BIRTH_SLOTS - 1) / BIRTH_SLOTS);
   if (f->birth_grid < 1) f->birth_grid = 1;
-  const size_t ssm = sort_smem_bytes(d.radix);
-  cudaError_t e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+  // the attribute is per kernel, shared by all filters: allow the largest digit's need
+  cudaError_t e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sort_smem_bytes(2048));
   if (e == cudaSuccess) e = cudaMemsetAsync(f->ws, 0, need, f->st);
   if (e == cudaSuccess) {
     k_init<<<sms * 8, 256, 0, f->st>>>(K, f->B);
@@ -385,6 +391,115 @@ int dog_create(const dog_params *params, void *d_workspace, size_t workspace_byt
   }
   *out = f;
   return DOG_OK;
+}
+
+struct dog_batch {
+  std::vector<dog_filter *> f;
+  cudaStream_t st = nullptr;
+  std::vector<cudaStream_t> side;     // capture-time branch streams, one per filter
+  std::vector<cudaEvent_t> join;      // branch ends
+  cudaEvent_t fork = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<unsigned char> radar;   // each filter's grid kind when the graph was captured
+};
+
+int dog_batch_create(dog_filter *const *filters, int n, dog_batch **out) {
+  if (!filters || !out || n < 1) return DOG_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!filters[i] || !filters[i]->st || filters[i]->profile || filters[i]->st != filters[0]->st)
+      return DOG_ERR_INVALID_ARG;
+  dog_batch *b = new dog_batch();
+  b->f.assign(filters, filters + n);
+  b->st = filters[0]->st;
+  b->side.assign(n, nullptr);
+  b->join.assign(n, nullptr);
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    dog_batch_destroy(b);
+    return cuda_fail(e);
+  }
+  *out = b;
+  return DOG_OK;
+}
+
+// capture one graph whose branch i is filter i's frame (enqueued on a side stream forked
+// from and joined back into the batch stream)
+static int batch_capture(dog_batch *b) {
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  const int n = (int)b->f.size();
+  DOG_CUDA(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+  int rc = cuda_fail(cudaEventRecord(b->fork, b->st));
+  for (int i = 0; i < n && rc == DOG_OK; ++i) {
+    dog_filter *f = b->f[i];
+    rc = cuda_fail(cudaStreamWaitEvent(b->side[i], b->fork, 0));
+    if (rc) break;
+    cudaStream_t own = f->st;
+    f->st = b->side[i];
+    rc = enqueue_frame(f, f->radar, nullptr);
+    f->st = own;
+    if (rc) break;
+    rc = cuda_fail(cudaEventRecord(b->join[i], b->side[i]));
+    if (rc == DOG_OK) rc = cuda_fail(cudaStreamWaitEvent(b->st, b->join[i], 0));
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->st, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  DOG_CUDA(e);
+  const cudaError_t e2 = cudaGraphInstantiate(&b->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  DOG_CUDA(e2);
+  b->radar.resize(n);
+  for (int i = 0; i < n; ++i) b->radar[i] = b->f[i]->radar ? 1 : 0;
+  return DOG_OK;
+}
+
+int dog_batch_step(dog_batch *b, const float *dt) {
+  if (!b || !dt) return DOG_ERR_INVALID_ARG;
+  const int n = (int)b->f.size();
+  for (int i = 0; i < n; ++i) {
+    if (!(dt[i] >= 0.0f) || !std::isfinite(dt[i])) return DOG_ERR_INVALID_ARG;
+    if (!b->f[i]->has_grid) return DOG_ERR_BAD_STATE;
+  }
+  bool recapture = !b->gexec;
+  for (int i = 0; i < n && !recapture; ++i) recapture = b->radar[i] != (b->f[i]->radar ? 1 : 0);
+  for (int i = 0; i < n; ++i) {  // time steps that changed, in stream order before the frame
+    dog_filter *f = b->f[i];
+    if (!f->dt_valid || dt[i] != f->dt) {
+      const float h = dt[i];
+      DOG_CUDA(cudaMemcpyAsync(&f->B.ctl->dt, &h, 4, cudaMemcpyHostToDevice, b->st));
+      f->dt = dt[i];
+      f->dt_valid = true;
+    }
+  }
+  if (recapture) {
+    const int rc = batch_capture(b);
+    if (rc) return rc;
+  }
+  DOG_CUDA(cudaGraphLaunch(b->gexec, b->st));
+  for (int i = 0; i < n; ++i) b->f[i]->frame += 1;
+  return DOG_OK;
+}
+
+void dog_batch_destroy(dog_batch *b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  for (auto x : b->side)
+    if (x) cudaStreamDestroy(x);
+  for (auto x : b->join)
+    if (x) cudaEventDestroy(x);
+  if (b->fork) cudaEventDestroy(b->fork);
+  delete b;
 }
 
 void dog_destroy(dog_filter *f) {

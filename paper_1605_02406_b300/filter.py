@@ -120,3 +120,28 @@ class DogFilter:
 
     def kernels_per_step(self) -> int:
         return N.dog_kernels_per_step(self.h)
+
+
+class DogBatch:
+    """Several ``DogFilter`` objects created on one stream, advanced together by one graph
+    launch per frame (``dog_batch_step``)."""
+
+    def __init__(self, filters: list):
+        self.filters = list(filters)
+        self.h = N.dog_batch_create([f.h for f in self.filters])
+
+    def step(self, dts) -> None:
+        if not hasattr(dts, "__len__"):
+            dts = [dts] * len(self.filters)
+        N.dog_batch_step(self.h, dts)
+
+    def close(self):
+        if getattr(self, "h", None):
+            N.dog_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -28,7 +28,8 @@ DOG_DBG = {n: k for k, n in enumerate(DBG)}
 SYMBOLS = ["dog_workspace_bytes", "dog_create", "dog_set_measurement_grid", "dog_step",
            "dog_get_cells", "dog_get_state", "dog_set_state", "dog_sync", "dog_get_debug",
            "dog_profile_read", "dog_kernels_per_step", "dog_destroy", "dog_error_string",
-           "dog_assign_cells_noalloc"]
+           "dog_assign_cells_noalloc", "dog_batch_create", "dog_batch_step", "dog_batch_destroy",
+           "dog_last_cuda_error"]
 DOG_NOALLOC_MAX_PARTICLES, DOG_NOALLOC_MAX_CELLS = 1 << 19, 1 << 22
 
 
@@ -65,7 +66,10 @@ _lib = None
 
 class DogError(RuntimeError):
     def __init__(self, fn: str, code: int):
-        super().__init__(f"{fn} failed: {DOG_ERR.get(code, code)}")
+        detail = ""
+        if code == -3 and _lib is not None:
+            detail = f" ({_lib.dog_last_cuda_error().decode()})"
+        super().__init__(f"{fn} failed: {DOG_ERR.get(code, code)}{detail}")
         self.code = code
 
 
@@ -94,8 +98,14 @@ def lib() -> C.CDLL:
         L.dog_assign_cells_noalloc.argtypes = [vp, C.c_uint32, C.c_uint32, vp, vp, vp, vp]
         L.dog_error_string.argtypes = [C.c_int]
         L.dog_error_string.restype = C.c_char_p
+        L.dog_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp)]
+        L.dog_batch_step.argtypes = [vp, C.POINTER(C.c_float)]
+        L.dog_batch_destroy.argtypes = [vp]
+        L.dog_batch_destroy.restype = None
+        L.dog_last_cuda_error.argtypes = []
+        L.dog_last_cuda_error.restype = C.c_char_p
         for n in SYMBOLS:
-            if n not in ("dog_destroy", "dog_error_string"):
+            if n not in ("dog_destroy", "dog_error_string", "dog_batch_destroy", "dog_last_cuda_error"):
                 getattr(L, n).restype = C.c_int
         _lib = L
     return _lib
@@ -194,3 +204,19 @@ def dog_assign_cells_noalloc(keys_ptr: int, n: int, num_cells: int, perm_ptr: in
 
 def dog_error_string(code: int) -> str:
     return lib().dog_error_string(code).decode()
+
+
+def dog_batch_create(handles: list) -> int:
+    arr = (C.c_void_p * len(handles))(*handles)
+    b = C.c_void_p()
+    check("dog_batch_create", lib().dog_batch_create(arr, len(handles), C.byref(b)))
+    return b.value
+
+
+def dog_batch_step(b: int, dts) -> None:
+    arr = (C.c_float * len(dts))(*[float(x) for x in dts])
+    check("dog_batch_step", lib().dog_batch_step(b, arr))
+
+
+def dog_batch_destroy(b: int) -> None:
+    lib().dog_batch_destroy(b)

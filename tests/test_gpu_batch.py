@@ -1,0 +1,98 @@
+"""GPU tests of batched stepping (dog_batch_*): several independent filters of different
+sizes advanced by one graph launch per frame must give, bit for bit, what stepping each
+filter alone gives -- and hence what the oracle gives, which the parity tests establish for
+single filters.  One filter switches from a lidar to a lidar + radar grid mid-run, which
+re-captures the batch graph.
+"""
+import numpy as np
+import pytest
+
+from paper_1605_02406_b300 import scene
+
+pytestmark = pytest.mark.gpu
+
+
+def _params(W, H, nu, nu_b, seed, cell=0.5):
+    return dict(width=W, height=H, cell_size=cell, nu=nu, nu_b=nu_b, p_S=0.99, p_B=0.02,
+                alpha=0.9, sigma_pos=0.1, sigma_vel=2.0, sigma_birth_vel=4.0,
+                sensor_x=W * cell * 0.5, sensor_y=H * cell * 0.4, seed=seed, flags=0)
+
+
+CASES = [_params(64, 48, 3000, 600, 11), _params(96, 96, 8192, 2048, 12),
+         _params(40, 40, 1000, 0, 13), _params(128, 80, 20000, 5000, 14, cell=0.25)]
+
+
+def _setup(filters, rng_seed):
+    rng = np.random.default_rng(rng_seed)
+    grids = []
+    for f, p in zip(filters, CASES):
+        st = scene.random_state(p, rng, occupied_frac=0.1)
+        f.set_state(st)
+        gl = [scene.random_measurement_grid(p["width"], p["height"], rng) for _ in range(4)]
+        gr = scene.random_measurement_grid(p["width"], p["height"], rng, radar=True)
+        grids.append((gl, gr))
+    return grids
+
+
+def _snapshot(f):
+    out = {k: v.copy() for k, v in f.cells().items()}
+    out.update({"state." + k: np.asarray(v).copy() for k, v in f.get_state().items()})
+    return out
+
+
+def test_batch_equals_single_filters():
+    import torch
+
+    from paper_1605_02406_b300.filter import DogBatch, DogFilter
+    shared = torch.cuda.Stream()
+    batched = [DogFilter(p, stream=shared) for p in CASES]
+    single = [DogFilter(p) for p in CASES]
+    g_b = _setup(batched, 7)
+    g_s = _setup(single, 7)
+    batch = DogBatch(batched)
+    dts = [0.1, 0.05, 0.1, 0.2]
+    for frame in range(5):
+        for i in range(len(CASES)):
+            gl, gr = g_b[i]
+            # filter 1 switches to a radar grid from frame 3 on (graph re-capture)
+            grid = gr if (i == 1 and frame >= 3) else gl[frame % len(gl)]
+            batched[i].set_measurement_grid(**grid)
+            single[i].set_measurement_grid(**grid)
+            single[i].step(dts[i])
+        batch.step(dts)
+        for i in range(len(CASES)):
+            a, b = _snapshot(batched[i]), _snapshot(single[i])
+            assert a.keys() == b.keys()
+            for k in a:
+                va, vb = np.asarray(a[k]), np.asarray(b[k])
+                if va.dtype.kind == "f":
+                    va, vb = va.astype(np.float32).view(np.uint32), vb.astype(np.float32).view(np.uint32)
+                assert np.array_equal(va, vb), f"frame {frame}, filter {i}: {k} differs"
+    batch.close()
+
+
+def test_batch_rejects_mixed_streams_and_missing_grid():
+    import torch
+
+    from paper_1605_02406_b300 import native as N
+    from paper_1605_02406_b300.filter import DogBatch, DogFilter
+    a = DogFilter(CASES[0])
+    b = DogFilter(CASES[2])  # its own stream
+    with pytest.raises(N.DogError) as e:
+        DogBatch([a, b])
+    assert e.value.code == -1
+    s = torch.cuda.Stream()
+    c, d = DogFilter(CASES[0], stream=s), DogFilter(CASES[2], stream=s)
+    batch = DogBatch([c, d])
+    with pytest.raises(N.DogError) as e:
+        batch.step([0.1, 0.1])  # no measurement grid yet
+    assert e.value.code == -6
+    rng = np.random.default_rng(3)
+    for f, p in ((c, CASES[0]), (d, CASES[2])):
+        f.set_measurement_grid(**scene.random_measurement_grid(p["width"], p["height"], rng))
+    with pytest.raises(N.DogError) as e:
+        batch.step([0.1, float("nan")])
+    assert e.value.code == -1
+    batch.step([0.1, 0.1])
+    c.sync()
+    batch.close()
