@@ -220,6 +220,34 @@ def batched_latency(frames: int, warmup: int, dt: float = 0.1) -> dict:
             "batched_particle_updates_per_s": nu_total / (float(np.median(t_batch)) * 1e-3)}
 
 
+def fusion_rate(steps: int, warmup: int) -> dict:
+    """Device-resident step rate of the lidar + radar workload (2048x2048 at 0.1 m,
+    16,777,216 + 4,194,304 particles, 64 radar detections a frame)."""
+    import torch
+
+    from paper_1605_02406_b300.filter import DogFilter
+    cfg = scene.CONFIGS["fusion_2048"]
+    params = scene.filter_params(cfg, seed=42)
+    grids = scene.frame_sequence(cfg, 8, 1005)
+    dev = [{k: torch.tensor(v, device="cuda") for k, v in g.items()} for g in grids]
+    f = DogFilter(params)
+    for k in range(warmup):
+        f.set_measurement_grid(**dev[k % 8])
+        f.step(cfg["dt"])
+    f.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(f.stream)
+    for k in range(steps):
+        f.set_measurement_grid(**dev[(warmup + k) % 8])
+        f.step(cfg["dt"])
+    e1.record(f.stream)
+    f.sync()
+    ms = e0.elapsed_time(e1) / steps
+    f.close()
+    return {"workload": cfg["name"], "steps": steps, "ms_per_step": ms,
+            "value": params["nu"] / (ms * 1e-3), "unit": "particle-updates/s"}
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -228,6 +256,7 @@ def main() -> None:
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-filter latency run")
+    ap.add_argument("--no-fusion", action="store_true", help="skip the lidar + radar workload")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -355,6 +384,9 @@ def main() -> None:
         if world > 1:
             dist.destroy_process_group()
         return
+    fusion = None
+    if not args.no_fusion:
+        fusion = fusion_rate(steps=min(args.steps, 100), warmup=args.warmup)
     batched = {"workload": None}
     if not args.no_batched:
         batched = batched_latency(frames=min(args.steps, 50), warmup=args.warmup)
@@ -386,6 +418,7 @@ def main() -> None:
         "kernels_gbs": {k: (round(v, 1) if v else None) for k, v in kern_gbs.items()},
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "fusion": fusion,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

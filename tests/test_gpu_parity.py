@@ -256,3 +256,23 @@ def test_full_size_automotive_frames():
     p = scene.filter_params(cfg, flags=RECORD)
     grids = scene.frame_sequence(cfg, 3, 1002)
     run_pair(p, 3, grids)
+
+
+def test_fusion_scene_radar_frames():
+    """Lidar + radar scene (radar detections on moving objects: p_A = 0.9, measured radial
+    velocity) at 512x512 with 2^20 + 2^18 particles, five frames, everything compared."""
+    cfg = dict(scene.CONFIGS["fusion_2048"], width=512, height=512, nu=1 << 20, nu_b=1 << 18,
+               beams=2160, n_moving=12, n_static=40)
+    p = scene.filter_params(cfg, flags=RECORD)
+    grids = scene.frame_sequence(cfg, 5, 1005)
+    assert any(float(g["p_A"].max()) > 0 for g in grids)
+    run_pair(p, 5, grids, radar=True)
+
+
+def test_full_size_fusion_frames():
+    """The 2048x2048, 16,777,216 + 4,194,304 particle lidar + radar workload, two frames
+    against the oracle in the launch configuration of the benchmark (CUDA graph)."""
+    cfg = scene.CONFIGS["fusion_2048"]
+    p = scene.filter_params(cfg, flags=RECORD)
+    grids = scene.frame_sequence(cfg, 2, 1005)
+    run_pair(p, 2, grids, radar=True)
