@@ -1104,22 +1104,22 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
       qb = q40(rb);
     }
     has[it] = qb > 0ull;
-    // inclusive warp scan of (qb, has)
-    unsigned long long sq = qb;
-    uint32_t sn = has[it] ? 1u : 0u;
+    // position among the warp's cells with newborn mass (ballot) and the inclusive prefix
+    // of their masses; cells with newborn mass are sparse, so most warps skip the scan
+    const uint32_t hb = __ballot_sync(FULL, has[it]);
+    nex[it] = wn + __popc(hb & lanemask_lt());
+    qin[it] = wq;
+    if (hb != 0u) {  // warp-uniform
+      unsigned long long sq = qb;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long tq = __shfl_up_sync(FULL, sq, o);
-      const uint32_t tn = __shfl_up_sync(FULL, sn, o);
-      if (lane >= (uint32_t)o) {
-        sq += tq;
-        sn += tn;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long tq = __shfl_up_sync(FULL, sq, o);
+        if (lane >= (uint32_t)o) sq += tq;
       }
+      qin[it] = wq + sq;
+      wq += __shfl_sync(FULL, sq, 31);
     }
-    qin[it] = wq + sq;
-    nex[it] = wn + sn - (has[it] ? 1u : 0u);
-    wq += __shfl_sync(FULL, sq, 31);
-    wn += __shfl_sync(FULL, sn, 31);
+    wn += __popc(hb);
   }
   if (lane == 0) {
     s_wq[warp] = wq;
