@@ -47,7 +47,7 @@ typedef enum dog_status {
 
 /* dog_params.flags */
 #define DOG_NO_RESAMPLE 0x2u /* keep the normalised persistent particles (test mode)     */
-#define DOG_RECORD 0x4u      /* also keep the cell and set of every newborn slot         */
+#define DOG_RECORD 0x4u      /* also keep newborn cells/sets and explicit cell ranges     */
 #define DOG_NO_GRAPH 0x8u    /* issue kernels one by one instead of a captured graph     */
 #define DOG_PROFILE 0x10u    /* time each kernel with CUDA events (dog_profile_read)      */
 
@@ -152,6 +152,7 @@ int dog_sync(dog_filter *f);
  *   DOG_DBG_KEY              u32   [nu]  cell index of each predicted particle
  *   DOG_DBG_PERM             u32   [nu]  sorted position -> particle index (Alg. 2)
  *   DOG_DBG_CELL_START/END   u32   [C]   half-open sorted range of each cell, 0/0 if empty
+ *                                  (a lidar-only filter writes them with DOG_RECORD only)
  *   DOG_DBG_SUM_W, SUM_GW    u64   [C]   fixed-point (2^-40) sums of w and g*w per cell
  *   DOG_DBG_M_OCC_PRED       float [C]   predicted occupied mass (Eq. DS_particle_sum_pred)
  *   DOG_DBG_MU_A, MU_UA      float [C]   normalisation factors (Eq. DSnormalizationfactor(2))

@@ -95,9 +95,8 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
                   &B->pO, &B->mean_x, &B->mean_y, &B->var_x, &B->var_y, &B->cov, &B->mpred,
                   &B->muA, &B->muU, &B->paeff, &B->rinv};
   for (auto q : pc) *q = (float *)take(4 * C);
-  B->S = (unsigned long long *)take(8 * C);
+  B->csum = (CellSum *)take(sizeof(CellSum) * C);
   B->A = (unsigned long long *)take(8 * C);
-  B->tag = (uint32_t *)take(4 * C);
   B->cstart = (uint32_t *)take(4 * C);
   B->cend = (uint32_t *)take(4 * C);
   const size_t CL = (size_t)d.tiles_cell * CELL_TILE;  // per-tile lists of birth cells
@@ -256,7 +255,7 @@ int read_err(dog_filter *f) {
 int reset_epochs(dog_filter *f) {
   const Derived &d = f->d;
   DevBufs &B = f->B;
-  DOG_CUDA(cudaMemsetAsync(B.tag, 0, 4 * (size_t)d.C, f->st));
+  DOG_CUDA(cudaMemsetAsync(B.csum, 0, sizeof(CellSum) * (size_t)d.C, f->st));
   DOG_CUDA(cudaMemsetAsync(B.S_piece, 0, 8 * (size_t)d.C, f->st));
   DOG_CUDA(cudaMemsetAsync(B.A_piece, 0, 8 * (size_t)d.C, f->st));
   DOG_CUDA(cudaMemsetAsync(B.Mx, 0, 8 * 5 * (size_t)d.C, f->st));
@@ -661,7 +660,7 @@ int dog_get_debug(dog_filter *f, int which, void *out, int mem_kind) {
     case DOG_DBG_PERM: src = B.perm; bytes = 4 * nu; break;
     case DOG_DBG_CELL_START: src = B.cstart; bytes = 4 * C; masked = true; break;
     case DOG_DBG_CELL_END: src = B.cend; bytes = 4 * C; masked = true; break;
-    case DOG_DBG_SUM_W: src = B.S; bytes = 8 * C; masked = true; break;
+    case DOG_DBG_SUM_W: src = &B.csum[0].S; bytes = 8 * C; masked = true; break;
     case DOG_DBG_SUM_GW: src = B.A; bytes = 8 * C; masked = true; break;
     case DOG_DBG_M_OCC_PRED: src = B.mpred; bytes = 4 * C; break;
     case DOG_DBG_MU_A: src = B.muA; bytes = 4 * C; break;
@@ -678,7 +677,8 @@ int dog_get_debug(dog_filter *f, int which, void *out, int mem_kind) {
     case DOG_DBG_SCALARS: break;
     default: return DOG_ERR_INVALID_ARG;
   }
-  if ((which == DOG_DBG_BIRTH_CELL || which == DOG_DBG_BIRTH_ASSOC) && !record)
+  if ((which == DOG_DBG_BIRTH_CELL || which == DOG_DBG_BIRTH_ASSOC ||
+       ((which == DOG_DBG_CELL_START || which == DOG_DBG_CELL_END) && !f->radar)) && !record)
     return DOG_ERR_BAD_STATE;
   DOG_CUDA(cudaStreamSynchronize(f->st));
   if (which == DOG_DBG_SCALARS) {
@@ -702,9 +702,12 @@ int dog_get_debug(dog_filter *f, int which, void *out, int mem_kind) {
   // cell arrays valid only where the cell received particles this frame (tag == frame)
   std::vector<uint32_t> tag(C);
   std::vector<unsigned char> buf(bytes);
-  DOG_CUDA(cudaMemcpy(tag.data(), B.tag, 4 * C, cudaMemcpyDeviceToHost));
-  DOG_CUDA(cudaMemcpy(buf.data(), src, bytes, cudaMemcpyDeviceToHost));
   const size_t es = bytes / C;
+  DOG_CUDA(cudaMemcpy2D(tag.data(), 4, &B.csum[0].tag, sizeof(CellSum), 4, C, cudaMemcpyDeviceToHost));
+  if (which == DOG_DBG_SUM_W)  // a field of the cell records
+    DOG_CUDA(cudaMemcpy2D(buf.data(), es, src, sizeof(CellSum), es, C, cudaMemcpyDeviceToHost));
+  else
+    DOG_CUDA(cudaMemcpy(buf.data(), src, bytes, cudaMemcpyDeviceToHost));
   for (size_t c = 0; c < C; ++c)
     if ((tag[c] >> 1) != f->frame || f->frame == 0) std::memset(buf.data() + c * es, 0, es);
   DOG_CUDA(cudaMemcpy(out, buf.data(), bytes, mem_kind == DOG_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));

@@ -33,6 +33,17 @@ struct DevCtl {
 //                   checkpoint, or a frame without resampling).
 enum : uint32_t { POST_RESAMPLED = 0, POST_DIRECT = 1 };
 
+// Per-cell result of the segment pass, one 32-byte record so that a finished cell costs two
+// 16-byte stores: S = 2^-40 fixed-point sum of the predicted weights, tag = 2 frame (cell
+// finished in one tile) or 2 frame + 1 (pieces in the accumulators), m = the lidar
+// filter's velocity moments (mean x, mean y, var x, var y, cov) of a cell finished in one tile.
+struct __align__(32) CellSum {
+  unsigned long long S;
+  uint32_t tag;
+  float m[5];
+};
+static_assert(sizeof(CellSum) == 32, "cell record is 32 bytes");
+
 struct KParams {
   int W, H;
   uint32_t C;
@@ -62,8 +73,9 @@ struct DevBufs {
   float *zO, *zF, *pA, *zv, *sgv;
   float *mO, *rho_p, *rho_b, *pO, *mean_x, *mean_y, *var_x, *var_y, *cov;
   float *mpred, *muA, *muU, *paeff, *rinv;
-  unsigned long long *S, *A;
-  uint32_t *tag, *cstart, *cend;
+  CellSum *csum;                   // [C] segment-pass result per cell
+  unsigned long long *A;           // [C] fixed-point sum of g w (radar)
+  uint32_t *cstart, *cend;         // [C] cell ranges (radar, or DOG_RECORD)
   uint32_t *bl_cell;               // [tiles_cell][1024] cells with newborn mass, per tile
   unsigned long long *bl_R;         // [tiles_cell][1024] tile-local inclusive newborn mass
   // all birth cells in cell order (entry G): first slot ([n + 1], last = nu_b), cell,

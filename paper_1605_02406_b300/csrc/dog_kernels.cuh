@@ -649,17 +649,36 @@ __device__ __forceinline__ void moments_store(const DevBufs &B, uint32_t c, cons
   B.cov[c] = __fsub_rn(m[4], __fmul_rn(mx, my));
 }
 
+// the first 16 bytes of a cell record: S, tag and the first moment
+__device__ __forceinline__ void csum_store_head(CellSum *r, unsigned long long S, uint32_t tag, float m0) {
+  *reinterpret_cast<uint4 *>(r) = make_uint4((uint32_t)S, (uint32_t)(S >> 32), tag, __float_as_uint(m0));
+}
+
 // moments from the sums of w v, w v^2, w vx vy over a cell and its weight sum S (2^-40
 // fixed point): the cell-normalised weight is w / S
-__device__ __forceinline__ void moments_from_sums(const DevBufs &B, uint32_t c, const float (&m)[5],
-                                                  unsigned long long S) {
+__device__ __forceinline__ void moments_of_sums(const float (&m)[5], unsigned long long S, float (&o)[5]) {
   float u[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   if (S != 0ull) {
     const float inv = __fdiv_rn(1.0f, fx40_to_f(S));
 #pragma unroll
     for (int k = 0; k < 5; ++k) u[k] = __fmul_rn(m[k], inv);
   }
-  moments_store(B, c, u);
+  const float mx = u[0], my = u[1];
+  o[0] = mx;
+  o[1] = my;
+  o[2] = fmaxf(__fsub_rn(u[2], __fmul_rn(mx, mx)), 0.0f);
+  o[3] = fmaxf(__fsub_rn(u[3], __fmul_rn(my, my)), 0.0f);
+  o[4] = __fsub_rn(u[4], __fmul_rn(mx, my));
+}
+__device__ __forceinline__ void moments_from_sums(const DevBufs &B, uint32_t c, const float (&m)[5],
+                                                  unsigned long long S) {
+  float o[5];
+  moments_of_sums(m, S, o);
+  B.mean_x[c] = o[0];
+  B.mean_y[c] = o[1];
+  B.var_x[c] = o[2];
+  B.var_y[c] = o[3];
+  B.cov[c] = o[4];
 }
 
 // k_segsum: cell ranges (Alg. 2) and S_c = sum of q40(w) (Eq. DS_particle_sum_pred as an
@@ -766,13 +785,12 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
     if (t) {
       B.cend[c] = j + 1;
       if (seen) {
-        B.S[c] = run[0];
+        csum_store_head(B.csum + c, run[0], frame << 1, 0.0f);
         if constexpr (RADAR) B.A[c] = run[N - 1];
-        B.tag[c] = frame << 1;
       } else {
         atomicAdd(B.S_piece + c, run[0]);
         if constexpr (RADAR) atomicAdd(B.A_piece + c, run[N - 1]);
-        B.tag[c] = (frame << 1) | 1u;
+        B.csum[c].tag = (frame << 1) | 1u;
       }
     } else if (j == last_valid) {
       atomicAdd(B.S_piece + c, run[0]);
@@ -858,6 +876,7 @@ __global__ void __launch_bounds__(SEG_BLOCK, 4) k_segsum_lidar(KParams P, DevBuf
   for (int k = 0; k < 5; ++k) rm[k] = ex.m[k];
   bool seen = ex.f != 0;  // the current segment's head lies in this tile
   const size_t Cs = P.C;
+  const bool record = (P.flags & 0x4u) != 0u;
 #pragma unroll
   for (int it = 0; it < SEG_ITEMS; ++it) {
     const uint32_t j = j0 + it;
@@ -872,17 +891,20 @@ __global__ void __launch_bounds__(SEG_BLOCK, 4) k_segsum_lidar(KParams P, DevBuf
     for (int k = 0; k < 5; ++k) rm[k] = h ? mt[k] : __fadd_rn(rm[k], mt[k]);
     seen |= h;
     const uint32_t c = key[it];
-    if (h) B.cstart[c] = j;
-    if (t) B.cend[c] = j + 1;
-    if (t && seen) {  // the whole cell lies in this tile
-      B.S[c] = rq;
-      B.tag[c] = frame << 1;
-      moments_from_sums(B, c, rm, rq);
+    if (record) {  // explicit cell ranges only for the diagnostic interface
+      if (h) B.cstart[c] = j;
+      if (t) B.cend[c] = j + 1;
+    }
+    if (t && seen) {  // the whole cell lies in this tile: one 32-byte record
+      float o[5];
+      moments_of_sums(rm, rq, o);
+      csum_store_head(B.csum + c, rq, frame << 1, o[0]);
+      *reinterpret_cast<float4 *>(&B.csum[c].m[1]) = make_float4(o[1], o[2], o[3], o[4]);
     } else if (t || j == last_valid) {  // a piece of a cell spread over several tiles
       atomicAdd(B.S_piece + c, rq);
 #pragma unroll
       for (int k = 0; k < 5; ++k) atomicAdd(B.Mx + k * Cs + c, q40s(rm[k]));
-      if (t) B.tag[c] = (frame << 1) | 1u;
+      if (t) B.csum[c].tag = (frame << 1) | 1u;
     }
   }
 }
@@ -1026,13 +1048,16 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
   uint32_t wn = 0u;
   // all loads of the thread's cells first (independent, in flight together)
   uint32_t tgs[CELL_ITEMS];
-  float mFs[CELL_ITEMS], zOs[CELL_ITEMS], zFs[CELL_ITEMS];
+  float mFs[CELL_ITEMS], zOs[CELL_ITEMS], zFs[CELL_ITEMS], m0s[CELL_ITEMS];
   unsigned long long Ss[CELL_ITEMS];
 #pragma unroll
   for (int it = 0; it < CELL_ITEMS; ++it) {
     const uint32_t c = tile * CELL_TILE + warp * (32 * CELL_ITEMS) + it * 32 + lane;
     const bool in = c < P.C;
-    tgs[it] = in ? B.tag[c] : 0u;
+    const uint4 h = in ? *reinterpret_cast<const uint4 *>(B.csum + c) : make_uint4(0u, 0u, 0u, 0u);
+    Ss[it] = ((unsigned long long)h.y << 32) | h.x;
+    tgs[it] = h.z;
+    m0s[it] = __uint_as_float(h.w);
     mFs[it] = in ? B.mF[c] : 0.0f;
     zOs[it] = in ? B.zO[c] : 0.0f;
     zFs[it] = in ? B.zF[c] : 0.0f;
@@ -1041,12 +1066,10 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
   for (int it = 0; it < CELL_ITEMS; ++it) {
     const uint32_t c = tile * CELL_TILE + warp * (32 * CELL_ITEMS) + it * 32 + lane;
     const bool occ = c < P.C && (tgs[it] >> 1) == frame;
-    Ss[it] = 0ull;
+    if (!occ) Ss[it] = 0ull;
     if (occ && (tgs[it] & 1u)) {
       Ss[it] = atomicExch(B.S_piece + c, 0ull);  // all pieces are in; clear for the next frame
-      B.S[c] = Ss[it];
-    } else if (occ) {
-      Ss[it] = B.S[c];
+      B.csum[c].S = Ss[it];
     }
   }
 #pragma unroll
@@ -1088,17 +1111,26 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
       }
       B.muA[c] = muA;
       if constexpr (!RADAR) {  // moments of the lidar filter (see k_segsum_lidar)
+        float o[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
         if (cross) {
           float mm[5];
 #pragma unroll
           for (int k = 0; k < 5; ++k) mm[k] = fx40s_to_f(atomicExch(B.Mx + (size_t)k * P.C + c, 0ull));
-          moments_from_sums(B, c, mm, rp > 0.0f ? S : 0ull);
-        } else if (occ && !(rp > 0.0f)) {
-          const float z[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-          moments_store(B, c, z);
+          moments_of_sums(mm, rp > 0.0f ? S : 0ull, o);
+        } else if (occ && rp > 0.0f) {  // finished by the segment pass
+          const float4 r = *reinterpret_cast<const float4 *>(&B.csum[c].m[1]);
+          o[0] = m0s[it];
+          o[1] = r.x;
+          o[2] = r.y;
+          o[3] = r.z;
+          o[4] = r.w;
         }
-      }
-      if (!occ) {
+        B.mean_x[c] = o[0];
+        B.mean_y[c] = o[1];
+        B.var_x[c] = o[2];
+        B.var_y[c] = o[3];
+        B.cov[c] = o[4];
+      } else if (!occ) {
         B.mean_x[c] = 0.0f; B.mean_y[c] = 0.0f; B.var_x[c] = 0.0f; B.var_y[c] = 0.0f; B.cov[c] = 0.0f;
       }
       qb = q40(rb);
