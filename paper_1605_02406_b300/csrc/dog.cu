@@ -695,6 +695,14 @@ int dog_get_debug(dog_filter *f, int which, void *out, int mem_kind) {
     if (rc) return rc;
     return read_err(f);
   }
+  if (which == DOG_DBG_KEY || which == DOG_DBG_PERM) {
+    // cell index / particle index without the out-of-grid flag the kernels carry in bit 31
+    std::vector<uint32_t> v(nu);
+    DOG_CUDA(cudaMemcpy(v.data(), src, 4 * nu, cudaMemcpyDeviceToHost));
+    for (auto &x : v) x &= ~OUT_OF_GRID;
+    DOG_CUDA(cudaMemcpy(out, v.data(), 4 * nu, mem_kind == DOG_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+    return read_err(f);
+  }
   if (!masked) {
     if (bytes) DOG_CUDA(cudaMemcpyAsync(out, src, bytes, kind_to(mem_kind), f->st));
     return read_err(f);

@@ -117,6 +117,10 @@ __global__ void k_validate(KParams P, DevBufs B, int radar) {
 // ====================================================================================
 constexpr int PRED_BLOCK = 256, PRED_ROUNDS = 4, PRED_TILE = PRED_BLOCK * 4 * PRED_ROUNDS;
 
+// key gets bit 31 set when the particle left the grid (its weight is then 0); the sort
+// moves that bit from the cell index to the particle index (see k_sort_pass)
+constexpr uint32_t OUT_OF_GRID = 0x80000000u;
+
 __device__ __forceinline__ void predict_one(const KParams &P, uint32_t i, uint32_t frame, float T,
                                             float4 &st, float &w, uint32_t &key) {
   float &x = st.x, &y = st.y, &vx = st.z, &vy = st.w;
@@ -136,6 +140,7 @@ __device__ __forceinline__ void predict_one(const KParams &P, uint32_t i, uint32
   const int row = !(fy >= 0.0f) ? 0 : (!(fy < Hf) ? P.H - 1 : (int)fy);
   if (!in) w = 0.0f;
   key = (uint32_t)row * (uint32_t)P.W + (uint32_t)col;
+  if (!in) key |= OUT_OF_GRID;
 }
 
 __global__ void __launch_bounds__(PRED_BLOCK) k_predict(KParams P, DevBufs B) {
@@ -406,12 +411,23 @@ __global__ void __launch_bounds__(SORT_BLOCK, 2)
   // load: warp w covers positions [w*256, w*256+256) of the tile, item k at k*32 + lane
   uint32_t key[SORT_ITEMS], val[SORT_ITEMS];
   const uint32_t base = tile * SORT_TILE + warp * (32 * SORT_ITEMS);
+  if (vals_in) {  // block-uniform
 #pragma unroll
-  for (int k = 0; k < SORT_ITEMS; ++k) {
-    const uint32_t pos = base + k * 32 + lane;
-    const bool ok = pos < P.nu;
-    key[k] = ok ? __ldg(keys_in + pos) : 0xffffffffu;
-    val[k] = ok ? (vals_in ? __ldg(vals_in + pos) : pos) : 0u;
+    for (int k = 0; k < SORT_ITEMS; ++k) {
+      const uint32_t pos = base + k * 32 + lane;
+      const bool ok = pos < P.nu;
+      key[k] = ok ? __ldg(keys_in + pos) : 0xffffffffu;
+      val[k] = ok ? __ldg(vals_in + pos) : 0u;
+    }
+  } else {  // first pass: the out-of-grid bit moves from the cell index to the particle index
+#pragma unroll
+    for (int k = 0; k < SORT_ITEMS; ++k) {
+      const uint32_t pos = base + k * 32 + lane;
+      const bool ok = pos < P.nu;
+      const uint32_t raw = ok ? __ldg(keys_in + pos) : 0xffffffffu;
+      key[k] = ok ? (raw & ~OUT_OF_GRID) : 0xffffffffu;
+      val[k] = ok ? (pos | (raw & OUT_OF_GRID)) : 0u;
+    }
   }
   // stable rank within the warp, item by item
   uint32_t rk[SORT_ITEMS];
@@ -712,8 +728,8 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
     st[it] = make_float4(0.f, 0.f, 0.f, 0.f);
     w[it] = 0.0f;
     if (gi[it] != 0xffffffffu) {
-      st[it] = __ldg(B.As + gi[it]);
-      w[it] = __ldg(B.Aw + gi[it]);
+      st[it] = __ldg(B.As + (gi[it] & ~OUT_OF_GRID));
+      w[it] = __ldg(B.Aw + (gi[it] & ~OUT_OF_GRID));
     }
   }
 #pragma unroll
@@ -812,7 +828,11 @@ __global__ void __launch_bounds__(SEG_BLOCK, 4) k_segsum_lidar(KParams P, DevBuf
   const uint32_t tile = blockIdx.x, frame = B.ctl->frame;
   const uint32_t base = tile * SEG_TILE;
   const uint32_t last_valid = min(base + SEG_TILE, P.nu) - 1u;
-  // gather phase, warp-striped, all loads in flight before the stores
+  // gather phase, warp-striped, all loads in flight before the stores.  After a resampled
+  // frame every predicted weight is p_S w_new, or 0 for a particle that left the grid (the
+  // sort carries that flag in the particle index), so only the record is gathered.
+  const bool uniform = B.ctl->post_mode == POST_RESAMPLED;
+  const float wu = __fmul_rn(P.p_S, B.ctl->w_new);
   uint32_t gi[SEG_ITEMS];
 #pragma unroll
   for (int it = 0; it < SEG_ITEMS; ++it) {
@@ -826,8 +846,9 @@ __global__ void __launch_bounds__(SEG_BLOCK, 4) k_segsum_lidar(KParams P, DevBuf
     st[it] = make_float4(0.f, 0.f, 0.f, 0.f);
     w[it] = 0.0f;
     if (gi[it] != 0xffffffffu) {
-      st[it] = __ldg(B.As + gi[it]);
-      w[it] = __ldg(B.Aw + gi[it]);
+      const uint32_t i = gi[it] & ~OUT_OF_GRID;
+      st[it] = __ldg(B.As + i);
+      w[it] = uniform ? ((gi[it] & OUT_OF_GRID) ? 0.0f : wu) : __ldg(B.Aw + i);
     }
   }
 #pragma unroll
