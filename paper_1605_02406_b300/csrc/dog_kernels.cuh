@@ -1573,7 +1573,7 @@ __global__ void __launch_bounds__(NORM_BLOCK) k_normalise_lidar(KParams P, DevBu
 // record of source Bsrc[i] with the equal weight W 2^-40 / nu (Eq.
 // resampledParticleWeights), which the next prediction reads through the index.
 // ====================================================================================
-constexpr int RES_BLOCK = 256;
+constexpr int RES_BLOCK = 512, RES_ITEMS = NORM_TILE / RES_BLOCK;  // sources per thread
 
 
 // #{i in [0, nu) : i W + u < X nu}, exactly
@@ -1604,7 +1604,7 @@ __device__ __forceinline__ uint32_t count_below(unsigned long long X, unsigned l
 
 constexpr int RES_OUT = 8192;  // outputs of a block staged in shared memory
 
-__global__ void __launch_bounds__(RES_BLOCK, 4) k_resample(KParams P, DevBufs B) {
+__global__ void __launch_bounds__(RES_BLOCK, 2) k_resample(KParams P, DevBufs B) {
   __shared__ uint32_t s_src[RES_OUT];  // source of output o_lo + k
   __shared__ unsigned long long s_wsum[RES_BLOCK / 32];
   __shared__ uint32_t s_lo, s_hi;
@@ -1624,20 +1624,20 @@ __global__ void __launch_bounds__(RES_BLOCK, 4) k_resample(KParams P, DevBufs B)
   const float inv_w = B.ctl->inv_w;
   // the thread's quantised weights and the CDF before its first source
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t j0 = base + threadIdx.x * NORM_ITEMS;
-  float w[NORM_ITEMS];
-  if (j0 + NORM_ITEMS <= P.nu) {
-    load_runf<NORM_ITEMS>(B.wn, j0, P.nu, w);
+  const uint32_t j0 = base + threadIdx.x * RES_ITEMS;
+  float w[RES_ITEMS];
+  if (j0 + RES_ITEMS <= P.nu) {
+    load_runf<RES_ITEMS>(B.wn, j0, P.nu, w);
   } else {
 #pragma unroll
-    for (int it = 0; it < NORM_ITEMS; ++it) {
+    for (int it = 0; it < RES_ITEMS; ++it) {
       const uint32_t j = j0 + it;
       w[it] = j < P.nu ? __ldg(B.wn + j) : (j < ntot ? __ldg(B.bw + (j - P.nu)) : 0.0f);
     }
   }
-  unsigned long long q[NORM_ITEMS], loc = 0ull;
+  unsigned long long q[RES_ITEMS], loc = 0ull;
 #pragma unroll
-  for (int it = 0; it < NORM_ITEMS; ++it) {
+  for (int it = 0; it < RES_ITEMS; ++it) {
     q[it] = q40(w[it]);
     loc += q[it];
   }
@@ -1658,7 +1658,7 @@ __global__ void __launch_bounds__(RES_BLOCK, 4) k_resample(KParams P, DevBufs B)
   const uint32_t o_lo = s_lo;
   U128 acc = add_128_64(mul_64x64(i, Wt), u);  // i W + u
 #pragma unroll
-  for (int it = 0; it < NORM_ITEMS; ++it) {
+  for (int it = 0; it < RES_ITEMS; ++it) {
     Q += q[it];
     const U128 lim = mul_64x64(Q, P.nu);
     const uint32_t j = j0 + it;
