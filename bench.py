@@ -220,6 +220,47 @@ def batched_latency(frames: int, warmup: int, dt: float = 0.1) -> dict:
             "batched_particle_updates_per_s": nu_total / (float(np.median(t_batch)) * 1e-3)}
 
 
+def evaluation_time(reps: int = 50) -> dict:
+    """Device time of the evaluation calls (cluster statistics of every object and the
+    Mahalanobis static/dynamic classification over 42 thresholds) on the 1024x1024 grid."""
+    import torch
+
+    from paper_1605_02406_b300 import native as N
+    from paper_1605_02406_b300.evaluate import Evaluator
+    from paper_1605_02406_b300.filter import DogFilter
+    cfg = scene.CONFIGS[CFG_ID]
+    seq = scene.frame_sequence_with_truth(cfg, 4, 1002)
+    f = DogFilter(scene.filter_params(cfg))
+    for g, _ in seq:
+        f.set_measurement_grid(**g)
+        f.step(cfg["dt"])
+    truth = seq[-1][1]
+    thr = np.concatenate([[0.0], np.logspace(-2, 3, 41)])
+    ev = Evaluator(f, len(truth["velocity"]), thr)
+    obj = torch.as_tensor(truth["object"], device="cuda")
+    lab = torch.as_tensor(truth["dynamic"], device="cuda")
+    f.stream.wait_stream(torch.cuda.current_stream())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def once():
+        N.dog_eval_clusters(f.h, obj.data_ptr(), ev.n_objects, ev.scratch.data_ptr(), ev.stats.data_ptr())
+        N.dog_eval_mahalanobis(f.h, lab.data_ptr(), 0.5, ev.thr.data_ptr(), len(ev.thr),
+                               ev.counts.data_ptr(), 0)
+    for _ in range(3):
+        once()
+    f.sync()
+    e0.record(f.stream)
+    for _ in range(reps):
+        once()
+    e1.record(f.stream)
+    f.sync()
+    us = e0.elapsed_time(e1) / reps * 1e3
+    out = {"grid": "1024x1024", "objects": int(ev.n_objects), "thresholds": len(thr),
+           "us_per_evaluation": us, "cells_per_s": f.C / (us * 1e-6)}
+    f.close()
+    return out
+
+
 def fusion_rate(steps: int, warmup: int) -> dict:
     """Device-resident step rate of the lidar + radar workload (2048x2048 at 0.1 m,
     16,777,216 + 4,194,304 particles, 64 radar detections a frame)."""
@@ -257,6 +298,7 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-filter latency run")
     ap.add_argument("--no-fusion", action="store_true", help="skip the lidar + radar workload")
+    ap.add_argument("--no-evaluation", action="store_true", help="skip timing the evaluation calls")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -384,6 +426,7 @@ def main() -> None:
         if world > 1:
             dist.destroy_process_group()
         return
+    evaluation = None if args.no_evaluation else evaluation_time()
     fusion = None
     if not args.no_fusion:
         fusion = fusion_rate(steps=min(args.steps, 100), warmup=args.warmup)
@@ -419,6 +462,7 @@ def main() -> None:
         "clocks": clocks,
         "cpu_baseline": cpu,
         "fusion": fusion,
+        "evaluation": evaluation,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -234,6 +234,36 @@ int dog_batch_step(dog_batch *b, const float *dt);
 /* Release the batch (waits for its stream); the filters stay. */
 void dog_batch_destroy(dog_batch *b);
 
+/* ---- Evaluation against ground truth (the experiments of Sect. VIII).  Both calls read
+ * the filter's current cell estimates (those of the last dog_step), take device pointers,
+ * run asynchronously on the filter's stream and return DOG_ERR_INVALID_ARG for NULL or
+ * empty arguments.
+ *
+ * dog_eval_clusters: velocity statistics of cell clusters S, one per object.
+ *   d_cell_object [C] int32: 0 = no object, k = 1..n_objects the object the cell belongs to.
+ *   d_scratch [n_objects][5] int64: work space (zeroed by the call).
+ *   d_stats   [n_objects][5] double out: |S|; the cluster mean velocity (Eq. mean_cluster:
+ *             the average of the cells' mean vx, vy); the cluster variance (Eq.
+ *             gaussian_mixture_x: average of var + mean^2 minus the squared cluster mean),
+ *             x then y.  Sums are exact in 2^-32 fixed point of the binary64 cell terms.
+ *   The normalised estimation error squared of Eq. NEES_x follows from d_stats and the
+ *   object's true velocity. */
+int dog_eval_clusters(dog_filter *f, const int32_t *d_cell_object, uint32_t n_objects,
+                      long long *d_scratch, double *d_stats);
+
+/* dog_eval_mahalanobis: the Mahalanobis distance m = v P^-1 v^T of each cell's velocity
+ * estimate (mean v, covariance P from var_vx, var_vy, cov_vxy) from v = 0 (Eq. mahadist;
+ * binary32, 0 for a singular P with v = 0, +inf for a singular P otherwise), and a
+ * classification histogram: over the cells with label 1 (dynamic) or 2 (static) and
+ * m_occ >= min_occ, d_counts[(label - 1) * (n_thresholds + 1) + j] counts the cells for
+ * which exactly j of the ascending d_thresholds are <= m (zeroed by the call).  A cell is
+ * detected as dynamic at threshold t_j when m >= t_j, so the detections at t_j are the
+ * cells counted in bins j + 1 .. n_thresholds.  d_m (optional, [C] float) receives m
+ * (0 for cells not evaluated).  Errors: INVALID_ARG, UNSUPPORTED (n_thresholds > 4096). */
+int dog_eval_mahalanobis(dog_filter *f, const uint8_t *d_label, float min_occ,
+                         const float *d_thresholds, uint32_t n_thresholds,
+                         unsigned long long *d_counts, float *d_m);
+
 /* Static description of a dog_status. */
 const char *dog_error_string(int code);
 

@@ -12,6 +12,7 @@
 
 #include "../../include/dog.h"
 #include "dog_kernels.cuh"
+#include "dog_eval.cuh"
 
 using namespace dog;
 
@@ -290,6 +291,28 @@ cudaMemcpyKind kind_from(int mem) { return mem == DOG_DEVICE ? cudaMemcpyDeviceT
 extern "C" {
 
 const char *dog_last_cuda_error(void) { return t_last_cuda_error; }
+
+int dog_eval_clusters(dog_filter *f, const int32_t *d_cell_object, uint32_t n_objects, long long *d_scratch,
+                      double *d_stats) {
+  if (!f || !d_cell_object || !d_scratch || !d_stats || n_objects == 0) return DOG_ERR_INVALID_ARG;
+  DOG_CUDA(cudaMemsetAsync(d_scratch, 0, sizeof(long long) * 5 * (size_t)n_objects, f->st));
+  const uint32_t grid = (f->d.C + EVAL_BLOCK - 1) / EVAL_BLOCK < 2048u ? (f->d.C + EVAL_BLOCK - 1) / EVAL_BLOCK : 2048u;
+  k_eval_cluster_sums<<<grid, EVAL_BLOCK, 0, f->st>>>(f->K, f->B, d_cell_object, n_objects, d_scratch);
+  k_eval_cluster_stats<<<(n_objects + 255) / 256, 256, 0, f->st>>>(d_scratch, n_objects, d_stats);
+  return cuda_fail(cudaGetLastError());
+}
+
+int dog_eval_mahalanobis(dog_filter *f, const uint8_t *d_label, float min_occ, const float *d_thresholds,
+                         uint32_t n_thresholds, unsigned long long *d_counts, float *d_m) {
+  if (!f || !d_label || !d_counts || (n_thresholds > 0 && !d_thresholds)) return DOG_ERR_INVALID_ARG;
+  if (n_thresholds > 4096) return DOG_ERR_UNSUPPORTED;
+  const size_t nb = 2 * ((size_t)n_thresholds + 1);
+  DOG_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(unsigned long long) * nb, f->st));
+  const uint32_t grid = (f->d.C + EVAL_BLOCK - 1) / EVAL_BLOCK < 1184u ? (f->d.C + EVAL_BLOCK - 1) / EVAL_BLOCK : 1184u;
+  k_eval_mahalanobis<<<grid, EVAL_BLOCK, 4 * nb, f->st>>>(f->K, f->B, d_label, min_occ, d_thresholds,
+                                                           n_thresholds, d_counts, d_m);
+  return cuda_fail(cudaGetLastError());
+}
 
 const char *dog_error_string(int code) {
   switch (code) {

@@ -29,7 +29,7 @@ SYMBOLS = ["dog_workspace_bytes", "dog_create", "dog_set_measurement_grid", "dog
            "dog_get_cells", "dog_get_state", "dog_set_state", "dog_sync", "dog_get_debug",
            "dog_profile_read", "dog_kernels_per_step", "dog_destroy", "dog_error_string",
            "dog_assign_cells_noalloc", "dog_batch_create", "dog_batch_step", "dog_batch_destroy",
-           "dog_last_cuda_error"]
+           "dog_last_cuda_error", "dog_eval_clusters", "dog_eval_mahalanobis"]
 DOG_NOALLOC_MAX_PARTICLES, DOG_NOALLOC_MAX_CELLS = 1 << 19, 1 << 22
 
 
@@ -103,6 +103,8 @@ def lib() -> C.CDLL:
         L.dog_batch_destroy.argtypes = [vp]
         L.dog_batch_destroy.restype = None
         L.dog_last_cuda_error.argtypes = []
+        L.dog_eval_clusters.argtypes = [vp, vp, C.c_uint32, vp, vp]
+        L.dog_eval_mahalanobis.argtypes = [vp, vp, C.c_float, vp, C.c_uint32, vp, vp]
         L.dog_last_cuda_error.restype = C.c_char_p
         for n in SYMBOLS:
             if n not in ("dog_destroy", "dog_error_string", "dog_batch_destroy", "dog_last_cuda_error"):
@@ -220,3 +222,15 @@ def dog_batch_step(b: int, dts) -> None:
 
 def dog_batch_destroy(b: int) -> None:
     lib().dog_batch_destroy(b)
+
+
+def dog_eval_clusters(h: int, d_cell_object: int, n_objects: int, d_scratch: int, d_stats: int) -> None:
+    check("dog_eval_clusters", lib().dog_eval_clusters(h, C.c_void_p(d_cell_object), n_objects,
+                                                       C.c_void_p(d_scratch), C.c_void_p(d_stats)))
+
+
+def dog_eval_mahalanobis(h: int, d_label: int, min_occ: float, d_thresholds: int, n_thresholds: int,
+                         d_counts: int, d_m: int | None) -> None:
+    check("dog_eval_mahalanobis", lib().dog_eval_mahalanobis(
+        h, C.c_void_p(d_label), float(min_occ), C.c_void_p(d_thresholds), n_thresholds,
+        C.c_void_p(d_counts), C.c_void_p(d_m)))

@@ -401,3 +401,45 @@ def random_state(params: dict, rng: np.random.Generator, occupied_frac: float = 
     f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
     return dict(x=f32(x), y=f32(y), vx=f32(vx), vy=f32(vy), w=f32(w), m_free=f32(m_free),
                 frame=int(frame))
+
+
+# --------------------------------------------------------------------------------------
+# ground truth for the evaluation (object cells and velocities)
+# --------------------------------------------------------------------------------------
+def label_cells(sc: Scene) -> dict:
+    """Cells whose centre lies inside an object at the scene's current time.
+
+    Returns object (int32 [C]: 0 = no object, k = sc.boxes[k - 1]), dynamic (uint8 [C]:
+    1 = a moving object, 2 = a static one, 0 = none) and the objects' true velocities
+    (float64 [n, 2])."""
+    W, H, s = int(sc.cfg["width"]), int(sc.cfg["height"]), float(sc.cfg["cell_size"])
+    obj = np.zeros(W * H, np.int32)
+    dyn = np.zeros(W * H, np.uint8)
+    vel = np.zeros((len(sc.boxes), 2))
+    for k, b in enumerate(sc.boxes):
+        vel[k] = (b.vx, b.vy)
+        r = math.hypot(b.hl, b.hw)
+        c0, c1 = max(0, int((b.cx - r) / s)), min(W - 1, int((b.cx + r) / s))
+        r0, r1 = max(0, int((b.cy - r) / s)), min(H - 1, int((b.cy + r) / s))
+        if c0 > c1 or r0 > r1:
+            continue
+        cols = np.arange(c0, c1 + 1)
+        rows = np.arange(r0, r1 + 1)
+        X, Y = np.meshgrid((cols + 0.5) * s - b.cx, (rows + 0.5) * s - b.cy)
+        c, sn = math.cos(b.heading), math.sin(b.heading)
+        inside = (np.abs(c * X + sn * Y) <= b.hl) & (np.abs(-sn * X + c * Y) <= b.hw)
+        idx = (rows[:, None] * W + cols[None, :])[inside]
+        obj[idx] = k + 1
+        dyn[idx] = 1 if (b.vx != 0.0 or b.vy != 0.0) else 2
+    return dict(object=obj, dynamic=dyn, velocity=vel)
+
+
+def frame_sequence_with_truth(cfg: dict, n_frames: int, seed: int) -> list:
+    """As frame_sequence, each frame paired with its ground truth (label_cells)."""
+    sc = make_scene(cfg, seed)
+    rng = np.random.default_rng(seed + 1)
+    out = []
+    for _ in range(n_frames):
+        advance(sc, cfg["dt"])
+        out.append((measurement_grid(sc, rng), label_cells(sc)))
+    return out
