@@ -54,6 +54,7 @@ typedef enum dog_status {
 /* memory kind of caller buffers */
 #define DOG_HOST 0
 #define DOG_DEVICE 1
+#define DOG_HOST_ASYNC 2 /* dog_set_measurement_grid only: host arrays, the call does not wait */
 
 /* Filter parameters (Table I of the paper gives typical values).  All POD; validated by
  * dog_workspace_bytes and dog_create.  Limits: 1 <= width, height; C = width*height < 2^24 (so
@@ -120,11 +121,14 @@ int dog_create(const dog_params *params, void *d_workspace, size_t workspace_byt
  * used by every following dog_step until replaced.  mem_kind says where the caller's arrays
  * live.  The grid is copied and validated on the device (m_occ, m_free in [0, 1] with
  * m_occ + m_free <= 1; p_A in [0, 1]; sigma_vr > 0 where p_A > 0; z_vr finite).
- * DOG_HOST: the call waits for the copy (the caller may then reuse its arrays) and returns
- * DOG_ERR_INPUT on a violation, after which dog_step refuses (DOG_ERR_BAD_STATE) until a
- * valid grid is set; it also returns any error latched by earlier frames.  DOG_DEVICE:
- * asynchronous; a violation is latched and reported as DOG_ERR_INPUT by the next
- * synchronising call. */
+ * DOG_HOST: the arrays are uploaded on the filter's upload stream (overlapping a frame
+ * still in flight) and the call returns when the upload is done, so the caller may reuse
+ * them; pinned host memory is fastest.  DOG_HOST_ASYNC: the same upload, but the call
+ * returns at once and the caller must leave the arrays unchanged until the upload is done
+ * (guaranteed after dog_sync, or after dog_get_cells_async / dog_wait_cells of a later
+ * frame has returned).  DOG_DEVICE: asynchronous.  In all cases a violation
+ * is latched and reported as DOG_ERR_INPUT by the next synchronising call (dog_sync,
+ * dog_get_cells, dog_wait_cells, ...); the frames stepped with that grid are void. */
 int dog_set_measurement_grid(dog_filter *f, const dog_meas_grid *grid, int mem_kind);
 
 /* One recursion of the filter with time step dt (s): Alg. 1-7 of Sect. VII.
@@ -135,6 +139,19 @@ int dog_step(dog_filter *f, float dt);
 /* Copy the per-cell outputs of the last frame; synchronises the filter's stream.  Returns
  * a latched device error if one occurred since the last synchronising call. */
 int dog_get_cells(dog_filter *f, const dog_cells *out, int mem_kind);
+
+/* Asynchronous read-back of the cells of the last dog_step into HOST arrays (any field NULL
+ * = skipped; pinned host memory lets the copy overlap the next frame).  The requested fields
+ * are copied on the device in stream order -- the next dog_step may be issued at once -- and
+ * from there to the host on the filter's read-back stream.  The arrays are valid after
+ * dog_wait_cells returns.  One read-back may be in flight per filter: a second call first
+ * waits for the previous one.  Errors latched by the frames before the read-back (input
+ * validation) are returned by dog_wait_cells.  Errors: INVALID_ARG, CUDA. */
+int dog_get_cells_async(dog_filter *f, const dog_cells *out);
+
+/* Block until the read-back started by dog_get_cells_async has arrived (DOG_OK at once if
+ * none is in flight).  Errors: INPUT / DEVICE (latched before the read-back), CUDA. */
+int dog_wait_cells(dog_filter *f);
 
 /* Read / write the posterior state and frame counter (checkpoint / resume; Philox draws
  * depend only on (seed, frame, index), so a resumed filter continues bit-exactly).

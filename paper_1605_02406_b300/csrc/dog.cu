@@ -97,6 +97,8 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
                   &B->muA, &B->muU, &B->paeff, &B->rinv};
   for (auto q : pc) *q = (float *)take(4 * C);
   B->csum = (CellSum *)take(sizeof(CellSum) * C);
+  B->g_stage = (float *)take(4 * 5 * C);
+  B->c_stage = (float *)take(4 * (10 * C + 64));
   B->A = (unsigned long long *)take(8 * C);
   B->cstart = (uint32_t *)take(4 * C);
   B->cend = (uint32_t *)take(4 * C);
@@ -152,6 +154,11 @@ struct dog_filter {
   int ring_head = 0, ring_count = 0;
   int nk = 0;
   int birth_grid = 1;
+  // host I/O overlapped with compute: grid uploads and cell read-backs on their own streams
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t ev_h2d = nullptr, ev_stage_free = nullptr, ev_snap = nullptr, ev_d2h = nullptr;
+  bool d2h_pending = false;
+  uint32_t *d2h_err = nullptr;  // pinned host word: error bits of the frame being read back
 };
 
 namespace {
@@ -400,15 +407,19 @@ int dog_create(const dog_params *params, void *d_workspace, size_t workspace_byt
     k_init<<<sms * 8, 256, 0, f->st>>>(K, f->B);
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&f->h2d, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&f->d2h, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMallocHost(&f->d2h_err, 64);  // pinned: the copy stays asynchronous
+  cudaEvent_t *evs[] = {&f->ev_h2d, &f->ev_stage_free, &f->ev_snap, &f->ev_d2h};
+  for (auto q : evs)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(q, cudaEventDisableTiming);
   if (e == cudaSuccess && f->profile) {
     f->ev.assign((size_t)PROFILE_RING * (MAX_KERNELS + 1), nullptr);
     for (auto &x : f->ev)
       if (e == cudaSuccess) e = cudaEventCreate(&x);
   }
   if (e != cudaSuccess) {
-    for (auto &x : f->ev)
-      if (x) cudaEventDestroy(x);
-    delete f;
+    dog_destroy(f);
     return cuda_fail(e);
   }
   *out = f;
@@ -527,6 +538,14 @@ void dog_batch_destroy(dog_batch *b) {
 void dog_destroy(dog_filter *f) {
   if (!f) return;
   if (f->st) cudaStreamSynchronize(f->st);
+  for (auto x : {f->h2d, f->d2h})
+    if (x) {
+      cudaStreamSynchronize(x);
+      cudaStreamDestroy(x);
+    }
+  for (auto x : {f->ev_h2d, f->ev_stage_free, f->ev_snap, f->ev_d2h})
+    if (x) cudaEventDestroy(x);
+  if (f->d2h_err) cudaFreeHost(f->d2h_err);
   for (auto &g : f->gexec)
     if (g) cudaGraphExecDestroy(g);
   for (auto &x : f->ev)
@@ -536,29 +555,36 @@ void dog_destroy(dog_filter *f) {
 
 int dog_set_measurement_grid(dog_filter *f, const dog_meas_grid *g, int mem_kind) {
   if (!f || !g || !g->m_occ || !g->m_free) return DOG_ERR_INVALID_ARG;
-  if (mem_kind != DOG_HOST && mem_kind != DOG_DEVICE) return DOG_ERR_INVALID_ARG;
+  if (mem_kind != DOG_HOST && mem_kind != DOG_DEVICE && mem_kind != DOG_HOST_ASYNC) return DOG_ERR_INVALID_ARG;
   const bool radar = g->p_A != nullptr;
   if (radar && (!g->z_vr || !g->sigma_vr)) return DOG_ERR_INVALID_ARG;
   const size_t C = f->d.C;
-  const cudaMemcpyKind kd = kind_from(mem_kind);
-  DOG_CUDA(cudaMemcpyAsync(f->B.zO, g->m_occ, 4 * C, kd, f->st));
-  DOG_CUDA(cudaMemcpyAsync(f->B.zF, g->m_free, 4 * C, kd, f->st));
-  if (radar) {
-    DOG_CUDA(cudaMemcpyAsync(f->B.pA, g->p_A, 4 * C, kd, f->st));
-    DOG_CUDA(cudaMemcpyAsync(f->B.zv, g->z_vr, 4 * C, kd, f->st));
-    DOG_CUDA(cudaMemcpyAsync(f->B.sgv, g->sigma_vr, 4 * C, kd, f->st));
+  const float *src[5] = {g->m_occ, g->m_free, g->p_A, g->z_vr, g->sigma_vr};
+  float *dst[5] = {f->B.zO, f->B.zF, f->B.pA, f->B.zv, f->B.sgv};
+  const int nfield = radar ? 5 : 2;
+  if (mem_kind == DOG_DEVICE) {
+    for (int k = 0; k < nfield; ++k)
+      DOG_CUDA(cudaMemcpyAsync(dst[k], src[k], 4 * C, cudaMemcpyDeviceToDevice, f->st));
+  } else {
+    // upload on the copy stream into the staging buffer (free once the previous grid was
+    // taken over), so that it overlaps the frame in flight; then take it over in stream order
+    DOG_CUDA(cudaStreamWaitEvent(f->h2d, f->ev_stage_free, 0));
+    for (int k = 0; k < nfield; ++k)
+      DOG_CUDA(cudaMemcpyAsync(f->B.g_stage + k * C, src[k], 4 * C, cudaMemcpyHostToDevice, f->h2d));
+    DOG_CUDA(cudaEventRecord(f->ev_h2d, f->h2d));
+    DOG_CUDA(cudaStreamWaitEvent(f->st, f->ev_h2d, 0));
+    for (int k = 0; k < nfield; ++k) k_copy<<<592, 256, 0, f->st>>>(f->B.g_stage + k * C, dst[k], C);
+    DOG_CUDA(cudaGetLastError());
+    DOG_CUDA(cudaEventRecord(f->ev_stage_free, f->st));
   }
   k_validate<<<256, 256, 0, f->st>>>(f->K, f->B, radar ? 1 : 0);
   DOG_CUDA(cudaGetLastError());
   f->radar = radar;
-  if (mem_kind == DOG_DEVICE) {  // asynchronous: a violation is reported by the next sync
-    f->has_grid = true;
-    return DOG_OK;
-  }
-  // host arrays: wait for the copy (the caller may reuse them) and report the validation
-  const int rc = read_err(f);
-  f->has_grid = rc == DOG_OK;
-  return rc;
+  f->has_grid = true;
+  // host arrays: the caller may reuse them once the upload is done (DOG_HOST_ASYNC: the
+  // caller waits for that itself, with dog_sync or a later call that waits)
+  if (mem_kind == DOG_HOST) DOG_CUDA(cudaEventSynchronize(f->ev_h2d));
+  return DOG_OK;
 }
 
 int dog_step(dog_filter *f, float dt) {
@@ -616,6 +642,47 @@ int dog_get_cells(dog_filter *f, const dog_cells *out, int mem_kind) {
   for (int k = 0; k < 10; ++k)
     if (dst[k]) DOG_CUDA(cudaMemcpyAsync(dst[k], src[k], n, kd, f->st));
   return read_err(f);
+}
+
+int dog_get_cells_async(dog_filter *f, const dog_cells *out) {
+  if (!f || !out) return DOG_ERR_INVALID_ARG;
+  if (f->d2h_pending) {  // one read-back in flight: let the previous one finish
+    const int rc = dog_wait_cells(f);
+    if (rc) return rc;
+  }
+  const size_t C = f->d.C;
+  float *dst[] = {out->m_occ, out->m_free, out->rho_p, out->rho_b, out->p_occ,
+                  out->mean_vx, out->mean_vy, out->var_vx, out->var_vy, out->cov_vxy};
+  const float *src[] = {f->B.mO, f->B.mF, f->B.rho_p, f->B.rho_b, f->B.pO,
+                        f->B.mean_x, f->B.mean_y, f->B.var_x, f->B.var_y, f->B.cov};
+  // snapshot in stream order (the next frame may then overwrite the cells), copy to the host
+  // on the read-back stream
+  uint32_t *err_snap = reinterpret_cast<uint32_t *>(f->B.c_stage + 10 * C);
+  for (int k = 0; k < 10; ++k)
+    if (dst[k]) k_copy<<<592, 256, 0, f->st>>>(src[k], f->B.c_stage + k * C, C);
+  k_copy<<<1, 32, 0, f->st>>>(reinterpret_cast<const float *>(&f->B.ctl->err), reinterpret_cast<float *>(err_snap), 1);
+  DOG_CUDA(cudaGetLastError());
+  DOG_CUDA(cudaMemsetAsync(&f->B.ctl->err, 0, 4, f->st));
+  DOG_CUDA(cudaEventRecord(f->ev_snap, f->st));
+  DOG_CUDA(cudaStreamWaitEvent(f->d2h, f->ev_snap, 0));
+  for (int k = 0; k < 10; ++k)
+    if (dst[k]) DOG_CUDA(cudaMemcpyAsync(dst[k], f->B.c_stage + k * C, 4 * C, cudaMemcpyDeviceToHost, f->d2h));
+  DOG_CUDA(cudaMemcpyAsync(f->d2h_err, err_snap, 4, cudaMemcpyDeviceToHost, f->d2h));
+  DOG_CUDA(cudaEventRecord(f->ev_d2h, f->d2h));
+  f->d2h_pending = true;
+  return DOG_OK;
+}
+
+int dog_wait_cells(dog_filter *f) {
+  if (!f) return DOG_ERR_INVALID_ARG;
+  if (!f->d2h_pending) return DOG_OK;
+  DOG_CUDA(cudaEventSynchronize(f->ev_d2h));
+  f->d2h_pending = false;
+  const uint32_t err = *f->d2h_err;
+  *f->d2h_err = 0;
+  if (err & ERR_INPUT) return DOG_ERR_INPUT;
+  if (err) return DOG_ERR_DEVICE;
+  return DOG_OK;
 }
 
 int dog_get_state(dog_filter *f, const dog_state *out, int mem_kind, uint32_t *frame) {

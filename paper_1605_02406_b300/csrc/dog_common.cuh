@@ -74,6 +74,8 @@ struct DevBufs {
   float *mO, *rho_p, *rho_b, *pO, *mean_x, *mean_y, *var_x, *var_y, *cov;
   float *mpred, *muA, *muU, *paeff, *rinv;
   CellSum *csum;                   // [C] segment-pass result per cell
+  float *g_stage;                  // [5][C] measurement grid uploaded from the host
+  float *c_stage;                  // [10][C] + error word: cells read back to the host
   unsigned long long *A;           // [C] fixed-point sum of g w (radar)
   uint32_t *cstart, *cend;         // [C] cell ranges (radar, or DOG_RECORD)
   uint32_t *bl_cell;               // [tiles_cell][1024] cells with newborn mass, per tile

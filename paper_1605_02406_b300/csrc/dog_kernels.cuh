@@ -73,6 +73,20 @@ __global__ void k_gather_posterior(KParams P, DevBufs B, float *__restrict__ out
   }
 }
 
+// device-to-device copy of n floats by the SMs (the copy engines stay free for the host
+// transfers that overlap the frame); 16-byte accesses where both ends allow
+__global__ void k_copy(const float *__restrict__ src, float *__restrict__ dst, size_t n) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  if ((((uintptr_t)src | (uintptr_t)dst) & 15) == 0) {
+    const size_t n4 = n / 4;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += stride)
+      reinterpret_cast<float4 *>(dst)[i] = __ldg(reinterpret_cast<const float4 *>(src) + i);
+    for (size_t i = 4 * n4 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
+  } else {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
+  }
+}
+
 // ====================================================================================
 // record <-> plain arrays (state checkpoint and diagnostics; not on the per-frame path)
 // ====================================================================================

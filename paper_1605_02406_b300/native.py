@@ -16,7 +16,7 @@ DOG_ERR = {-1: "DOG_ERR_INVALID_ARG", -2: "DOG_ERR_WORKSPACE_TOO_SMALL", -3: "DO
            -4: "DOG_ERR_DEVICE", -5: "DOG_ERR_INPUT", -6: "DOG_ERR_BAD_STATE",
            -7: "DOG_ERR_UNSUPPORTED"}
 DOG_NO_RESAMPLE, DOG_RECORD, DOG_NO_GRAPH, DOG_PROFILE = 0x2, 0x4, 0x8, 0x10
-DOG_HOST, DOG_DEVICE = 0, 1
+DOG_HOST, DOG_DEVICE, DOG_HOST_ASYNC = 0, 1, 2
 
 DBG = ["PRED_X", "PRED_Y", "PRED_VX", "PRED_VY", "PRED_W", "KEY", "PERM", "CELL_START",
        "CELL_END", "SUM_W", "SUM_GW", "M_OCC_PRED", "MU_A", "MU_UA", "W_NORM", "BIRTH_X",
@@ -29,7 +29,8 @@ SYMBOLS = ["dog_workspace_bytes", "dog_create", "dog_set_measurement_grid", "dog
            "dog_get_cells", "dog_get_state", "dog_set_state", "dog_sync", "dog_get_debug",
            "dog_profile_read", "dog_kernels_per_step", "dog_destroy", "dog_error_string",
            "dog_assign_cells_noalloc", "dog_batch_create", "dog_batch_step", "dog_batch_destroy",
-           "dog_last_cuda_error", "dog_eval_clusters", "dog_eval_mahalanobis"]
+           "dog_last_cuda_error", "dog_eval_clusters", "dog_eval_mahalanobis",
+           "dog_get_cells_async", "dog_wait_cells"]
 DOG_NOALLOC_MAX_PARTICLES, DOG_NOALLOC_MAX_CELLS = 1 << 19, 1 << 22
 
 
@@ -104,6 +105,8 @@ def lib() -> C.CDLL:
         L.dog_batch_destroy.restype = None
         L.dog_last_cuda_error.argtypes = []
         L.dog_eval_clusters.argtypes = [vp, vp, C.c_uint32, vp, vp]
+        L.dog_get_cells_async.argtypes = [vp, C.POINTER(dog_cells)]
+        L.dog_wait_cells.argtypes = [vp]
         L.dog_eval_mahalanobis.argtypes = [vp, vp, C.c_float, vp, C.c_uint32, vp, vp]
         L.dog_last_cuda_error.restype = C.c_char_p
         for n in SYMBOLS:
@@ -234,3 +237,12 @@ def dog_eval_mahalanobis(h: int, d_label: int, min_occ: float, d_thresholds: int
     check("dog_eval_mahalanobis", lib().dog_eval_mahalanobis(
         h, C.c_void_p(d_label), float(min_occ), C.c_void_p(d_thresholds), n_thresholds,
         C.c_void_p(d_counts), C.c_void_p(d_m)))
+
+
+def dog_get_cells_async(h: int, ptrs: dict) -> None:
+    c = dog_cells(**{k: ptrs.get(k) for k in CELL_FIELDS})
+    check("dog_get_cells_async", lib().dog_get_cells_async(h, C.byref(c)))
+
+
+def dog_wait_cells(h: int) -> None:
+    check("dog_wait_cells", lib().dog_wait_cells(h))

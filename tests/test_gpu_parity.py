@@ -232,12 +232,14 @@ def test_invalid_measurement_grid_is_rejected():
     g = _gpu(p)
     bad = np.zeros(64, np.float32)
     bad[3] = np.nan
+    g.set_measurement_grid(bad, np.zeros(64, np.float32))  # validated on the device
     with pytest.raises(N.DogError) as e:
-        g.set_measurement_grid(bad, np.zeros(64, np.float32))
+        g.sync()
     assert e.value.code == -5
     over = np.full(64, 0.6, np.float32)
+    g.set_measurement_grid(over, over)
     with pytest.raises(N.DogError):
-        g.set_measurement_grid(over, over)
+        g.sync()
     # device-resident input: validated on the stream, reported at the next sync
     dev = torch.tensor(over, device="cuda")
     g.set_measurement_grid(dev, dev)
@@ -276,3 +278,40 @@ def test_full_size_fusion_frames():
     p = scene.filter_params(cfg, flags=RECORD)
     grids = scene.frame_sequence(cfg, 2, 1005)
     run_pair(p, 2, grids, radar=True)
+
+
+def test_async_cell_readback_pipelined():
+    """dog_get_cells_async with the next frame issued before the wait returns the same cells
+    as the synchronous read, frame by frame, and reports a grid violation at the wait."""
+    import torch
+
+    from paper_1605_02406_b300 import native as N
+    p = small(64, 48, nu=20000, nu_b=4000, flags=0)
+    rng = np.random.default_rng(5)
+    grids = [scene.random_measurement_grid(64, 48, rng) for _ in range(6)]
+    a, b = _gpu(p), _gpu(p)
+    C = 64 * 48
+    bufs = [{k: torch.empty(C, dtype=torch.float32).pin_memory() for k in ("m_occ", "p_occ", "mean_vx")}
+            for _ in range(2)]
+    got = []
+    for k, grid in enumerate(grids):
+        a.set_measurement_grid(**grid)
+        a.step(0.1)
+        N.dog_get_cells_async(a.h, {kk: v.data_ptr() for kk, v in bufs[k % 2].items()})
+        if k > 0:  # the call above let frame k - 1's read-back finish first
+            got.append({kk: v.numpy().copy() for kk, v in bufs[(k - 1) % 2].items()})
+    N.dog_wait_cells(a.h)
+    got.append({kk: v.numpy().copy() for kk, v in bufs[(len(grids) - 1) % 2].items()})
+    for k, grid in enumerate(grids):
+        b.set_measurement_grid(**grid)
+        b.step(0.1)
+        ref = b.cells(["m_occ", "p_occ", "mean_vx"])
+        for kk in ref:
+            assert_bits(f"frame {k} {kk}", got[k][kk], ref[kk])
+    bad = np.full(C, 0.7, np.float32)
+    a.set_measurement_grid(bad, bad)
+    a.step(0.1)
+    N.dog_get_cells_async(a.h, {kk: v.data_ptr() for kk, v in bufs[0].items()})
+    with pytest.raises(N.DogError) as e:
+        N.dog_wait_cells(a.h)
+    assert e.value.code == -5
