@@ -299,6 +299,7 @@ def main() -> None:
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-filter latency run")
     ap.add_argument("--no-fusion", action="store_true", help="skip the lidar + radar workload")
     ap.add_argument("--no-evaluation", action="store_true", help="skip timing the evaluation calls")
+    ap.add_argument("--no-serving", action="store_true", help="skip the 3 s serving-loop run")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -433,6 +434,10 @@ def main() -> None:
             dist.destroy_process_group()
         return
     evaluation = None if args.no_evaluation else evaluation_time()
+    serving = None
+    if not args.no_serving:
+        from paper_1605_02406_b300 import serve
+        serving = serve.run(seconds=3.0)
     fusion = None
     if not args.no_fusion:
         fusion = fusion_rate(steps=min(args.steps, 100), warmup=args.warmup)
@@ -469,6 +474,7 @@ def main() -> None:
         "cpu_baseline": cpu,
         "fusion": fusion,
         "evaluation": evaluation,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -96,3 +96,33 @@ def test_batch_rejects_mixed_streams_and_missing_grid():
     batch.step([0.1, 0.1])
     c.sync()
     batch.close()
+
+
+def test_streams_in_a_mix_equal_streams_alone():
+    """Filters stepped concurrently on their own CUDA streams, with their frames interleaved
+    as the serving loop issues them, end in exactly the state each reaches alone."""
+    import torch
+
+    from paper_1605_02406_b300.filter import DogFilter
+    mix = [DogFilter(p) for p in CASES]
+    alone = [DogFilter(p) for p in CASES]
+    g_m = _setup(mix, 9)
+    g_a = _setup(alone, 9)
+    order = [0, 2, 1, 3, 3, 0, 1, 2, 0, 3, 1, 1, 2, 0]  # an interleaving of requests
+    seen = [0] * len(CASES)
+    for i in order:  # issued back to back, no synchronisation in between
+        mix[i].set_measurement_grid(**g_m[i][0][seen[i] % 4])
+        mix[i].step(0.1)
+        seen[i] += 1
+    torch.cuda.synchronize()
+    for i in range(len(CASES)):
+        for t in range(order.count(i)):
+            alone[i].set_measurement_grid(**g_a[i][0][t % 4])
+            alone[i].step(0.1)
+    for i in range(len(CASES)):
+        a, b = _snapshot(mix[i]), _snapshot(alone[i])
+        for k in a:
+            va, vb = np.asarray(a[k]), np.asarray(b[k])
+            if va.dtype.kind == "f":
+                va, vb = va.astype(np.float32).view(np.uint32), vb.astype(np.float32).view(np.uint32)
+            assert np.array_equal(va, vb), f"filter {i}: {k} differs"
