@@ -912,6 +912,10 @@ __global__ void __launch_bounds__(SEG_BLOCK, 4) k_segsum_lidar(KParams P, DevBuf
   bool seen = ex.f != 0;  // the current segment's head lies in this tile
   const size_t Cs = P.C;
   const bool record = (P.flags & 0x4u) != 0u;
+  // the running sums are only read at a segment's end (or the tile's last particle): a
+  // thread inside one segment, as most are, has nothing more to do
+  const bool has_last = j0 <= last_valid && last_valid < j0 + SEG_ITEMS;
+  if (tail == 0u && !has_last && !(record && head != 0u)) return;
 #pragma unroll
   for (int it = 0; it < SEG_ITEMS; ++it) {
     const uint32_t j = j0 + it;
@@ -1500,6 +1504,8 @@ __global__ void __launch_bounds__(NORM_BLOCK, 4) k_normalise(KParams P, DevBufs 
 #pragma unroll
   for (int k = 0; k < 5; ++k) run[k] = ex.v[k];
   bool seen = ex.f != 0;
+  // the running sums are only read at a segment's end or the tile's last particle
+  if (tail == 0u && !(j0 <= last_valid && last_valid < j0 + NORM_ITEMS)) return;
 #pragma unroll
   for (int it = 0; it < NORM_ITEMS; ++it) {
     const uint32_t j = j0 + it;
