@@ -331,8 +331,9 @@ __global__ void __launch_bounds__(COUNT_BLOCK) k_sort_count(KParams P, DevBufs B
 
 // k_sort_offsets: for one pass, counts[d][t] -> (sum of the histogram below digit d) +
 // sum_{t' < t} counts[d][t'], in place.  One block per digit; thread k owns a contiguous run
-// of tiles, and the block scans the runs' totals.
-constexpr int OFF_BLOCK = 256, OFF_WARPS = OFF_BLOCK / 32, OFF_PER = 8;
+// of tiles, held in registers (read once, 16-byte loads where the row allows), and the
+// block scans the runs' totals.
+constexpr int OFF_BLOCK = 256, OFF_WARPS = OFF_BLOCK / 32, OFF_PER = 16;
 
 __global__ void __launch_bounds__(OFF_BLOCK) k_sort_offsets(KParams P, DevBufs B, int pass) {
   __shared__ uint32_t s_h[OFF_WARPS], s_t[OFF_WARPS];
@@ -343,16 +344,36 @@ __global__ void __launch_bounds__(OFF_BLOCK) k_sort_offsets(KParams P, DevBufs B
   uint32_t *M = B.dcnt + ((size_t)pass * P.radix + d) * T;
   const uint32_t per = (T + OFF_BLOCK - 1) / OFF_BLOCK;  // tiles per thread
   const uint32_t t0 = threadIdx.x * per;
-  // this thread's share of the histogram below d, and the total of its tiles
-  uint32_t hsum = 0, tsum = 0;
+  // this thread's share of the histogram below d
+  uint32_t hsum = 0;
   for (uint32_t e = threadIdx.x; e < d; e += OFF_BLOCK) hsum += __ldg(hist + e);
-  for (uint32_t j0 = 0; j0 < per; j0 += OFF_PER) {
-    uint32_t c[OFF_PER];
+  // rows of up to OFF_PER tiles per thread stay in registers; the 16-byte path needs the
+  // row and the thread's run to start on 16-byte boundaries
+  const bool in_regs = per <= (uint32_t)OFF_PER;
+  const bool vec = in_regs && (per % 4u) == 0u && (T % 4u) == 0u;
+  uint32_t c[OFF_PER];
+  uint32_t tsum = 0;
+  if (vec) {
+#pragma unroll
+    for (int j = 0; j < OFF_PER; j += 4) {
+      const uint32_t t = t0 + j;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if ((uint32_t)j < per && t < T) v = *reinterpret_cast<const uint4 *>(M + t);  // T % 4 == 0
+      c[j] = v.x; c[j + 1] = v.y; c[j + 2] = v.z; c[j + 3] = v.w;
+    }
+  } else if (in_regs) {
 #pragma unroll
     for (int j = 0; j < OFF_PER; ++j) {
-      const uint32_t t = t0 + j0 + j;
-      c[j] = (j0 + j < per && t < T) ? M[t] : 0u;
+      const uint32_t t = t0 + j;
+      c[j] = ((uint32_t)j < per && t < T) ? M[t] : 0u;
     }
+  } else {
+    for (uint32_t j = 0; j < per; ++j) {
+      const uint32_t t = t0 + j;
+      tsum += t < T ? M[t] : 0u;
+    }
+  }
+  if (in_regs) {
 #pragma unroll
     for (int j = 0; j < OFF_PER; ++j) tsum += c[j];
   }
@@ -374,18 +395,31 @@ __global__ void __launch_bounds__(OFF_BLOCK) k_sort_offsets(KParams P, DevBufs B
     run += s_h[w];
     if (w < warp) run += s_t[w];
   }
-  for (uint32_t j0 = 0; j0 < per; j0 += OFF_PER) {
-    uint32_t c[OFF_PER];
+  if (vec) {
 #pragma unroll
-    for (int j = 0; j < OFF_PER; ++j) {
-      const uint32_t t = t0 + j0 + j;
-      c[j] = (j0 + j < per && t < T) ? M[t] : 0u;
+    for (int j = 0; j < OFF_PER; j += 4) {
+      const uint32_t t = t0 + j;
+      uint4 v;
+      v.x = run; run += c[j];
+      v.y = run; run += c[j + 1];
+      v.z = run; run += c[j + 2];
+      v.w = run; run += c[j + 3];
+      if ((uint32_t)j < per && t < T) *reinterpret_cast<uint4 *>(M + t) = v;
     }
+  } else if (in_regs) {
 #pragma unroll
     for (int j = 0; j < OFF_PER; ++j) {
-      const uint32_t t = t0 + j0 + j;
-      if (j0 + j < per && t < T) M[t] = run;
+      const uint32_t t = t0 + j;
+      if ((uint32_t)j < per && t < T) M[t] = run;
       run += c[j];
+    }
+  } else {
+    for (uint32_t j = 0; j < per; ++j) {
+      const uint32_t t = t0 + j;
+      if (t >= T) break;
+      const uint32_t v = M[t];
+      M[t] = run;
+      run += v;
     }
   }
 }
