@@ -751,7 +751,8 @@ __device__ __forceinline__ void moments_from_sums(const DevBufs &B, uint32_t c, 
 // predicted state is gathered through the sort permutation into sorted order (Os, Ow) with
 // consecutive lanes on consecutive sorted positions (neighbouring particles mostly come
 // from neighbouring slots), and the fixed-point weights reach the blocked segmented scan
-// through shared memory.
+// through shared memory.  The radar filter also leaves each particle's likelihood g in wn
+// (sorted order), where k_normalise reads it before it writes the normalised weight.
 template <bool RADAR>
 __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
   constexpr int N = RADAR ? 2 : 1;
@@ -763,6 +764,10 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
   // gather phase, warp-striped: position base + it*256 + threadIdx.x.  All permutation
   // loads are issued, then all record loads, then the stores, so that a thread keeps
   // SEG_ITEMS independent gathers in flight.
+  // after a resampled frame every predicted weight is p_S w_new, or 0 for a particle that
+  // left the grid (flagged in the particle index), so only the record is gathered
+  const bool uniform = B.ctl->post_mode == POST_RESAMPLED;
+  const float wu = __fmul_rn(P.p_S, B.ctl->w_new);
   uint32_t gi[SEG_ITEMS];
 #pragma unroll
   for (int it = 0; it < SEG_ITEMS; ++it) {
@@ -776,8 +781,9 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
     st[it] = make_float4(0.f, 0.f, 0.f, 0.f);
     w[it] = 0.0f;
     if (gi[it] != 0xffffffffu) {
-      st[it] = __ldg(B.As + (gi[it] & ~OUT_OF_GRID));
-      w[it] = __ldg(B.Aw + (gi[it] & ~OUT_OF_GRID));
+      const uint32_t i = gi[it] & ~OUT_OF_GRID;
+      st[it] = __ldg(B.As + i);
+      w[it] = uniform ? ((gi[it] & OUT_OF_GRID) ? 0.0f : wu) : __ldg(B.Aw + i);
     }
   }
 #pragma unroll
@@ -791,10 +797,12 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
       q = q40(w[it]);
       if constexpr (RADAR) {
         const uint32_t c = __ldg(B.key_sorted + j);
-        if (__ldg(B.pA + c) > 0.0f)
-          gq = q40(__fmul_rn(radar_lik(P, st[it].x, st[it].y, st[it].z, st[it].w, __ldg(B.zv + c),
-                                       __ldg(B.sgv + c)),
-                             w[it]));
+        float g = 0.0f;
+        if (__ldg(B.pA + c) > 0.0f) {
+          g = radar_lik(P, st[it].x, st[it].y, st[it].z, st[it].w, __ldg(B.zv + c), __ldg(B.sgv + c));
+          gq = q40(__fmul_rn(g, w[it]));
+        }
+        B.wn[j] = g;  // kept for k_normalise, which overwrites it with the normalised weight
       }
     }
     s_q[0][pad8(m)] = q;
@@ -836,6 +844,8 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
 #pragma unroll
   for (int k = 0; k < N; ++k) run[k] = ex.v[k];
   bool seen = ex.f != 0;  // the current segment's head lies in this tile
+  // a thread inside one segment, as most are, writes nothing
+  if (head == 0u && tail == 0u && !(j0 <= last_valid && last_valid < j0 + SEG_ITEMS)) return;
 #pragma unroll
   for (int it = 0; it < SEG_ITEMS; ++it) {
     const uint32_t j = j0 + it;
@@ -1455,9 +1465,12 @@ __global__ void __launch_bounds__(NORM_BLOCK, 4) k_normalise(KParams P, DevBufs 
 #pragma unroll
   for (int k = 0; k < 5; ++k) agg.v[k] = 0.0f;
   if (has_pers) {
-    float ws[NORM_ITEMS];
+    float ws[NORM_ITEMS], gs[NORM_ITEMS];
     load_run<NORM_ITEMS>(B.key_sorted, j0, P.nu, key, 0xffffffffu);
     load_runf<NORM_ITEMS>(B.Ow, j0, P.nu, ws);
+    // the radar likelihood g of each particle, left in wn by k_segsum (for every particle of
+    // a cell with p_A > 0, which includes every cell with an effective p_A > 0)
+    if (RADAR) load_runf<NORM_ITEMS>(B.wn, j0, P.nu, gs);
     float4 st[NORM_ITEMS];
 #pragma unroll
     for (int it = 0; it < NORM_ITEMS; ++it) {
@@ -1495,8 +1508,7 @@ __global__ void __launch_bounds__(NORM_BLOCK, 4) k_normalise(KParams P, DevBufs 
         float wn;
         const float pa = RADAR ? __ldg(B.paeff + c) : 0.0f;
         if (RADAR && pa > 0.0f) {
-          const float g = radar_lik(P, st[it].x, st[it].y, mvx[it], mvy[it],
-                                    __ldg(B.zv + c), __ldg(B.sgv + c));
+          const float g = gs[it];
           const float a = __fmul_rn(__fmul_rn(__fmul_rn(pa, __ldg(B.muA + c)), g), w);
           const float b = __fmul_rn(__fmul_rn(__fsub_rn(1.0f, pa), muU), w);
           wn = __fadd_rn(a, b);
