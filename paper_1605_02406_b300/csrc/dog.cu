@@ -868,6 +868,7 @@ constexpr uint32_t NA_MAX_N = 1u << 19;      // particles per call
 constexpr uint32_t NA_MAX_CELLS = 1u << 22;  // cells per call (keys of at most 22 bits)
 constexpr uint32_t NA_TILES = NA_MAX_N / SORT_TILE;
 constexpr size_t NA_CTL = 256;
+static_assert(sizeof(DevCtl) <= NA_CTL, "the control block fits its slot");
 constexpr size_t NA_HIST = 2 * 2048 * 4;
 constexpr size_t NA_DCNT = (size_t)2 * NA_TILES * 2048 * 4;
 constexpr size_t NA_ARR = (size_t)NA_MAX_N * 4;

@@ -20,9 +20,12 @@ struct DevCtl {
   unsigned long long W_total;
   unsigned long long u_offset;  // systematic resampling offset u in [0, W_total)
   float w_new;                   // resampled weight (W_total 2^-40) / nu
-  float inv_w;                   // 1 / W_total (binary32 estimate for the source ranges)
+  float inv_w;                   // 1 / W_total (binary32 estimate for the output counts)
   uint32_t post_mode;            // posterior held as POST_RESAMPLED or POST_DIRECT
-  uint32_t pad[5];
+  // resampling thresholds theta_i = floor((i W + u) / nu) = i th_a + th_c +
+  // floor((i th_b + th_e) / nu), from W = th_a nu + th_b and u = th_c nu + th_e
+  unsigned long long th_a, th_c;
+  uint32_t th_b, th_e;
 };
 
 // How the posterior particles are held between frames:

@@ -1017,9 +1017,72 @@ __device__ void resample_setup(const KParams &P, DevCtl *ctl, unsigned long long
   ctl->post_mode = POST_RESAMPLED;
   const U4 r = philox(0u, ctl->frame, TAG_RESAMPLE, P.seed_lo, P.seed_hi);
   const unsigned long long r64 = ((unsigned long long)r.a << 32) | r.b;
-  ctl->u_offset = __umul64hi(r64, Wt);
+  const unsigned long long u = __umul64hi(r64, Wt);
+  ctl->u_offset = u;
   ctl->w_new = (float)((__ull2double_rn(Wt) * 0x1p-40) / (double)P.nu);
   ctl->inv_w = __fdiv_rn(1.0f, u64_to_f32_approx(Wt));
+  ctl->th_a = Wt / P.nu;
+  ctl->th_b = (uint32_t)(Wt % P.nu);
+  ctl->th_c = u / P.nu;
+  ctl->th_e = (uint32_t)(u % P.nu);
+}
+
+// The systematic rule "output i takes the first source j with Q_j nu > i W + u" reads, for
+// integer Q_j, Q_j > theta_i with theta_i = floor((i W + u) / nu); theta_i < 2^64 and is
+// exact in 64-bit arithmetic from the split W = a nu + b, u = c nu + e:
+// theta_i = i a + c + floor((i b + e) / nu), where i b + e < 2^51.
+struct Theta {
+  unsigned long long a, c;
+  uint32_t b, e, nu;
+  float inv_nu;
+};
+__device__ __forceinline__ Theta theta_of(const DevCtl *ctl, uint32_t nu) {
+  return Theta{ctl->th_a, ctl->th_c, ctl->th_b, ctl->th_e, nu, __fdiv_rn(1.0f, (float)nu)};
+}
+__device__ __forceinline__ unsigned long long theta_at(const Theta &T, uint32_t i, uint32_t *rem = nullptr) {
+  const unsigned long long r = (unsigned long long)i * T.b + T.e;
+  // floor(r / nu) lies in [0, i]: binary32 estimate (off by a few units at most), then
+  // exact corrections, with integer division if the estimate was far off
+  const float est = __fmul_rn(u64_to_f32_approx(r), T.inv_nu);
+  uint32_t q = !(est > 0.0f) ? 0u : (est >= (float)i ? i : (uint32_t)est);
+  int guard = 0;
+  while (q > 0u && (unsigned long long)q * T.nu > r && guard < 64) {
+    --q;
+    ++guard;
+  }
+  while ((unsigned long long)(q + 1u) * T.nu <= r && guard < 64) {
+    ++q;
+    ++guard;
+  }
+  if (guard >= 64) q = (uint32_t)(r / T.nu);
+  if (rem) *rem = (uint32_t)(r - (unsigned long long)q * T.nu);  // (i b + e) mod nu
+  return (unsigned long long)i * T.a + T.c + q;
+}
+// #{i in [0, nu) : theta_i < X}, i.e. #{i : i W + u < X nu}: binary32 estimate, exact
+// corrections (theta is non-decreasing), bisection if the estimate was far off
+__device__ __forceinline__ uint32_t count_theta_below(const Theta &T, unsigned long long X, float inv_w) {
+  const uint32_t nu = T.nu;
+  if (X <= T.c) return 0u;  // theta_0 = c
+  const float est = __fmul_rn(__fmul_rn(u64_to_f32_approx(X - T.c), (float)nu), inv_w);
+  uint32_t i = !(est > 0.0f) ? 0u : (est >= (float)nu ? nu : (uint32_t)est);
+  int guard = 0;
+  while (i > 0u && theta_at(T, i - 1u) >= X && guard < 32) {
+    --i;
+    ++guard;
+  }
+  while (i < nu && theta_at(T, i) < X && guard < 32) {
+    ++i;
+    ++guard;
+  }
+  if (guard >= 32) {
+    uint32_t lo = 0, hi = nu;
+    while (lo < hi) {
+      const uint32_t mid = lo + (hi - lo) / 2;
+      if (theta_at(T, mid) < X) lo = mid + 1; else hi = mid;
+    }
+    i = lo;
+  }
+  return i;
 }
 
 template <bool SETUP>
@@ -1629,55 +1692,36 @@ __global__ void __launch_bounds__(NORM_BLOCK) k_normalise_lidar(KParams P, DevBu
 
 // ====================================================================================
 // k_resample (Alg. 7, systematic): with joint inclusive fixed-point CDF Q, total W and one
-// uniform offset u in [0, W), output i takes the first source j with Q_j * nu > i W + u.
-// A block takes a tile of 2048 sources (8 consecutive per thread).  A thread finds its
-// first output i = #{i : i W + u < E nu} (E = CDF before its first source) from a binary32
-// estimate corrected in exact 128-bit arithmetic, then walks its sources in order with the
-// running value i W + u, handing each output to the source whose Q_j nu first exceeds it --
-// the definition itself, one comparison per output.  The source of each output goes to
-// shared memory and then to Bsrc in output order (coalesced): posterior particle i is the
-// record of source Bsrc[i] with the equal weight W 2^-40 / nu (Eq.
-// resampledParticleWeights), which the next prediction reads through the index.
+// uniform offset u in [0, W), output i takes the first source j with Q_j * nu > i W + u,
+// that is the first j with Q_j > theta_i = floor((i W + u) / nu) (see theta_at).  A block
+// takes a tile of 2048 sources: its inclusive CDF goes to shared memory, and its outputs
+// [#{i : theta_i < E}, #{i : theta_i < E'}) for the CDF E before and E' after the tile
+// (two counts at the start of the block) each find their source by binary
+// search in it -- the same work for every output whatever the weights are.  Sources are
+// written to Bsrc in output order (coalesced): posterior particle i is the record of source
+// Bsrc[i] with the equal weight W 2^-40 / nu (Eq. resampledParticleWeights), which the next
+// prediction reads through the index.
 // ====================================================================================
 constexpr int RES_BLOCK = 512, RES_ITEMS = NORM_TILE / RES_BLOCK;  // sources per thread
+constexpr int RES_RUN = 4;  // consecutive outputs per thread
 
-
-// #{i in [0, nu) : i W + u < X nu}, exactly
-__device__ __forceinline__ uint32_t count_below(unsigned long long X, unsigned long long Wt,
-                                                unsigned long long u, uint32_t nu, float inv_w) {
-  const U128 lim = mul_64x64(X, nu);
-  const float est = __fmul_rn(__fsub_rn(__fmul_rn(u64_to_f32_approx(X), (float)nu), u64_to_f32_approx(u)), inv_w);
-  uint32_t i = est <= 0.0f ? 0u : (est >= (float)nu ? nu : (uint32_t)ceilf(est));
-  int guard = 0;
-  while (i > 0u && !lt_128(add_128_64(mul_64x64(i - 1u, Wt), u), lim) && guard < 64) {
-    --i;
-    ++guard;
+// first y in [lo, hi] with Q[y] > th, hi if there is none (Q non-decreasing)
+__device__ __forceinline__ uint32_t first_above(const unsigned long long *Q, uint32_t lo, uint32_t hi,
+                                                unsigned long long th) {
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (Q[mid] > th) hi = mid; else lo = mid + 1u;
   }
-  while (i < nu && lt_128(add_128_64(mul_64x64(i, Wt), u), lim) && guard < 128) {
-    ++i;
-    ++guard;
-  }
-  if (guard >= 64) {  // the estimate was far off: bisection over [0, nu]
-    uint32_t lo = 0, hi = nu;
-    while (lo < hi) {
-      const uint32_t mid = lo + (hi - lo) / 2;
-      if (lt_128(add_128_64(mul_64x64(mid, Wt), u), lim)) lo = mid + 1; else hi = mid;
-    }
-    i = lo;
-  }
-  return i;
+  return lo;
 }
 
-constexpr int RES_OUT = 8192;  // outputs of a block staged in shared memory
-
 __global__ void __launch_bounds__(RES_BLOCK, 2) k_resample(KParams P, DevBufs B) {
-  __shared__ uint32_t s_src[RES_OUT];  // source of output o_lo + k
+  __shared__ unsigned long long s_Q[NORM_TILE];  // inclusive CDF at each source of the tile
   __shared__ unsigned long long s_wsum[RES_BLOCK / 32];
-  __shared__ uint32_t s_lo, s_hi;
+  __shared__ uint32_t s_o[2];
   const uint32_t tile = blockIdx.x;
   const uint32_t base = tile * NORM_TILE, ntot = P.nu + P.nu_b;
   const unsigned long long Wt = B.ctl->W_total;
-  const unsigned long long E = tile > 0 ? B.cdf_incl[tile - 1] : 0ull;
   if ((P.flags & 0x2u) != 0u || Wt == 0ull) {
     // no resampling: the persistent particles carry over in sorted order (POST_DIRECT)
     for (uint32_t i = base + threadIdx.x; i < min(base + NORM_TILE, P.nu); i += RES_BLOCK) {
@@ -1686,9 +1730,12 @@ __global__ void __launch_bounds__(RES_BLOCK, 2) k_resample(KParams P, DevBufs B)
     }
     return;
   }
-  const unsigned long long u = B.ctl->u_offset;
-  const float inv_w = B.ctl->inv_w;
-  // the thread's quantised weights and the CDF before its first source
+  const unsigned long long E = tile > 0 ? B.cdf_incl[tile - 1] : 0ull;
+  const Theta T = theta_of(B.ctl, P.nu);
+  // the tile's outputs [o_lo, o_hi): counted by two warps while the others load weights
+  if (threadIdx.x == 0) s_o[0] = count_theta_below(T, E, B.ctl->inv_w);
+  if (threadIdx.x == 32) s_o[1] = count_theta_below(T, B.cdf_incl[tile], B.ctl->inv_w);
+  // the thread's quantised weights and the tile's CDF
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t j0 = base + threadIdx.x * RES_ITEMS;
   float w[RES_ITEMS];
@@ -1717,29 +1764,42 @@ __global__ void __launch_bounds__(RES_BLOCK, 2) k_resample(KParams P, DevBufs B)
   __syncthreads();
   unsigned long long Q = E + inc - loc;
   for (uint32_t k = 0; k < warp; ++k) Q += s_wsum[k];
-  // first output of this thread, then the walk over its sources
-  uint32_t i = count_below(Q, Wt, u, P.nu, inv_w);
-  if (threadIdx.x == 0) s_lo = i;
-  __syncthreads();
-  const uint32_t o_lo = s_lo;
-  U128 acc = add_128_64(mul_64x64(i, Wt), u);  // i W + u
 #pragma unroll
   for (int it = 0; it < RES_ITEMS; ++it) {
     Q += q[it];
-    const U128 lim = mul_64x64(Q, P.nu);
-    const uint32_t j = j0 + it;
-    while (i < P.nu && lt_128(acc, lim)) {
-      if (i - o_lo < (uint32_t)RES_OUT) s_src[i - o_lo] = j;
-      else B.Bsrc[i] = j;  // beyond the staging buffer
-      ++i;
-      acc = add_128_64(acc, Wt);
+    s_Q[threadIdx.x * RES_ITEMS + it] = Q;
+  }
+  __syncthreads();
+  // every output of the tile has E <= theta < the tile's last Q, so the search ends inside
+  const uint32_t nS = min((uint32_t)NORM_TILE, ntot - base);
+  const uint32_t o_lo = s_o[0], o_hi = s_o[1];
+  // a thread takes RES_RUN consecutive outputs: the first by binary search over the tile,
+  // the next ones from theta_{x+1} = theta_x + a + [rem_x + b >= nu] and a forward scan
+  // (an output's source is never before the previous output's), bounded, then a search
+  for (uint32_t x0 = o_lo + RES_RUN * threadIdx.x; x0 < o_hi; x0 += RES_RUN * RES_BLOCK) {
+    uint32_t rem;
+    unsigned long long th = theta_at(T, x0, &rem);
+    uint32_t y = first_above(s_Q, 0u, nS - 1u, th);
+    B.Bsrc[x0] = base + y;
+#pragma unroll
+    for (int k = 1; k < RES_RUN; ++k) {
+      const uint32_t x = x0 + k;
+      if (x >= o_hi) break;
+      rem += T.b;  // < 2 nu
+      th += T.a;
+      if (rem >= T.nu) {
+        rem -= T.nu;
+        ++th;
+      }
+      int steps = 0;
+      while (y < nS - 1u && s_Q[y] <= th && steps < 4) {
+        ++y;
+        ++steps;
+      }
+      if (s_Q[y] <= th) y = first_above(s_Q, y, nS - 1u, th);
+      B.Bsrc[x] = base + y;
     }
   }
-  if (threadIdx.x == RES_BLOCK - 1) s_hi = i;
-  __syncthreads();
-  // sources in output order (coalesced)
-  const uint32_t o_hi = min(s_hi, o_lo + (uint32_t)RES_OUT);
-  for (uint32_t k = o_lo + threadIdx.x; k < o_hi; k += RES_BLOCK) B.Bsrc[k] = s_src[k - o_lo];
 }
 
 }  // namespace dog
