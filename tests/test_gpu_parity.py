@@ -182,6 +182,27 @@ def test_edge_cases(case):
     run_pair(p, 3, grids, state=st)
 
 
+def test_dominant_source_resampling():
+    """One particle carries nearly all of the filter's weight, so systematic resampling hands
+    almost every output to a single source (and the rest to a few others): the outputs of
+    one tile far exceed its sources, the case in which per-source work is most uneven."""
+    p = small(32, 32, nu=3 * 4096 + 17, nu_b=700, sigma_pos=0.0, sigma_vel=0.0)
+    W, H = p["width"], p["height"]
+    rng = np.random.default_rng(21)
+    st = scene.random_state(p, rng, occupied_frac=0.2)
+    c0 = 5 * W + 7
+    st["x"][0], st["y"][0] = np.float32((7 + 0.5) * p["cell_size"]), np.float32((5 + 0.5) * p["cell_size"])
+    st["vx"][0] = st["vy"][0] = np.float32(0.0)
+    st["w"][:] = np.float32(1e-9)
+    st["w"][0] = np.float32(0.95)
+    m_occ = np.zeros(W * H, np.float32)
+    m_free = np.full(W * H, 0.95, np.float32)
+    m_occ[c0], m_free[c0] = 0.95, 0.0
+    g, o = run_pair(p, 2, [dict(m_occ=m_occ, m_free=m_free)], state=st)
+    src = np.asarray(g.debug("RESAMPLE_SRC"))
+    assert np.bincount(src).max() > p["nu"] // 2  # one source took most outputs
+
+
 def test_checkpoint_resume_is_bit_exact():
     cfg = scene.CONFIGS["plain_128"]
     p = scene.filter_params(cfg)
