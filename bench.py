@@ -43,8 +43,12 @@ ALG_BYTES = {
     "k_sort_pass0": (12, 0, 0),   # read cell index 4; write (index, particle) pair 8
     "k_sort_pass1": (16, 0, 0),   # read pair 8; write pair 8
     "k_sort_pass2": (16, 0, 0),
-    "k_segsum": (48, 0, 0),       # read key 4 + perm 4 + gathered state 20; write sorted copy 20
-    "k_cell": (0, 0, 60),         # read S 8, tag 4, m_F 4, z_O 4, z_F 4; write 9 cell fields
+    # read key 4 + perm 4 + gathered record 16 (the weight follows from the out-of-grid flag
+    # after a resampled frame); write sorted copy 20
+    "k_segsum": (44, 0, 0),
+    # lidar: read the cell record 32 (S, tag, 5 moment sums), m_F, z_O, z_F 12; write 9 cell
+    # fields 36 and the 5 velocity moments 20
+    "k_cell": (0, 0, 100),
     "k_birth": (0, 20, 0),        # write newborn state 16 + weight 4
     "k_normalise": (12, 4, 0),    # lidar: read key 4, w 4, write w' 4; newborn w 4
     "k_resample": (8, 4, 0),      # read w' 4; write the source index 4; newborn w 4
