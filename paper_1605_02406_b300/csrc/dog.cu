@@ -117,6 +117,9 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
   B->A_piece = (unsigned long long *)take(8 * C);
   B->Mx = (unsigned long long *)take(8 * 5 * C);
   B->Mcnt = (uint32_t *)take(4 * C);
+  B->Pf = (float *)take(4 * 10 * (size_t)d.tiles_seg);
+  B->tile_whole = (uint32_t *)take(4 * (size_t)d.tiles_seg);
+  B->cross_t1 = (uint32_t *)take(4 * C);
   B->tile_q = (unsigned long long *)take(8 * (size_t)d.tiles_cell);
   B->tile_qin = (unsigned long long *)take(8 * (size_t)d.tiles_cell);
   B->tile_n = (uint32_t *)take(4 * (size_t)d.tiles_cell);

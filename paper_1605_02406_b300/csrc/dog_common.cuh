@@ -93,7 +93,12 @@ struct DevBufs {
   uint32_t *dcnt;                  // [passes][tiles_sort][radix] digit counts of each sort
                                    // tile, turned into global output offsets in place
   unsigned long long *S_piece, *A_piece;  // [C] pieces of cells spread over several tiles
-  unsigned long long *Mx;          // [5][C] moment pieces
+  unsigned long long *Mx;          // [5][C] moment pieces (radar normalisation)
+  float *Pf;                       // [tiles_seg][2][5] lidar moment sums of a segment tile's
+                                   // first segment begun earlier (or the whole tile) and of
+                                   // its last segment continued later
+  uint32_t *tile_whole;            // [tiles_seg] 1: the tile lies inside one cell
+  uint32_t *cross_t1;              // [C] first segment tile of a cell spread over tiles
   uint32_t *Mcnt;                  // [C] pieces counted in so far
   unsigned long long *tile_q, *tile_qin;  // [tiles_cell] newborn mass per tile, inclusive
   uint32_t *tile_n, *tile_nin;             // [tiles_cell] birth cells per tile, inclusive

@@ -878,8 +878,9 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
 // is w' = (rho_p / S_c) w, so the weight each moment uses, w' / rho_p, equals w / S_c: the
 // moments follow from the predicted weights here, one pass earlier than the normalisation.
 // w v, w v^2, w vx vy are summed per cell in binary32 by the same block-wide segmented
-// scan; a cell inside the tile is finished here, a cell spread over tiles adds its pieces
-// in exact 2^-40 fixed point and k_cell finishes it.
+// scan; a cell inside the tile is finished here; a cell spread over tiles adds the pieces
+// of S in exact 2^-40 fixed point and leaves its binary32 moment pieces in per-tile slots,
+// which k_cell adds in tile order.
 __global__ void __launch_bounds__(SEG_BLOCK, 4) k_segsum_lidar(KParams P, DevBufs B) {
   __shared__ SegQM s_wqm[SEG_BLOCK / 32 + 1];
   __shared__ float s_x[3][SEG_TILE + SEG_TILE / 8];  // w, vx, vy in tile order (padded)
@@ -954,7 +955,6 @@ __global__ void __launch_bounds__(SEG_BLOCK, 4) k_segsum_lidar(KParams P, DevBuf
 #pragma unroll
   for (int k = 0; k < 5; ++k) rm[k] = ex.m[k];
   bool seen = ex.f != 0;  // the current segment's head lies in this tile
-  const size_t Cs = P.C;
   const bool record = (P.flags & 0x4u) != 0u;
   // the running sums are only read at a segment's end (or the tile's last particle): a
   // thread inside one segment, as most are, has nothing more to do
@@ -978,15 +978,21 @@ __global__ void __launch_bounds__(SEG_BLOCK, 4) k_segsum_lidar(KParams P, DevBuf
       if (h) B.cstart[c] = j;
       if (t) B.cend[c] = j + 1;
     }
+    if (j == last_valid) B.tile_whole[tile] = (!t && !seen) ? 1u : 0u;
     if (t && seen) {  // the whole cell lies in this tile: one 32-byte record
       float o[5];
       moments_of_sums(rm, rq, o);
       csum_store_head(B.csum + c, rq, frame << 1, o[0]);
       *reinterpret_cast<float4 *>(&B.csum[c].m[1]) = make_float4(o[1], o[2], o[3], o[4]);
     } else if (t || j == last_valid) {  // a piece of a cell spread over several tiles
+      // S exactly in fixed point; the moment sums in binary32 in this tile's slot (0: the
+      // cell began in an earlier tile, 1: it continues in a later one), which k_cell adds in
+      // tile order (full relative precision however small the weights are)
       atomicAdd(B.S_piece + c, rq);
+      float *slot = B.Pf + ((size_t)tile * 2u + (seen ? 1u : 0u)) * 5u;
 #pragma unroll
-      for (int k = 0; k < 5; ++k) atomicAdd(B.Mx + k * Cs + c, q40s(rm[k]));
+      for (int k = 0; k < 5; ++k) slot[k] = rm[k];
+      if (seen) B.cross_t1[c] = tile;
       if (t) B.csum[c].tag = (frame << 1) | 1u;
     }
   }
@@ -1258,10 +1264,18 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
       B.muA[c] = muA;
       if constexpr (!RADAR) {  // moments of the lidar filter (see k_segsum_lidar)
         float o[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        if (cross) {
+        if (cross) {  // the cell's pieces in tile order: first, whole tiles, last
+          uint32_t t = B.cross_t1[c];
           float mm[5];
+          const float *first = B.Pf + ((size_t)t * 2u + 1u) * 5u;
 #pragma unroll
-          for (int k = 0; k < 5; ++k) mm[k] = fx40s_to_f(atomicExch(B.Mx + (size_t)k * P.C + c, 0ull));
+          for (int k = 0; k < 5; ++k) mm[k] = first[k];
+          for (++t; t < P.tiles_seg; ++t) {
+            const float *pc = B.Pf + (size_t)t * 10u;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) mm[k] = __fadd_rn(mm[k], pc[k]);
+            if (!B.tile_whole[t]) break;
+          }
           moments_of_sums(mm, rp > 0.0f ? S : 0ull, o);
         } else if (occ && rp > 0.0f) {  // finished by the segment pass
           const float4 r = *reinterpret_cast<const float4 *>(&B.csum[c].m[1]);
