@@ -362,7 +362,7 @@ def main() -> None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
     value = world * params["nu"] * args.steps / (ms_max * 1e-3)
-    launches = args.steps * (f.kernels_per_step() + 1)  # + the grid validation kernel
+    launches = args.steps * (f.kernels_per_step() + 1)  # + the grid take-over kernel
     cells_check = f.cells(["m_occ"])["m_occ"]
     assert np.isfinite(cells_check).all()
     f.close()
@@ -375,17 +375,23 @@ def main() -> None:
 
     out2 = [out, {k: torch.empty(C, dtype=torch.float32).pin_memory() for k in out}]
 
-    def e2e_step(k):
-        # upload frame k (overlapping frame k - 1 on the GPU; each frame has its own pinned
-        # buffers, reused only frames later), step, start reading its cells back; the
-        # read-back of frame k - 1 is complete when the call returns
-        g = pin[k % n_grids]
+    def upload(k):
+        g = pin[k % n_grids]  # each frame has its own pinned buffers, reused frames later
         N.dog_set_measurement_grid(fe.h, {kk: v.data_ptr() for kk, v in g.items()}, N.DOG_HOST_ASYNC)
+
+    def e2e_step(k):
+        # step frame k (its grid is already uploaded or on its way), upload frame k + 1 so
+        # that the copy overlaps frame k on the GPU, then start reading frame k's cells back;
+        # the read-back of frame k - 1 is complete when that call returns
         N.dog_step(fe.h, cfg["dt"])
+        upload(k + 1)
         N.dog_get_cells_async(fe.h, {kk: v.data_ptr() for kk, v in out2[k % 2].items()})
 
+    upload(0)
     for k in range(args.warmup):
         e2e_step(k)
+    N.dog_wait_cells(fe.h)
+    torch.cuda.synchronize()
     barrier()
     ke = min(args.steps, 100)
     t0 = time.perf_counter()

@@ -145,8 +145,10 @@ int dog_get_cells(dog_filter *f, const dog_cells *out, int mem_kind);
  * are copied on the device in stream order -- the next dog_step may be issued at once -- and
  * from there to the host on the filter's read-back stream.  The arrays are valid after
  * dog_wait_cells returns.  One read-back may be in flight per filter: a second call first
- * waits for the previous one.  Errors latched by the frames before the read-back (input
- * validation) are returned by dog_wait_cells.  Errors: INVALID_ARG, CUDA. */
+ * waits for the previous one.  Errors latched in stream order before the snapshot (input
+ * validation of any grid set before this call) are returned by dog_wait_cells.  To keep
+ * the GPU busy, upload the next frame's grid (DOG_HOST_ASYNC) before this call: dog_step(k),
+ * dog_set_measurement_grid(k + 1), dog_get_cells_async(k).  Errors: INVALID_ARG, CUDA. */
 int dog_get_cells_async(dog_filter *f, const dog_cells *out);
 
 /* Block until the read-back started by dog_get_cells_async has arrived (DOG_OK at once if

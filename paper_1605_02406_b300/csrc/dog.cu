@@ -563,11 +563,10 @@ int dog_set_measurement_grid(dog_filter *f, const dog_meas_grid *g, int mem_kind
   if (radar && (!g->z_vr || !g->sigma_vr)) return DOG_ERR_INVALID_ARG;
   const size_t C = f->d.C;
   const float *src[5] = {g->m_occ, g->m_free, g->p_A, g->z_vr, g->sigma_vr};
-  float *dst[5] = {f->B.zO, f->B.zF, f->B.pA, f->B.zv, f->B.sgv};
   const int nfield = radar ? 5 : 2;
+  GridSrc gs{};
   if (mem_kind == DOG_DEVICE) {
-    for (int k = 0; k < nfield; ++k)
-      DOG_CUDA(cudaMemcpyAsync(dst[k], src[k], 4 * C, cudaMemcpyDeviceToDevice, f->st));
+    for (int k = 0; k < nfield; ++k) gs.f[k] = src[k];
   } else {
     // upload on the copy stream into the staging buffer (free once the previous grid was
     // taken over), so that it overlaps the frame in flight; then take it over in stream order
@@ -576,12 +575,12 @@ int dog_set_measurement_grid(dog_filter *f, const dog_meas_grid *g, int mem_kind
       DOG_CUDA(cudaMemcpyAsync(f->B.g_stage + k * C, src[k], 4 * C, cudaMemcpyHostToDevice, f->h2d));
     DOG_CUDA(cudaEventRecord(f->ev_h2d, f->h2d));
     DOG_CUDA(cudaStreamWaitEvent(f->st, f->ev_h2d, 0));
-    for (int k = 0; k < nfield; ++k) k_copy<<<592, 256, 0, f->st>>>(f->B.g_stage + k * C, dst[k], C);
-    DOG_CUDA(cudaGetLastError());
-    DOG_CUDA(cudaEventRecord(f->ev_stage_free, f->st));
+    for (int k = 0; k < nfield; ++k) gs.f[k] = f->B.g_stage + k * C;
   }
-  k_validate<<<256, 256, 0, f->st>>>(f->K, f->B, radar ? 1 : 0);
+  // copy into place and validate in one pass
+  k_take_grid<<<592, 256, 0, f->st>>>(f->K, f->B, gs, radar ? 1 : 0);
   DOG_CUDA(cudaGetLastError());
+  if (mem_kind != DOG_DEVICE) DOG_CUDA(cudaEventRecord(f->ev_stage_free, f->st));
   f->radar = radar;
   f->has_grid = true;
   // host arrays: the caller may reuse them once the upload is done (DOG_HOST_ASYNC: the
@@ -661,11 +660,10 @@ int dog_get_cells_async(dog_filter *f, const dog_cells *out) {
   // snapshot in stream order (the next frame may then overwrite the cells), copy to the host
   // on the read-back stream
   uint32_t *err_snap = reinterpret_cast<uint32_t *>(f->B.c_stage + 10 * C);
-  for (int k = 0; k < 10; ++k)
-    if (dst[k]) k_copy<<<592, 256, 0, f->st>>>(src[k], f->B.c_stage + k * C, C);
-  k_copy<<<1, 32, 0, f->st>>>(reinterpret_cast<const float *>(&f->B.ctl->err), reinterpret_cast<float *>(err_snap), 1);
+  CellSnap snap{};
+  for (int k = 0; k < 10; ++k) snap.f[k] = dst[k] ? src[k] : nullptr;
+  k_snapshot<<<592, 256, 0, f->st>>>(snap, f->B.c_stage, (uint32_t)C, &f->B.ctl->err, err_snap);
   DOG_CUDA(cudaGetLastError());
-  DOG_CUDA(cudaMemsetAsync(&f->B.ctl->err, 0, 4, f->st));
   DOG_CUDA(cudaEventRecord(f->ev_snap, f->st));
   DOG_CUDA(cudaStreamWaitEvent(f->d2h, f->ev_snap, 0));
   for (int k = 0; k < 10; ++k)

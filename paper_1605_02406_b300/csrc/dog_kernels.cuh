@@ -73,20 +73,6 @@ __global__ void k_gather_posterior(KParams P, DevBufs B, float *__restrict__ out
   }
 }
 
-// device-to-device copy of n floats by the SMs (the copy engines stay free for the host
-// transfers that overlap the frame); 16-byte accesses where both ends allow
-__global__ void k_copy(const float *__restrict__ src, float *__restrict__ dst, size_t n) {
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  if ((((uintptr_t)src | (uintptr_t)dst) & 15) == 0) {
-    const size_t n4 = n / 4;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += stride)
-      reinterpret_cast<float4 *>(dst)[i] = __ldg(reinterpret_cast<const float4 *>(src) + i);
-    for (size_t i = 4 * n4 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
-  } else {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
-  }
-}
-
 // ====================================================================================
 // record <-> plain arrays (state checkpoint and diagnostics; not on the per-frame path)
 // ====================================================================================
@@ -104,20 +90,53 @@ __global__ void k_pack(const float *__restrict__ in /* [4][n] */, uint32_t n, fl
     rec[i] = make_float4(in[i], in[n + i], in[2 * (size_t)n + i], in[3 * (size_t)n + i]);
 }
 
+// snapshot for an asynchronous read-back: the requested cell fields (null = skipped) into
+// the read-back staging buffer, and the error word (then cleared), in one launch
+struct CellSnap {
+  const float *f[10];
+};
+
+__global__ void k_snapshot(CellSnap src, float *__restrict__ stage, uint32_t C, uint32_t *err,
+                           uint32_t *err_snap) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    if (!src.f[k]) continue;  // uniform
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += stride)
+      stage[(size_t)k * C + c] = __ldg(src.f[k] + c);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *err_snap = *err;
+    *err = 0u;
+  }
+}
+
 // ====================================================================================
-// k_validate: measurement grid domain check (device-resident input)
+// the measurement grid of the next frame: copied into place from the staging buffer or the
+// caller's device arrays and validated in the same pass (m_O, m_F in [0, 1] with sum <= 1;
+// radar: p_A in [0, 1], sigma_vr > 0 where p_A > 0, z_vr finite); a violation latches
+// ERR_INPUT
 // ====================================================================================
-__global__ void k_validate(KParams P, DevBufs B, int radar) {
+struct GridSrc {
+  const float *f[5];  // m_occ, m_free, p_A, z_vr, sigma_vr (the last three: radar only)
+};
+
+__global__ void k_take_grid(KParams P, DevBufs B, GridSrc src, int radar) {
   const uint32_t stride = gridDim.x * blockDim.x;
   bool bad = false;
   for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < P.C; c += stride) {
-    const float a = B.zO[c], b = B.zF[c];
+    const float a = __ldg(src.f[0] + c), b = __ldg(src.f[1] + c);
+    B.zO[c] = a;
+    B.zF[c] = b;
     bad |= !(a >= 0.0f && a <= 1.0f && b >= 0.0f && b <= 1.0f && a + b <= 1.000001f);
     if (radar) {
-      const float pa = B.pA[c];
+      const float pa = __ldg(src.f[2] + c), zv = __ldg(src.f[3] + c), sg = __ldg(src.f[4] + c);
+      B.pA[c] = pa;
+      B.zv[c] = zv;
+      B.sgv[c] = sg;
       bad |= !(pa >= 0.0f && pa <= 1.0f);
-      bad |= (pa > 0.0f) && !(B.sgv[c] > 0.0f);
-      bad |= !(fabsf(B.zv[c]) < 3.0e38f);
+      bad |= (pa > 0.0f) && !(sg > 0.0f);
+      bad |= !(fabsf(zv) < 3.0e38f);
     }
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&B.ctl->err, ERR_INPUT);
