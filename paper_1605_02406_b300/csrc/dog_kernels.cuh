@@ -1411,7 +1411,7 @@ __device__ __forceinline__ void birth_init(const KParams &P, const DevBufs &B, u
 // cell order (entry G = birth cells of earlier tiles + position in the tile); and, for each
 // block of BIRTH_SLOTS slots, the entry that owns the block's first slot.  One block per
 // cell tile.
-constexpr int BIRTH_SLOTS = 2048, BIRTH_CACHE = 2048;
+constexpr int BIRTH_SLOTS = 512, BIRTH_CACHE = 2048;
 
 template <bool RADAR>
 __global__ void __launch_bounds__(CELL_BLOCK) k_birth_prep(KParams P, DevBufs B) {
@@ -1738,6 +1738,25 @@ __global__ void __launch_bounds__(NORM_BLOCK) k_normalise_lidar(KParams P, DevBu
 constexpr int RES_BLOCK = 512, RES_ITEMS = NORM_TILE / RES_BLOCK;  // sources per thread
 constexpr int RES_RUN = 4;  // consecutive outputs per thread
 
+// count_theta_below by a warp: the 32 indices around the binary32 estimate are tested at
+// once (theta is non-decreasing, so the lanes below the count form a prefix); outside that
+// window, the serial count
+__device__ __forceinline__ uint32_t count_theta_below_warp(const Theta &T, unsigned long long X, float inv_w,
+                                                           uint32_t lane) {
+  if (X <= T.c) return 0u;  // warp-uniform
+  const uint32_t nu = T.nu;
+  const float est = __fmul_rn(__fmul_rn(u64_to_f32_approx(X - T.c), (float)nu), inv_w);
+  const uint32_t i0 = !(est > 0.0f) ? 0u : (est >= (float)nu ? nu : (uint32_t)est);
+  const uint32_t base = i0 > 16u ? i0 - 16u : 0u;
+  const uint32_t cand = base + lane;
+  const bool below = cand < nu && theta_at(T, cand) < X;
+  const uint32_t k = (uint32_t)__popc(__ballot_sync(FULL, below));
+  if ((k > 0u || base == 0u) && (k < 32u || base + 32u >= nu)) return base + k;
+  uint32_t r = 0u;
+  if (lane == 0u) r = count_theta_below(T, X, inv_w);
+  return __shfl_sync(FULL, r, 0);
+}
+
 // first y in [lo, hi] with Q[y] > th, hi if there is none (Q non-decreasing)
 __device__ __forceinline__ uint32_t first_above(const unsigned long long *Q, uint32_t lo, uint32_t hi,
                                                 unsigned long long th) {
@@ -1766,10 +1785,13 @@ __global__ void __launch_bounds__(RES_BLOCK, 2) k_resample(KParams P, DevBufs B)
   const unsigned long long E = tile > 0 ? B.cdf_incl[tile - 1] : 0ull;
   const Theta T = theta_of(B.ctl, P.nu);
   // the tile's outputs [o_lo, o_hi): counted by two warps while the others load weights
-  if (threadIdx.x == 0) s_o[0] = count_theta_below(T, E, B.ctl->inv_w);
-  if (threadIdx.x == 32) s_o[1] = count_theta_below(T, B.cdf_incl[tile], B.ctl->inv_w);
-  // the thread's quantised weights and the tile's CDF
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp < 2u) {
+    const unsigned long long X = warp == 0u ? E : B.cdf_incl[tile];
+    const uint32_t cnt = count_theta_below_warp(T, X, B.ctl->inv_w, lane);
+    if (lane == 0u) s_o[warp] = cnt;
+  }
+  // the thread's quantised weights and the tile's CDF
   const uint32_t j0 = base + threadIdx.x * RES_ITEMS;
   float w[RES_ITEMS];
   if (j0 + RES_ITEMS <= P.nu) {
