@@ -157,6 +157,7 @@ struct dog_filter {
   int ring_head = 0, ring_count = 0;
   int nk = 0;
   int birth_grid = 1;
+  uint32_t count_ct = 1;  // sort tiles per k_sort_count block
   // host I/O overlapped with compute: grid uploads and cell read-backs on their own streams
   cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaEvent_t ev_h2d = nullptr, ev_stage_free = nullptr, ev_snap = nullptr, ev_d2h = nullptr;
@@ -211,7 +212,8 @@ int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
       vout = B.val_t1;
     }
     if (p > 0) {
-      k_sort_count<<<K.tiles_sort, COUNT_BLOCK, 4u * K.radix, st>>>(K, B, kin, p);
+      k_sort_count<<<(K.tiles_sort + f->count_ct - 1) / f->count_ct, COUNT_BLOCK,
+                     count_smem_bytes(K.radix, f->count_ct), st>>>(K, B, kin, p, f->count_ct);
       ++k; mark();
     }
     k_sort_offsets<<<K.radix, OFF_BLOCK, 0, st>>>(K, B, p);
@@ -401,10 +403,14 @@ int dog_create(const dog_params *params, void *d_workspace, size_t workspace_byt
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   f->birth_grid = (int)((params->num_birth + BIRTH_SLOTS - 1) / BIRTH_SLOTS);
+  f->count_ct = count_tiles_per_block(d.tiles_sort, sms);
   if (f->birth_grid < 1) f->birth_grid = 1;
   // the attribute is per kernel, shared by all filters: allow the largest digit's need
   cudaError_t e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sort_smem_bytes(2048));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sort_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)count_smem_bytes(2048, COUNT_TILES));
   if (e == cudaSuccess) e = cudaMemsetAsync(f->ws, 0, need, f->st);
   if (e == cudaSuccess) {
     k_init<<<sms * 8, 256, 0, f->st>>>(K, f->B);
@@ -932,6 +938,8 @@ int na_setup(char **base) {
     DOG_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
     DOG_CUDA(cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sort_smem_bytes(2048)));
+    DOG_CUDA(cudaFuncSetAttribute(k_sort_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)count_smem_bytes(2048, COUNT_TILES)));
     g_na_dev[dev].base = (char *)p;
     g_na_dev[dev].ready = true;
   }
@@ -974,11 +982,20 @@ extern "C" int dog_assign_cells_noalloc(const uint32_t *d_keys, uint32_t n, uint
   k_tick<<<1, 256, 0, st>>>(B, 2048 * K.passes);
   k_na_hist<<<K.tiles_sort, 256, 4u * K.passes * K.radix, st>>>(d_keys, K, B);
   const size_t ssm = sort_smem_bytes(K.radix);
+  int sms = 148;
+  {
+    int dev = 0;
+    DOG_CUDA(cudaGetDevice(&dev));
+    DOG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const uint32_t ct = count_tiles_per_block(K.tiles_sort, sms);
   const uint32_t *kin = d_keys, *vin = nullptr;
   for (int p = 0; p < K.passes; ++p) {
     uint32_t *kout = (p == K.passes - 1) ? key_sorted : key_t0;
     uint32_t *vout = (p == K.passes - 1) ? d_perm : val_t0;
-    if (p > 0) k_sort_count<<<K.tiles_sort, COUNT_BLOCK, 4u * K.radix, st>>>(K, B, kin, p);
+    if (p > 0)
+      k_sort_count<<<(K.tiles_sort + ct - 1) / ct, COUNT_BLOCK, count_smem_bytes(K.radix, ct), st>>>(K, B, kin,
+                                                                                                       p, ct);
     k_sort_offsets<<<K.radix, OFF_BLOCK, 0, st>>>(K, B, p);
     k_sort_pass<<<K.tiles_sort, SORT_BLOCK, ssm, st>>>(K, B, kin, vin, kout, vout, p);
     kin = kout;

@@ -320,32 +320,78 @@ __device__ void block_excl_scan_u32(const uint32_t *in, uint32_t *out, uint32_t 
   __syncthreads();
 }
 
-// k_sort_count: digit counts of one pass's tiles (block t counts keys [4096 t, 4096 t + 4096)
-// of the pass's input)
-constexpr int COUNT_BLOCK = 256;
+// k_sort_count: digit counts of one pass's tiles in the output of the pass before.  A block
+// counts ct consecutive tiles (ct = 1, 2, 4 or 8, the most that still leaves two blocks per
+// SM; 16-byte key loads, shared-memory counters per tile), so that each digit's counts of
+// those tiles are contiguous in its row of the digit-major table and go out as 16-byte
+// (or 8-byte) stores instead of ct separate 4-byte ones
+constexpr int COUNT_BLOCK = 512, COUNT_TILES = 8;  // at most
+
+__host__ __device__ constexpr size_t count_smem_bytes(uint32_t radix, uint32_t ct) {
+  return (size_t)ct * radix * 4;
+}
+inline uint32_t count_tiles_per_block(uint32_t tiles, int sms) {
+  uint32_t ct = COUNT_TILES;
+  while (ct > 1u && tiles / ct < 2u * (uint32_t)sms) ct >>= 1;
+  return ct;
+}
 
 __global__ void __launch_bounds__(COUNT_BLOCK) k_sort_count(KParams P, DevBufs B,
-                                                            const uint32_t *__restrict__ keys, int pass) {
-  extern __shared__ uint32_t sh_cnt[];  // [radix]
+                                                            const uint32_t *__restrict__ keys, int pass,
+                                                            uint32_t ct) {
+  extern __shared__ uint32_t sh_cnt[];  // [ct][radix]
   const uint32_t radix = P.radix, mask = radix - 1u;
   const int shift = pass * P.dbits;
-  for (uint32_t d = threadIdx.x; d < radix; d += COUNT_BLOCK) sh_cnt[d] = 0u;
+  for (uint32_t k = threadIdx.x; k < ct * radix; k += COUNT_BLOCK) sh_cnt[k] = 0u;
   __syncthreads();
-  const uint32_t base = blockIdx.x * SORT_TILE;
-  constexpr int N = SORT_TILE / COUNT_BLOCK;
-  uint32_t k[N];  // all loads in flight before the first count
+  const uint32_t t0 = blockIdx.x * ct;
+  const uint32_t base = t0 * SORT_TILE;
+  const uint32_t end = min(base + ct * SORT_TILE, P.nu);
+  // four consecutive keys per thread and step (the same tile: SORT_TILE % 4 == 0); equal
+  // neighbouring digits are added together
+  for (uint32_t i = base + 4 * threadIdx.x; i < end; i += 4 * COUNT_BLOCK) {
+    uint32_t k4[4];
+    if (i + 4 <= end) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4 *>(keys + i));
+      k4[0] = v.x; k4[1] = v.y; k4[2] = v.z; k4[3] = v.w;
+    } else {
 #pragma unroll
-  for (int it = 0; it < N; ++it) {
-    const uint32_t i = base + it * COUNT_BLOCK + threadIdx.x;
-    k[it] = i < P.nu ? __ldg(keys + i) : 0xffffffffu;
+      for (int j = 0; j < 4; ++j) k4[j] = i + j < end ? __ldg(keys + i + j) : 0xffffffffu;
+    }
+    uint32_t *cnt = sh_cnt + ((i - base) / SORT_TILE) * radix;
+    uint32_t cur = 0xffffffffu, run = 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (k4[j] == 0xffffffffu) continue;  // past the end
+      const uint32_t d = (k4[j] >> shift) & mask;
+      if (d != cur) {
+        if (run) atomicAdd(cnt + cur, run);
+        cur = d;
+        run = 0u;
+      }
+      ++run;
+    }
+    if (run) atomicAdd(cnt + cur, run);
   }
-#pragma unroll
-  for (int it = 0; it < N; ++it)
-    if (k[it] != 0xffffffffu) atomicAdd(&sh_cnt[(k[it] >> shift) & mask], 1u);
   __syncthreads();
   uint32_t *col = B.dcnt + (size_t)pass * radix * P.tiles_sort;
-  for (uint32_t d = threadIdx.x; d < radix; d += COUNT_BLOCK)
-    col[(size_t)d * P.tiles_sort + blockIdx.x] = sh_cnt[d];
+  const uint32_t nt = min(ct, P.tiles_sort - t0);
+  // rows start on 16-byte (8-byte) boundaries when tiles_sort is a multiple of 4 (2), and so
+  // does this block's run t0 = blockIdx.x * ct
+  const bool v4 = nt == ct && ct % 4u == 0u && P.tiles_sort % 4u == 0u;
+  const bool v2 = nt == ct && ct == 2u && P.tiles_sort % 2u == 0u;
+  for (uint32_t d = threadIdx.x; d < radix; d += COUNT_BLOCK) {
+    uint32_t *row = col + (size_t)d * P.tiles_sort + t0;
+    if (v4) {
+      for (uint32_t t = 0; t < ct; t += 4)
+        *reinterpret_cast<uint4 *>(row + t) = make_uint4(sh_cnt[t * radix + d], sh_cnt[(t + 1) * radix + d],
+                                                         sh_cnt[(t + 2) * radix + d], sh_cnt[(t + 3) * radix + d]);
+    } else if (v2) {
+      *reinterpret_cast<uint2 *>(row) = make_uint2(sh_cnt[d], sh_cnt[radix + d]);
+    } else {
+      for (uint32_t t = 0; t < nt; ++t) row[t] = sh_cnt[t * radix + d];
+    }
+  }
 }
 
 // k_sort_offsets: for one pass, counts[d][t] -> (sum of the histogram below digit d) +
