@@ -50,6 +50,7 @@ typedef enum dog_status {
 #define DOG_RECORD 0x4u      /* also keep newborn cells/sets and explicit cell ranges     */
 #define DOG_NO_GRAPH 0x8u    /* issue kernels one by one instead of a captured graph     */
 #define DOG_PROFILE 0x10u    /* time each kernel with CUDA events (dog_profile_read)      */
+#define DOG_EGO 0x20u        /* the grid moves with the vehicle: dog_set_ego_motion         */
 
 /* memory kind of caller buffers */
 #define DOG_HOST 0
@@ -130,6 +131,20 @@ int dog_create(const dog_params *params, void *d_workspace, size_t workspace_byt
  * is latched and reported as DOG_ERR_INPUT by the next synchronising call (dog_sync,
  * dog_get_cells, dog_wait_cells, ...); the frames stepped with that grid are void. */
 int dog_set_measurement_grid(dog_filter *f, const dog_meas_grid *grid, int mem_kind);
+
+/* Ego-motion compensation for the next dog_step (filters created with DOG_EGO; the paper's
+ * experiments compensate the vehicle's motion from speed and yaw rate, Sect. VIII, without
+ * fixing how).  The grid is attached to the vehicle, the sensor at (sensor_x, sensor_y):
+ * since the previous frame the vehicle moved by (dx, dy) m, in the previous grid's axes,
+ * and turned by dyaw rad (counter-clockwise) about the sensor position.  At the start of
+ * the next step every posterior particle enters the new grid at q + R(-dyaw)(p - q - d)
+ * with velocity R(-dyaw) v (q the sensor position, d = (dx, dy)), before the process model;
+ * the posterior free mass of each new cell is read at the old cell under its centre,
+ * q + R(dyaw)(c - q) + d (nearest cell; 0 outside the old grid).  cos and sin of dyaw are
+ * taken in binary64 and rounded to binary32 once.  Applies to one step; a step without a
+ * call keeps the grid where it is.  Asynchronous (the values are passed by value).
+ * Errors: INVALID_ARG (non-finite argument), BAD_STATE (filter without DOG_EGO). */
+int dog_set_ego_motion(dog_filter *f, float dx, float dy, float dyaw);
 
 /* One recursion of the filter with time step dt (s): Alg. 1-7 of Sect. VII.
  * Asynchronous.  Errors: INVALID_ARG (dt not finite or < 0), BAD_STATE (no measurement

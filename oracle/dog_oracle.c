@@ -78,6 +78,9 @@ typedef struct {
   uint8_t *bassoc;                /* [nu_b] 1 = associated set */
   uint32_t *rsrc;                 /* [nu] resampled source index (joint index space) */
   uint64_t Wq, RC, u;
+  /* ego motion to apply at the start of the next step (oracle_set_ego_motion) */
+  int ego_on;
+  real ego_c, ego_s, ego_dx, ego_dy;
 } oracle;
 
 /* ------------------------------------------------------------------------------------
@@ -408,6 +411,71 @@ static void cell_update(real mp, real mF_prev, real zO, real zF, real alpha, rea
   *mFp_out = mFp;
 }
 
+/* Ego-motion compensation (the paper's experiments compensate the vehicle's motion, from
+ * speed and yaw rate, in the grid map, Sect. VIII, without saying how).  Reading: the grid
+ * is attached to the vehicle with the sensor at q = (sensor_x, sensor_y); since the
+ * previous frame the vehicle moved by d = (dx, dy) in the previous grid's axes and turned
+ * by theta about q.  Before the next prediction every posterior particle is expressed in
+ * the new grid, p' = q + R(-theta)(p - q - d), v' = R(-theta) v, and the posterior free
+ * mass of each new cell is that of the old cell under its centre c, q + R(theta)(c - q) + d
+ * (0 when that lies outside the old grid).  cos and sin of theta come from binary64 libm,
+ * rounded once in the FP32 mirror.  One call applies to one step. */
+void oracle_set_ego_motion(oracle *o, float dx, float dy, float dyaw) {
+  o->ego_on = (dx != 0.0f || dy != 0.0f || dyaw != 0.0f);
+  o->ego_c = (real)cos((double)dyaw);
+  o->ego_s = (real)sin((double)dyaw);
+  o->ego_dx = (real)dx;
+  o->ego_dy = (real)dy;
+}
+
+static void apply_ego_motion(oracle *o) {
+  const or_params *p = &o->p;
+  const int64_t C = o->C;
+  const int W = p->width, H = p->height;
+  const real qx = (real)p->sensor_x, qy = (real)p->sensor_y, s = (real)p->cell_size;
+  const real c = o->ego_c, sn = o->ego_s, dx = o->ego_dx, dy = o->ego_dy;
+  for (uint32_t i = 0; i < p->nu; ++i) {
+    real ax = o->x[i] - qx;
+    real rx = ax - dx;
+    real ay = o->y[i] - qy;
+    real ry = ay - dy;
+    real t1 = c * rx, t2 = sn * ry;
+    real t3 = t1 + t2;
+    real t4 = c * ry, t5 = sn * rx;
+    real t6 = t4 - t5;
+    o->x[i] = qx + t3;
+    o->y[i] = qy + t6;
+    real vx = o->vx[i], vy = o->vy[i];
+    real a1 = c * vx, a2 = sn * vy;
+    real b1 = c * vy, b2 = sn * vx;
+    o->vx[i] = a1 + a2;
+    o->vy[i] = b1 - b2;
+  }
+  real *mF2 = (real *)malloc(sizeof(real) * (size_t)C);
+  for (int64_t cell = 0; cell < C; ++cell) {
+    int row = (int)(cell / W), col = (int)(cell % W);
+    real cx = (real)col + R(0.5);
+    real ux0 = cx * s;
+    real ux = ux0 - qx;
+    real cy = (real)row + R(0.5);
+    real uy0 = cy * s;
+    real uy = uy0 - qy;
+    real e1 = c * ux, e2 = sn * uy;
+    real e3 = e1 - e2;
+    real e4 = qx + e3;
+    real ox = e4 + dx;
+    real g1 = sn * ux, g2 = c * uy;
+    real g3 = g1 + g2;
+    real g4 = qy + g3;
+    real oy = g4 + dy;
+    real fx = ox / s, fy = oy / s;
+    int in = (fx >= 0 && fx < (real)W && fy >= 0 && fy < (real)H);
+    mF2[cell] = in ? o->mF[(int64_t)(int)fy * W + (int)fx] : 0;
+  }
+  memcpy(o->mF, mF2, sizeof(real) * (size_t)C);
+  free(mF2);
+}
+
 int oracle_step(oracle *o, float dt_f) {
   const or_params *p = &o->p;
   const uint32_t nu = p->nu, nb = p->nu_b;
@@ -416,6 +484,12 @@ int oracle_step(oracle *o, float dt_f) {
   const uint32_t f = ++o->frame;
   const real T = (real)dt_f, s = (real)p->cell_size;
   const real sp = (real)p->sigma_pos, sv = (real)p->sigma_vel, pS = (real)p->p_S;
+
+  /* ---- a0: ego-motion compensation of the posterior, if set for this step */
+  if (o->ego_on) {
+    apply_ego_motion(o);
+    o->ego_on = 0;
+  }
 
   /* ---- a1: particle prediction (Eq. process with process noise, Eq. particle_persistence) */
   for (uint32_t i = 0; i < nu; ++i) {

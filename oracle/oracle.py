@@ -34,6 +34,8 @@ def _lib(mode: str):
         dp = C.POINTER(C.c_double)
         lib.oracle_set_measurement_grid.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
         lib.oracle_step.argtypes = [C.c_void_p, C.c_float]
+        lib.oracle_set_ego_motion.argtypes = [C.c_void_p, C.c_float, C.c_float, C.c_float]
+        lib.oracle_set_ego_motion.restype = None
         lib.oracle_get_cell_array.argtypes = [C.c_void_p, C.c_int, dp]
         lib.oracle_get_particle_array.argtypes = [C.c_void_p, C.c_int, dp]
         lib.oracle_get_index_array.argtypes = [C.c_void_p, C.c_int, u32p]
@@ -117,6 +119,10 @@ class OracleFilter:
             rc = self.lib.oracle_set_measurement_grid(self._h, _d(a), _d(b), _d(pa), _d(zv), _d(sg))
         if rc != 0:
             raise ValueError(f"oracle_set_measurement_grid: invalid input ({rc})")
+
+    def set_ego_motion(self, dx: float, dy: float, dyaw: float):
+        """Vehicle motion since the previous frame, applied at the start of the next step."""
+        self.lib.oracle_set_ego_motion(self._h, float(dx), float(dy), float(dyaw))
 
     def step(self, dt: float):
         rc = self.lib.oracle_step(self._h, float(dt))

@@ -96,6 +96,8 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
                   &B->pO, &B->mean_x, &B->mean_y, &B->var_x, &B->var_y, &B->cov, &B->mpred,
                   &B->muA, &B->muU, &B->paeff, &B->rinv};
   for (auto q : pc) *q = (float *)take(4 * C);
+  B->mF_warp = (p.flags & DOG_EGO) ? (float *)take(4 * C) : nullptr;
+  B->mF_in = (p.flags & DOG_EGO) ? B->mF_warp : B->mF;
   B->csum = (CellSum *)take(sizeof(CellSum) * C);
   B->g_stage = (float *)take(4 * 5 * C);
   B->c_stage = (float *)take(4 * (10 * C + 64));
@@ -158,6 +160,9 @@ struct dog_filter {
   int nk = 0;
   int birth_grid = 1;
   uint32_t count_ct = 1;  // sort tiles per k_sort_count block
+  // ego motion for the next step (DOG_EGO): on, cos, sin, dx, dy
+  bool ego_on = false;
+  float ego_c = 1.0f, ego_s = 0.0f, ego_dx = 0.0f, ego_dy = 0.0f;
   // host I/O overlapped with compute: grid uploads and cell read-backs on their own streams
   cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaEvent_t ev_h2d = nullptr, ev_stage_free = nullptr, ev_snap = nullptr, ev_d2h = nullptr;
@@ -193,6 +198,7 @@ int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
   };
   mark();
   k_tick<<<1, 256, 0, st>>>(B, 2048 * K.passes);
+  if (K.flags & DOG_EGO) k_ego_warp<<<592, 256, 0, st>>>(K, B);  // timed with k_tick
   ++k; mark();
   const uint32_t pred_grid = (K.nu + PRED_TILE - 1) / PRED_TILE;
   k_predict<<<pred_grid, PRED_BLOCK, 4u * K.passes * K.radix, st>>>(K, B);
@@ -350,7 +356,37 @@ int dog_workspace_bytes(const dog_params *params, size_t *out_bytes) {
   return DOG_OK;
 }
 
-int dog_kernels_per_step(const dog_filter *f) { return f ? f->nk : 0; }
+int dog_kernels_per_step(const dog_filter *f) {
+  if (!f) return 0;
+  return f->nk + ((f->p.flags & DOG_EGO) ? 2 : 0);  // + the ego-motion setting and warp
+}
+
+static_assert(FLAG_EGO == DOG_EGO, "the kernels' ego flag is the ABI's");
+
+int dog_set_ego_motion(dog_filter *f, float dx, float dy, float dyaw) {
+  if (!f) return DOG_ERR_INVALID_ARG;
+  if (!(f->p.flags & DOG_EGO)) return DOG_ERR_BAD_STATE;
+  if (!std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dyaw)) return DOG_ERR_INVALID_ARG;
+  f->ego_on = dx != 0.0f || dy != 0.0f || dyaw != 0.0f;
+  f->ego_c = (float)std::cos((double)dyaw);
+  f->ego_s = (float)std::sin((double)dyaw);
+  f->ego_dx = dx;
+  f->ego_dy = dy;
+  return DOG_OK;
+}
+
+namespace {
+// the pending ego motion into the control block, in stream order before the frame; it then
+// returns to "none" for the frames after
+int issue_ego(dog_filter *f, cudaStream_t st) {
+  if (!(f->p.flags & DOG_EGO)) return DOG_OK;
+  k_set_ego<<<1, 1, 0, st>>>(f->B.ctl, f->ego_on ? 1u : 0u, f->ego_c, f->ego_s, f->ego_dx, f->ego_dy);
+  f->ego_on = false;
+  f->ego_c = 1.0f;
+  f->ego_s = f->ego_dx = f->ego_dy = 0.0f;
+  return cuda_fail(cudaGetLastError());
+}
+}  // namespace
 
 int dog_create(const dog_params *params, void *d_workspace, size_t workspace_bytes, void *cuda_stream,
                dog_filter **out) {
@@ -523,6 +559,10 @@ int dog_batch_step(dog_batch *b, const float *dt) {
       f->dt_valid = true;
     }
   }
+  for (int i = 0; i < n; ++i) {
+    const int rc = issue_ego(b->f[i], b->st);
+    if (rc) return rc;
+  }
   if (recapture) {
     const int rc = batch_capture(b);
     if (rc) return rc;
@@ -604,6 +644,10 @@ int dog_step(dog_filter *f, float dt) {
     DOG_CUDA(cudaMemcpyAsync(&f->B.ctl->dt, &h, 4, cudaMemcpyHostToDevice, f->st));
     f->dt = dt;
     f->dt_valid = true;
+  }
+  {
+    const int rc = issue_ego(f, f->st);
+    if (rc) return rc;
   }
   const int gi = f->radar ? 1 : 0;
   if (f->profile) {

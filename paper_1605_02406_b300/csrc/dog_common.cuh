@@ -26,6 +26,11 @@ struct DevCtl {
   // floor((i th_b + th_e) / nu), from W = th_a nu + th_b and u = th_c nu + th_e
   unsigned long long th_a, th_c;
   uint32_t th_b, th_e;
+  // ego motion applied at the start of this frame (filters created with the ego flag): the
+  // vehicle moved by (ego_dx, ego_dy) m in the previous grid's axes and turned by the angle
+  // whose cosine and sine are ego_c, ego_s, about the sensor position; ego_on = 0: none
+  uint32_t ego_on;
+  float ego_c, ego_s, ego_dx, ego_dy;
 };
 
 // How the posterior particles are held between frames:
@@ -73,6 +78,9 @@ struct DevBufs {
   uint32_t *bcell, *bassoc;  // newborn cells and association flags (record only)
   // cells
   float *mF;
+  const float *mF_in;  // [C] free mass the cell update starts from: mF, or for a filter with
+                       // ego-motion compensation mF_warp (mF carried into the new grid)
+  float *mF_warp;      // [C] (ego filters)
   float *zO, *zF, *pA, *zv, *sgv;
   float *mO, *rho_p, *rho_b, *pO, *mean_x, *mean_y, *var_x, *var_y, *cov;
   float *mpred, *muA, *muU, *paeff, *rinv;

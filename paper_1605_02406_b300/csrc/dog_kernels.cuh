@@ -143,6 +143,62 @@ __global__ void k_take_grid(KParams P, DevBufs B, GridSrc src, int radar) {
 }
 
 // ====================================================================================
+// Ego-motion compensation (filters created with DOG_EGO).  The grid moves with the
+// vehicle: between two frames the vehicle moved by d = (dx, dy) in the previous grid's
+// axes and turned by theta about the sensor position q.  A posterior particle enters the
+// new grid at p' = q + R(-theta) (p - q - d) with velocity v' = R(-theta) v (k_predict,
+// before the process model); the free mass carried over is read, for each new cell, at the
+// old cell under its centre q + R(theta) (c - q) + d (k_ego_warp; 0 outside the old grid).
+// ====================================================================================
+constexpr uint32_t FLAG_EGO = 0x20u;
+
+__global__ void k_set_ego(DevCtl *ctl, uint32_t on, float c, float s, float dx, float dy) {
+  ctl->ego_on = on;
+  ctl->ego_c = c;
+  ctl->ego_s = s;
+  ctl->ego_dx = dx;
+  ctl->ego_dy = dy;
+}
+
+struct Ego {
+  float c, s, dx, dy;
+};
+
+__device__ __forceinline__ void ego_transform(const KParams &P, const Ego &E, float4 &st) {
+  const float rx = __fsub_rn(__fsub_rn(st.x, P.sensor_x), E.dx);
+  const float ry = __fsub_rn(__fsub_rn(st.y, P.sensor_y), E.dy);
+  st.x = __fadd_rn(P.sensor_x, __fadd_rn(__fmul_rn(E.c, rx), __fmul_rn(E.s, ry)));
+  st.y = __fadd_rn(P.sensor_y, __fsub_rn(__fmul_rn(E.c, ry), __fmul_rn(E.s, rx)));
+  const float vx = st.z, vy = st.w;
+  st.z = __fadd_rn(__fmul_rn(E.c, vx), __fmul_rn(E.s, vy));
+  st.w = __fsub_rn(__fmul_rn(E.c, vy), __fmul_rn(E.s, vx));
+}
+
+__global__ void k_ego_warp(KParams P, DevBufs B) {
+  const DevCtl *ctl = B.ctl;
+  const bool on = ctl->ego_on != 0u;
+  const Ego E{ctl->ego_c, ctl->ego_s, ctl->ego_dx, ctl->ego_dy};
+  const uint32_t stride = gridDim.x * blockDim.x;
+  const float Wf = (float)P.W, Hf = (float)P.H;
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < P.C; c += stride) {
+    float v;
+    if (!on) {
+      v = B.mF[c];
+    } else {
+      const uint32_t row = c / (uint32_t)P.W, col = c - row * (uint32_t)P.W;
+      const float ux = __fsub_rn(__fmul_rn(__fadd_rn((float)col, 0.5f), P.s), P.sensor_x);
+      const float uy = __fsub_rn(__fmul_rn(__fadd_rn((float)row, 0.5f), P.s), P.sensor_y);
+      const float ox = __fadd_rn(__fadd_rn(P.sensor_x, __fsub_rn(__fmul_rn(E.c, ux), __fmul_rn(E.s, uy))), E.dx);
+      const float oy = __fadd_rn(__fadd_rn(P.sensor_y, __fadd_rn(__fmul_rn(E.s, ux), __fmul_rn(E.c, uy))), E.dy);
+      const float fx = __fdiv_rn(ox, P.s), fy = __fdiv_rn(oy, P.s);
+      const bool in = fx >= 0.0f && fx < Wf && fy >= 0.0f && fy < Hf;
+      v = in ? B.mF[(uint32_t)(int)fy * (uint32_t)P.W + (uint32_t)(int)fx] : 0.0f;
+    }
+    B.mF_warp[c] = v;
+  }
+}
+
+// ====================================================================================
 // k_predict (Alg. 1): Eq. process with per-frame Gaussian noise, Eq. particle_persistence,
 // cell index floor(x/s), floor(y/s) (outside the grid: nearest border cell, weight 0).
 // Each block handles 4096 particles, 4 per thread per round with 16-byte accesses, and
@@ -186,6 +242,8 @@ __global__ void __launch_bounds__(PRED_BLOCK) k_predict(KParams P, DevBufs B) {
   const uint32_t mode = B.ctl->post_mode;
   const float w_res = B.ctl->w_new;
   const uint32_t mask = P.radix - 1u;
+  const bool ego = (P.flags & FLAG_EGO) != 0u && B.ctl->ego_on != 0u;
+  const Ego E{B.ctl->ego_c, B.ctl->ego_s, B.ctl->ego_dx, B.ctl->ego_dy};
   for (int rnd = 0; rnd < PRED_ROUNDS; ++rnd) {
     const uint32_t i0 = blockIdx.x * PRED_TILE + (uint32_t)rnd * (PRED_BLOCK * 4) + threadIdx.x * 4;
     uint32_t key[4];
@@ -202,6 +260,12 @@ __global__ void __launch_bounds__(PRED_BLOCK) k_predict(KParams P, DevBufs B) {
         s2 = j.z < P.nu ? B.Os[j.z] : B.bs[j.z - P.nu];
         s3 = j.w < P.nu ? B.Os[j.w] : B.bs[j.w - P.nu];
         w = make_float4(w_res, w_res, w_res, w_res);
+      }
+      if (ego) {  // into the new frame's grid first
+        ego_transform(P, E, s0);
+        ego_transform(P, E, s1);
+        ego_transform(P, E, s2);
+        ego_transform(P, E, s3);
       }
       predict_one(P, i0 + 0, frame, T, s0, w.x, key[0]);
       predict_one(P, i0 + 1, frame, T, s1, w.y, key[1]);
@@ -222,6 +286,7 @@ __global__ void __launch_bounds__(PRED_BLOCK) k_predict(KParams P, DevBufs B) {
         key[k] = 0u;
         if (valid[k]) {
           float4 s = posterior_record(P, B, mode, i);
+          if (ego) ego_transform(P, E, s);
           float w = mode == POST_DIRECT ? B.Bw[i] : w_res;
           predict_one(P, i, frame, T, s, w, key[k]);
           B.As[i] = s;
@@ -1275,7 +1340,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
     Ss[it] = ((unsigned long long)h.y << 32) | h.x;
     tgs[it] = h.z;
     m0s[it] = __uint_as_float(h.w);
-    mFs[it] = in ? B.mF[c] : 0.0f;
+    mFs[it] = in ? B.mF_in[c] : 0.0f;
     zOs[it] = in ? B.zO[c] : 0.0f;
     zFs[it] = in ? B.zF[c] : 0.0f;
   }

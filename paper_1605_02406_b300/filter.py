@@ -68,6 +68,11 @@ class DogFilter:
         N.dog_set_measurement_grid(self.h, ptrs, N.DOG_DEVICE if on_dev else N.DOG_HOST)
         self._keep = keep
 
+    def set_ego_motion(self, dx: float, dy: float, dyaw: float):
+        """Vehicle motion since the previous frame (filters created with DOG_EGO): moved by
+        (dx, dy) m in the previous grid's axes, turned by dyaw rad about the sensor."""
+        N.dog_set_ego_motion(self.h, dx, dy, dyaw)
+
     def step(self, dt: float):
         N.dog_step(self.h, dt)
 

@@ -15,7 +15,7 @@ DOG_OK = 0
 DOG_ERR = {-1: "DOG_ERR_INVALID_ARG", -2: "DOG_ERR_WORKSPACE_TOO_SMALL", -3: "DOG_ERR_CUDA",
            -4: "DOG_ERR_DEVICE", -5: "DOG_ERR_INPUT", -6: "DOG_ERR_BAD_STATE",
            -7: "DOG_ERR_UNSUPPORTED"}
-DOG_NO_RESAMPLE, DOG_RECORD, DOG_NO_GRAPH, DOG_PROFILE = 0x2, 0x4, 0x8, 0x10
+DOG_NO_RESAMPLE, DOG_RECORD, DOG_NO_GRAPH, DOG_PROFILE, DOG_EGO = 0x2, 0x4, 0x8, 0x10, 0x20
 DOG_HOST, DOG_DEVICE, DOG_HOST_ASYNC = 0, 1, 2
 
 DBG = ["PRED_X", "PRED_Y", "PRED_VX", "PRED_VY", "PRED_W", "KEY", "PERM", "CELL_START",
@@ -30,7 +30,7 @@ SYMBOLS = ["dog_workspace_bytes", "dog_create", "dog_set_measurement_grid", "dog
            "dog_profile_read", "dog_kernels_per_step", "dog_destroy", "dog_error_string",
            "dog_assign_cells_noalloc", "dog_batch_create", "dog_batch_step", "dog_batch_destroy",
            "dog_last_cuda_error", "dog_eval_clusters", "dog_eval_mahalanobis",
-           "dog_get_cells_async", "dog_wait_cells"]
+           "dog_get_cells_async", "dog_wait_cells", "dog_set_ego_motion"]
 DOG_NOALLOC_MAX_PARTICLES, DOG_NOALLOC_MAX_CELLS = 1 << 19, 1 << 22
 
 
@@ -107,6 +107,7 @@ def lib() -> C.CDLL:
         L.dog_eval_clusters.argtypes = [vp, vp, C.c_uint32, vp, vp]
         L.dog_get_cells_async.argtypes = [vp, C.POINTER(dog_cells)]
         L.dog_wait_cells.argtypes = [vp]
+        L.dog_set_ego_motion.argtypes = [vp, C.c_float, C.c_float, C.c_float]
         L.dog_eval_mahalanobis.argtypes = [vp, vp, C.c_float, vp, C.c_uint32, vp, vp]
         L.dog_last_cuda_error.restype = C.c_char_p
         for n in SYMBOLS:
@@ -153,6 +154,10 @@ def dog_set_measurement_grid(h: int, ptrs: dict, mem_kind: int) -> None:
 
 def dog_step(h: int, dt: float) -> None:
     check("dog_step", lib().dog_step(h, float(dt)))
+
+
+def dog_set_ego_motion(h: int, dx: float, dy: float, dyaw: float) -> None:
+    check("dog_set_ego_motion", lib().dog_set_ego_motion(h, float(dx), float(dy), float(dyaw)))
 
 
 def dog_get_cells(h: int, ptrs: dict, mem_kind: int) -> None:

@@ -25,7 +25,7 @@ from paper_1605_02406_b300 import scene
 
 pytestmark = pytest.mark.gpu
 
-NO_RESAMPLE, RECORD, NO_GRAPH = 0x2, 0x4, 0x8
+NO_RESAMPLE, RECORD, NO_GRAPH, EGO = 0x2, 0x4, 0x8, 0x20
 MASS_FIELDS = ["m_occ", "m_free", "rho_p", "rho_b", "p_occ"]
 MOMENT_FIELDS = ["mean_vx", "mean_vy", "var_vx", "var_vy", "cov_vxy"]
 
@@ -208,6 +208,40 @@ def test_dominant_source_resampling():
         f.set_measurement_grid(**grid)
         f.step(0.1)
     compare_frame(g, o, what="frame 1: ")
+
+
+@pytest.mark.parametrize("flags", [RECORD | EGO, RECORD | EGO | NO_GRAPH])
+def test_ego_motion_frames(flags):
+    """Ego-motion compensation (posterior particles into the new grid in the prediction,
+    free mass warped to the new cells) bit for bit against the oracle: frames with a
+    translation and a turn, without a call (the grid stays), a pure turn, a pure translation."""
+    p = small(48, 37, nu=3 * 4096 + 1234, nu_b=2 * 2048 + 77, flags=flags)
+    rng = np.random.default_rng(15)
+    st = scene.random_state(p, rng, occupied_frac=0.1)
+    grids = [scene.random_measurement_grid(48, 37, rng) for _ in range(3)]
+    g, o = _gpu(p), OracleFilter(p, "f32")
+    g.set_state(st)
+    o.set_state(st)
+    for k, m in enumerate([(0.4, -0.25, 0.05), None, (0.0, 0.0, -0.3), (1.1, 0.3, 0.0)]):
+        for f in (g, o):
+            f.set_measurement_grid(**grids[k % 3])
+            if m is not None:
+                f.set_ego_motion(*m)
+            f.step(0.1)
+        compare_frame(g, o, what=f"frame {k}: ")
+
+
+def test_ego_motion_call_errors():
+    from paper_1605_02406_b300 import native as N
+    g = _gpu(small(8, 8, nu=256, nu_b=16))  # created without the ego flag
+    with pytest.raises(N.DogError) as e:
+        g.set_ego_motion(0.1, 0.0, 0.0)
+    assert e.value.code == -6
+    h = _gpu(small(8, 8, nu=256, nu_b=16, flags=EGO))
+    with pytest.raises(N.DogError) as e:
+        h.set_ego_motion(float("nan"), 0.0, 0.0)
+    assert e.value.code == -1
+    h.set_ego_motion(0.1, 0.2, 0.3)
 
 
 def test_checkpoint_resume_is_bit_exact():
