@@ -293,6 +293,43 @@ def fusion_rate(steps: int, warmup: int) -> dict:
             "value": params["nu"] / (ms * 1e-3), "unit": "particle-updates/s"}
 
 
+def ego_rate(steps: int, warmup: int) -> dict:
+    """Device-resident step rate of the 1024x1024 workload with ego-motion compensation
+    every frame (vehicle at 10 m/s turning at 0.2 rad/s: 1 m and 0.02 rad a frame), next
+    to the same filter without it."""
+    import torch
+
+    from paper_1605_02406_b300 import native as N
+    from paper_1605_02406_b300.filter import DogFilter
+    cfg = scene.CONFIGS["automotive_1024"]
+    grids = scene.frame_sequence(cfg, 8, 1002)
+    dev = [{k: torch.tensor(v, device="cuda") for k, v in g.items()} for g in grids]
+    out = {"workload": cfg["name"] + ", ego motion 1 m and 0.02 rad a frame", "steps": steps}
+    for name, flags in (("ego", N.DOG_EGO), ("plain", 0)):
+        f = DogFilter(scene.filter_params(cfg, flags=flags))
+
+        def frame(k):
+            f.set_measurement_grid(**dev[k % 8])
+            if flags:
+                f.set_ego_motion(1.0, 0.0, 0.02)
+            f.step(cfg["dt"])
+
+        for k in range(warmup):
+            frame(k)
+        f.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(f.stream)
+        for k in range(steps):
+            frame(warmup + k)
+        e1.record(f.stream)
+        f.sync()
+        out[name + "_ms_per_step"] = e0.elapsed_time(e1) / steps
+        f.close()
+    out["value"] = cfg["nu"] / (out["ego_ms_per_step"] * 1e-3)
+    out["unit"] = "particle-updates/s"
+    return out
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -304,6 +341,7 @@ def main() -> None:
     ap.add_argument("--no-fusion", action="store_true", help="skip the lidar + radar workload")
     ap.add_argument("--no-evaluation", action="store_true", help="skip timing the evaluation calls")
     ap.add_argument("--no-serving", action="store_true", help="skip the 3 s serving-loop run")
+    ap.add_argument("--no-ego", action="store_true", help="skip the ego-motion workload")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -451,6 +489,7 @@ def main() -> None:
     fusion = None
     if not args.no_fusion:
         fusion = fusion_rate(steps=min(args.steps, 100), warmup=args.warmup)
+    ego = None if args.no_ego else ego_rate(steps=min(args.steps, 200), warmup=args.warmup)
     batched = {"workload": None}
     if not args.no_batched:
         batched = batched_latency(frames=min(args.steps, 50), warmup=args.warmup)
@@ -483,6 +522,7 @@ def main() -> None:
         "clocks": clocks,
         "cpu_baseline": cpu,
         "fusion": fusion,
+        "ego": ego,
         "evaluation": evaluation,
         "serving": serving,
     }

@@ -126,3 +126,40 @@ def test_streams_in_a_mix_equal_streams_alone():
             if va.dtype.kind == "f":
                 va, vb = va.astype(np.float32).view(np.uint32), vb.astype(np.float32).view(np.uint32)
             assert np.array_equal(va, vb), f"filter {i}: {k} differs"
+
+
+def test_batch_with_ego_motion_equals_single_filters():
+    """A filter with ego-motion compensation in a batch: the motion set before each batched
+    step applies to that filter only, as when it is stepped alone."""
+    import torch
+
+    from paper_1605_02406_b300.filter import DogBatch, DogFilter
+    cases = [dict(CASES[0], flags=0x20), CASES[2]]
+    shared = torch.cuda.Stream()
+    batched = [DogFilter(p, stream=shared) for p in cases]
+    single = [DogFilter(p) for p in cases]
+    rng = np.random.default_rng(17)
+    grids = []
+    for fb, fs, p in zip(batched, single, cases):
+        st = scene.random_state(p, rng, occupied_frac=0.1)
+        fb.set_state(st)
+        fs.set_state(st)
+        grids.append([scene.random_measurement_grid(p["width"], p["height"], rng) for _ in range(3)])
+    batch = DogBatch(batched)
+    motions = [(0.5, 0.1, 0.03), None, (0.0, -0.4, -0.1)]
+    for frame in range(3):
+        for i in range(2):
+            for f in (batched[i], single[i]):
+                f.set_measurement_grid(**grids[i][frame])
+                if i == 0 and motions[frame] is not None:
+                    f.set_ego_motion(*motions[frame])
+            single[i].step(0.1)
+        batch.step([0.1, 0.1])
+        for i in range(2):
+            a, b = _snapshot(batched[i]), _snapshot(single[i])
+            for k in a:
+                va, vb = np.asarray(a[k]), np.asarray(b[k])
+                if va.dtype.kind == "f":
+                    va, vb = va.astype(np.float32).view(np.uint32), vb.astype(np.float32).view(np.uint32)
+                assert np.array_equal(va, vb), f"frame {frame}, filter {i}: {k} differs"
+    batch.close()
