@@ -51,6 +51,8 @@ typedef enum dog_status {
 #define DOG_NO_GRAPH 0x8u    /* issue kernels one by one instead of a captured graph     */
 #define DOG_PROFILE 0x10u    /* time each kernel with CUDA events (dog_profile_read)      */
 #define DOG_EGO 0x20u        /* the grid moves with the vehicle: dog_set_ego_motion         */
+#define DOG_FULL 0x40u       /* the PHD/MIB filter of Sect. VI with its Bernoulli observation
+                                (dog_set_bernoulli_grid) instead of the DS approximation */
 
 /* memory kind of caller buffers */
 #define DOG_HOST 0
@@ -86,6 +88,18 @@ typedef struct dog_meas_grid {
   const float *m_occ, *m_free;
   const float *p_A, *z_vr, *sigma_vr;
 } dog_meas_grid;
+
+/* Bernoulli observation of each cell for the PHD/MIB filter (Sect. VI, Bernoulli
+ * Observation Process), SoA with C entries each: z = 1 where a measurement occurred, else 0;
+ * p_tp, p_fp in (0,1): the cell's true / false positive probabilities; p_a in [0,1]: the
+ * association probability; p_c > 0: the clutter density of the cell's measurement.  The
+ * single-object likelihood of a measured cell is 1 over the cell (an occupancy-grid
+ * detection carries no position inside the cell), so p_c is the likelihood ratio of clutter
+ * to the object.  Fields of unmeasured cells other than p_tp, p_fp are not used but must
+ * still lie in their ranges. */
+typedef struct dog_bern_grid {
+  const float *z, *p_tp, *p_fp, *p_a, *p_c;
+} dog_bern_grid;
 
 /* Per-cell outputs of the last frame; any pointer may be NULL (not copied).
  * m_occ, m_free: posterior BBA (Eq. DS_comb); rho_p, rho_b: persistent / newborn parts of
@@ -131,6 +145,21 @@ int dog_create(const dog_params *params, void *d_workspace, size_t workspace_byt
  * is latched and reported as DOG_ERR_INPUT by the next synchronising call (dog_sync,
  * dog_get_cells, dog_wait_cells, ...); the frames stepped with that grid are void. */
 int dog_set_measurement_grid(dog_filter *f, const dog_meas_grid *grid, int mem_kind);
+
+/* The same for a filter created with DOG_FULL: the PHD/MIB filter of Sect. VI.  Each frame
+ * then runs the particle realisation of Sect. VI: persistent prediction as in Alg. 1;
+ * r_p = min(sum of the cell's predicted weights, 1) (weights of a cell over 1 scaled to sum
+ * 1); newborn existence r_b = p_B (1 - r_p) (Eq. pred_birth_prob), newborn slots shared out
+ * in proportion to r_b with weights r_b / n; the Bernoulli update (Eq. filter_update with
+ * normalization_empty / normalization_meas), which with a likelihood of 1 multiplies every
+ * weight of the cell by f = p_tp g_A / N_z (measured, g_A = p_a + (1 - p_a) p_c, N_z =
+ * p_fp p_c (1 - r) + p_tp g_A r) or f = (1 - p_tp) / ((1 - p_tp) r + (1 - p_fp)(1 - r))
+ * (not measured), r = r_p + r_b; resampling as in Alg. 7.  dog_get_cells then gives
+ * m_occ = p_occ = the posterior existence r' = f r (Eq. occprob_integral), m_free = 1 - r',
+ * rho_p = f r_p, rho_b = f r_b.  Errors: as dog_set_measurement_grid (INPUT: z not 0 or 1,
+ * a probability or p_c out of range); BAD_STATE: filter without DOG_FULL (and
+ * dog_set_measurement_grid on a DOG_FULL filter). */
+int dog_set_bernoulli_grid(dog_filter *f, const dog_bern_grid *grid, int mem_kind);
 
 /* Ego-motion compensation for the next dog_step (filters created with DOG_EGO; the paper's
  * experiments compensate the vehicle's motion from speed and yaw rate, Sect. VIII, without

@@ -44,6 +44,7 @@ typedef double real;
 #endif
 
 #define OR_NO_RESAMPLE 0x2u
+#define OR_FULL 0x40u /* the PHD/MIB filter of Sect. VI instead of the DS approximation */
 
 typedef struct {
   int32_t width, height;
@@ -78,6 +79,9 @@ typedef struct {
   uint8_t *bassoc;                /* [nu_b] 1 = associated set */
   uint32_t *rsrc;                 /* [nu] resampled source index (joint index space) */
   uint64_t Wq, RC, u;
+  /* PHD/MIB filter (OR_FULL): Bernoulli observation per cell and per-cell intermediates */
+  real *bz, *bptp, *bpfp, *bpa, *bpc; /* [C] z, p_TP, p_FP, p_A, p_c */
+  real *rbp, *fcell;                  /* [C] predicted newborn existence, update factor */
   /* ego motion to apply at the start of the next step (oracle_set_ego_motion) */
   int ego_on;
   real ego_c, ego_s, ego_dx, ego_dy;
@@ -272,6 +276,7 @@ oracle *oracle_create(const or_params *p) {
   AR(wn, nu);
   AR(bx, nb); AR(by, nb); AR(bvx, nb); AR(bvy, nb); AR(bw, nb); AR(bcell, nb); AR(bassoc, nb);
   AR(rsrc, nu);
+  AR(bz, C); AR(bptp, C); AR(bpfp, C); AR(bpa, C); AR(bpc, C); AR(rbp, C); AR(fcell, C);
 #undef AR
   for (int64_t c = 0; c < C; ++c) o->sgv[c] = 1;
   /* reading: initial state -- particles uniform over the grid, birth-distribution
@@ -299,7 +304,8 @@ void oracle_destroy(oracle *o) {
                   o->mO, o->rho_p, o->rho_b, o->pO, o->mean_x, o->mean_y, o->var_x, o->var_y,
                   o->cov, o->mpred, o->muA, o->muU, o->px, o->py, o->pvx, o->pvy, o->pw,
                   o->key, o->perm, o->cstart, o->cend, o->S, o->A, o->wn, o->bx, o->by,
-                  o->bvx, o->bvy, o->bw, o->bcell, o->bassoc, o->rsrc};
+                  o->bvx, o->bvy, o->bw, o->bcell, o->bassoc, o->rsrc, o->bz, o->bptp,
+                  o->bpfp, o->bpa, o->bpc, o->rbp, o->fcell};
   for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); ++k) free(ptrs[k]);
   free(o);
 }
@@ -321,6 +327,30 @@ int oracle_set_measurement_grid(oracle *o, const double *m_occ, const double *m_
     o->pA[c] = p_A ? (real)p_A[c] : 0;
     o->zv[c] = p_A ? (real)z_vr[c] : 0;
     o->sgv[c] = p_A ? (real)sigma_vr[c] : 1;
+  }
+  return 0;
+}
+
+/* Bernoulli observation of each cell for the PHD/MIB filter (Sect. VI, Bernoulli
+ * Observation Process): z = 1 where a measurement occurred; true / false positive
+ * probabilities in (0,1); association probability in [0,1]; clutter density p_c > 0
+ * (reading: an occupancy-grid detection carries no position inside its cell, so the
+ * single-object likelihood is 1 over the cell and p_c is the clutter-to-object ratio). */
+int oracle_set_bernoulli_grid(oracle *o, const double *z, const double *p_tp, const double *p_fp,
+                              const double *p_a, const double *p_c) {
+  for (int64_t c = 0; c < o->C; ++c) {
+    if (!(z[c] == 0.0 || z[c] == 1.0)) return -5;
+    if (!(p_tp[c] > 0.0 && p_tp[c] < 1.0 && p_fp[c] > 0.0 && p_fp[c] < 1.0)) return -5;
+    if (!(p_a[c] >= 0.0 && p_a[c] <= 1.0) || !(p_c[c] > 0.0 && p_c[c] < 3.0e38)) return -5;
+  }
+  o->has_radar = 0;
+  for (int64_t c = 0; c < o->C; ++c) {
+    o->bz[c] = (real)z[c];
+    o->bptp[c] = (real)p_tp[c];
+    o->bpfp[c] = (real)p_fp[c];
+    o->bpa[c] = (real)p_a[c];
+    o->bpc[c] = (real)p_c[c];
+    o->pA[c] = 0;
   }
   return 0;
 }
@@ -554,7 +584,57 @@ int oracle_step(oracle *o, float dt_f) {
 
   /* ---- a4: occupancy prediction and DS update per cell (Alg. 3) */
   const real alpha = (real)p->alpha, pB = (real)p->p_B;
-  for (int64_t c = 0; c < C; ++c) {
+  const int full = (p->flags & OR_FULL) != 0;
+  for (int64_t c = 0; c < C && full; ++c) {
+    /* PHD/MIB filter, Sect. VI.  Predicted Bernoulli RFS: persistent existence r_p = the
+     * cell's predicted weight sum, truncated to 1 (reading: the weights of a cell whose sum
+     * exceeds 1 are scaled to sum 1), newborn existence r_b = p_B (1 - r_p) (Eq.
+     * pred_birth_prob).  Update (Eq. updateParticleWeightsUnnormalized, applyNormalization,
+     * normalizationCalculation; updateParticleWeightsEmpty) with a likelihood of 1: every
+     * particle weight of the cell is multiplied by one factor f; the sums over the cell's
+     * persistent and newborn weights in the normaliser are r_p and r_b. */
+    real Sr = fx2r(o->S[c]);
+    real rp = R_MIN(Sr, R(1.0));
+    real omp = R(1.0) - rp;
+    real rb = pB * omp;
+    real r = rp + rb;
+    real omr = R(1.0) - r;
+    real ptp = o->bptp[c], pfp = o->bpfp[c];
+    real fc;
+    if (o->bz[c] != 0) {
+      real pa = o->bpa[c], pc = o->bpc[c];
+      real q = R(1.0) - pa;
+      real q2 = q * pc;
+      real gam = pa + q2;                   /* g_A = p_A g + (1 - p_A) p_c, g = 1 */
+      real num = ptp * gam;
+      real t1 = pfp * pc;
+      real t2 = t1 * omr;
+      real t3 = num * r;
+      real Nz = t2 + t3;
+      fc = num / Nz;
+    } else {
+      real a = R(1.0) - ptp;
+      real b = R(1.0) - pfp;
+      real t1 = a * r;
+      real t2 = b * omr;
+      real Ne = t1 + t2;
+      fc = a / Ne;
+    }
+    real rhop = fc * rp;
+    real rhob = fc * rb;
+    real rpost = rhop + rhob;              /* posterior existence, Eq. occupancyProbParticles */
+    o->mpred[c] = rp;
+    o->mO[c] = rpost;
+    o->mF[c] = R(1.0) - rpost;             /* reading: the free probability 1 - r' */
+    o->rho_p[c] = rhop;
+    o->rho_b[c] = rhob;
+    o->pO[c] = rpost;
+    o->muU[c] = (o->S[c] > 0) ? (Sr > R(1.0) ? fc / Sr : fc) : 0;
+    o->muA[c] = fc;
+    o->rbp[c] = rb;
+    o->fcell[c] = fc;
+  }
+  for (int64_t c = 0; c < C && !full; ++c) {
     real Sr = fx2r(o->S[c]);
     real mp = R_MIN(Sr, R(1.0));           /* Eq. predExistenceProb: min(sum, 1) */
     real mO, mF, rb, rp, mFp;
@@ -629,8 +709,11 @@ int oracle_step(oracle *o, float dt_f) {
   }
 
   /* ---- a6: newborn particles (Alg. 5) */
+  /* newborn slots follow the posterior newborn mass (DS) or, in the PHD/MIB filter, the
+   * predicted newborn existence (Sect. VI: births are sampled in the prediction) */
+  const real *bmass = full ? o->rbp : o->rho_b;
   uint64_t RC = 0;
-  for (int64_t c = 0; c < C; ++c) RC += q40(o->rho_b[c]);
+  for (int64_t c = 0; c < C; ++c) RC += q40(bmass[c]);
   o->RC = RC;
   const real sB = (real)p->sigma_birth_vel;
   if (RC == 0) {
@@ -645,7 +728,7 @@ int oracle_step(oracle *o, float dt_f) {
      * [floor(nu_b R_{c-1} / R_C), floor(nu_b R_c / R_C)) */
     uint64_t Rprev = 0;
     for (int64_t c = 0; c < C; ++c) {
-      uint64_t qb = q40(o->rho_b[c]);
+      uint64_t qb = q40(bmass[c]);
       if (qb == 0) continue;
       uint64_t Rc = Rprev + qb;
       uint32_t lo = (uint32_t)floor_muldiv(nb, Rprev, RC);
@@ -661,9 +744,14 @@ int oracle_step(oracle *o, float dt_f) {
       uint32_t nA = (uint32_t)tn;
       if (nA > n) nA = n;
       uint32_t nUA = n - nA;
-      real rb = o->rho_b[c];
+      real rb = bmass[c];
       real wA = 0, wUA = 0;
-      if (nA > 0 && nUA > 0) {
+      if (full) {
+        /* Eq. predExistenceProbParticlesBorn: r_b / n, then the cell's update factor */
+        real a = rb / (real)n;
+        wUA = o->fcell[c] * a;
+        nA = 0;
+      } else if (nA > 0 && nUA > 0) {
         real a = pA * rb;
         wA = a / (real)nA;                  /* Eq. weights_associated */
         real b = R(1.0) - pA;

@@ -35,6 +35,7 @@ def _lib(mode: str):
         lib.oracle_set_measurement_grid.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
         lib.oracle_step.argtypes = [C.c_void_p, C.c_float]
         lib.oracle_set_ego_motion.argtypes = [C.c_void_p, C.c_float, C.c_float, C.c_float]
+        lib.oracle_set_bernoulli_grid.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
         lib.oracle_set_ego_motion.restype = None
         lib.oracle_get_cell_array.argtypes = [C.c_void_p, C.c_int, dp]
         lib.oracle_get_particle_array.argtypes = [C.c_void_p, C.c_int, dp]
@@ -119,6 +120,13 @@ class OracleFilter:
             rc = self.lib.oracle_set_measurement_grid(self._h, _d(a), _d(b), _d(pa), _d(zv), _d(sg))
         if rc != 0:
             raise ValueError(f"oracle_set_measurement_grid: invalid input ({rc})")
+
+    def set_bernoulli_grid(self, z, p_tp, p_fp, p_a, p_c):
+        """Bernoulli observation per cell (PHD/MIB filter, flag 0x40)."""
+        arrs = [_cf64(a, self.C) for a in (z, p_tp, p_fp, p_a, p_c)]
+        rc = self.lib.oracle_set_bernoulli_grid(self._h, *[_d(a) for a in arrs])
+        if rc != 0:
+            raise ValueError(f"oracle_set_bernoulli_grid: {rc}")
 
     def set_ego_motion(self, dx: float, dy: float, dyaw: float):
         """Vehicle motion since the previous frame, applied at the start of the next step."""

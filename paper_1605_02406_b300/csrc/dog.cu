@@ -98,6 +98,7 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
   for (auto q : pc) *q = (float *)take(4 * C);
   B->mF_warp = (p.flags & DOG_EGO) ? (float *)take(4 * C) : nullptr;
   B->mF_in = (p.flags & DOG_EGO) ? B->mF_warp : B->mF;
+  B->rb_pred = (p.flags & DOG_FULL) ? (float *)take(4 * C) : nullptr;
   B->csum = (CellSum *)take(sizeof(CellSum) * C);
   B->g_stage = (float *)take(4 * 5 * C);
   B->c_stage = (float *)take(4 * (10 * C + 64));
@@ -602,14 +603,12 @@ void dog_destroy(dog_filter *f) {
   delete f;
 }
 
-int dog_set_measurement_grid(dog_filter *f, const dog_meas_grid *g, int mem_kind) {
-  if (!f || !g || !g->m_occ || !g->m_free) return DOG_ERR_INVALID_ARG;
-  if (mem_kind != DOG_HOST && mem_kind != DOG_DEVICE && mem_kind != DOG_HOST_ASYNC) return DOG_ERR_INVALID_ARG;
-  const bool radar = g->p_A != nullptr;
-  if (radar && (!g->z_vr || !g->sigma_vr)) return DOG_ERR_INVALID_ARG;
+namespace {
+// upload (host kinds) or reference (device) the grid's fields and take them over with one
+// copy-and-validate kernel in stream order
+int take_grid(dog_filter *f, const float *const src[5], int nfield, int kind, int mem_kind) {
   const size_t C = f->d.C;
-  const float *src[5] = {g->m_occ, g->m_free, g->p_A, g->z_vr, g->sigma_vr};
-  const int nfield = radar ? 5 : 2;
+  const bool radar = kind == GRID_RADAR;
   GridSrc gs{};
   if (mem_kind == DOG_DEVICE) {
     for (int k = 0; k < nfield; ++k) gs.f[k] = src[k];
@@ -624,7 +623,7 @@ int dog_set_measurement_grid(dog_filter *f, const dog_meas_grid *g, int mem_kind
     for (int k = 0; k < nfield; ++k) gs.f[k] = f->B.g_stage + k * C;
   }
   // copy into place and validate in one pass
-  k_take_grid<<<592, 256, 0, f->st>>>(f->K, f->B, gs, radar ? 1 : 0);
+  k_take_grid<<<592, 256, 0, f->st>>>(f->K, f->B, gs, kind);
   DOG_CUDA(cudaGetLastError());
   if (mem_kind != DOG_DEVICE) DOG_CUDA(cudaEventRecord(f->ev_stage_free, f->st));
   f->radar = radar;
@@ -633,6 +632,28 @@ int dog_set_measurement_grid(dog_filter *f, const dog_meas_grid *g, int mem_kind
   // caller waits for that itself, with dog_sync or a later call that waits)
   if (mem_kind == DOG_HOST) DOG_CUDA(cudaEventSynchronize(f->ev_h2d));
   return DOG_OK;
+}
+}  // namespace
+
+int dog_set_measurement_grid(dog_filter *f, const dog_meas_grid *g, int mem_kind) {
+  if (!f || !g || !g->m_occ || !g->m_free) return DOG_ERR_INVALID_ARG;
+  if (mem_kind != DOG_HOST && mem_kind != DOG_DEVICE && mem_kind != DOG_HOST_ASYNC) return DOG_ERR_INVALID_ARG;
+  if (f->p.flags & DOG_FULL) return DOG_ERR_BAD_STATE;  // takes dog_set_bernoulli_grid
+  const bool radar = g->p_A != nullptr;
+  if (radar && (!g->z_vr || !g->sigma_vr)) return DOG_ERR_INVALID_ARG;
+  const float *src[5] = {g->m_occ, g->m_free, g->p_A, g->z_vr, g->sigma_vr};
+  return take_grid(f, src, radar ? 5 : 2, radar ? GRID_RADAR : GRID_LIDAR, mem_kind);
+}
+
+static_assert(FLAG_FULL == DOG_FULL, "the kernels' PHD/MIB flag is the ABI's");
+
+int dog_set_bernoulli_grid(dog_filter *f, const dog_bern_grid *g, int mem_kind) {
+  if (!f || !g || !g->z || !g->p_tp || !g->p_fp || !g->p_a || !g->p_c) return DOG_ERR_INVALID_ARG;
+  if (mem_kind != DOG_HOST && mem_kind != DOG_DEVICE && mem_kind != DOG_HOST_ASYNC) return DOG_ERR_INVALID_ARG;
+  if (!(f->p.flags & DOG_FULL)) return DOG_ERR_BAD_STATE;
+  // layout of the grid buffers for the Bernoulli observation: z, p_TP, p_A, p_FP, p_c
+  const float *src[5] = {g->z, g->p_tp, g->p_a, g->p_fp, g->p_c};
+  return take_grid(f, src, 5, GRID_BERNOULLI, mem_kind);
 }
 
 int dog_step(dog_filter *f, float dt) {

@@ -81,6 +81,10 @@ struct DevBufs {
   const float *mF_in;  // [C] free mass the cell update starts from: mF, or for a filter with
                        // ego-motion compensation mF_warp (mF carried into the new grid)
   float *mF_warp;      // [C] (ego filters)
+  float *rb_pred;      // [C] predicted newborn existence (the PHD/MIB filter, Sect. VI)
+  // measurement grid.  DS filter: m_O, m_F (+ radar p_A, z_vr, sigma_vr).  PHD/MIB filter
+  // (Bernoulli observation of Sect. VI): zO = z (1: a measurement occurred), zF = p_TP,
+  // pA = p_A, zv = p_FP, sgv = p_c (clutter density; the single-object likelihood is 1)
   float *zO, *zF, *pA, *zv, *sgv;
   float *mO, *rho_p, *rho_b, *pO, *mean_x, *mean_y, *var_x, *var_y, *cov;
   float *mpred, *muA, *muU, *paeff, *rinv;

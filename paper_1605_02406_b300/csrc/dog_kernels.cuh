@@ -121,15 +121,28 @@ struct GridSrc {
   const float *f[5];  // m_occ, m_free, p_A, z_vr, sigma_vr (the last three: radar only)
 };
 
-__global__ void k_take_grid(KParams P, DevBufs B, GridSrc src, int radar) {
+enum : int { GRID_LIDAR = 0, GRID_RADAR = 1, GRID_BERNOULLI = 2 };
+
+__global__ void k_take_grid(KParams P, DevBufs B, GridSrc src, int kind) {
   const uint32_t stride = gridDim.x * blockDim.x;
   bool bad = false;
   for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < P.C; c += stride) {
     const float a = __ldg(src.f[0] + c), b = __ldg(src.f[1] + c);
     B.zO[c] = a;
     B.zF[c] = b;
+    if (kind == GRID_BERNOULLI) {  // z in {0, 1}; p_TP, p_FP in (0, 1); p_A in [0, 1]; p_c > 0
+      const float pa = __ldg(src.f[2] + c), pfp = __ldg(src.f[3] + c), pc = __ldg(src.f[4] + c);
+      B.pA[c] = pa;
+      B.zv[c] = pfp;
+      B.sgv[c] = pc;
+      bad |= !(a == 0.0f || a == 1.0f);
+      bad |= !(b > 0.0f && b < 1.0f && pfp > 0.0f && pfp < 1.0f);
+      bad |= !(pa >= 0.0f && pa <= 1.0f);
+      bad |= !(pc > 0.0f && pc < 3.0e38f);
+      continue;
+    }
     bad |= !(a >= 0.0f && a <= 1.0f && b >= 0.0f && b <= 1.0f && a + b <= 1.000001f);
-    if (radar) {
+    if (kind == GRID_RADAR) {
       const float pa = __ldg(src.f[2] + c), zv = __ldg(src.f[3] + c), sg = __ldg(src.f[4] + c);
       B.pA[c] = pa;
       B.zv[c] = zv;
@@ -150,7 +163,7 @@ __global__ void k_take_grid(KParams P, DevBufs B, GridSrc src, int radar) {
 // before the process model); the free mass carried over is read, for each new cell, at the
 // old cell under its centre q + R(theta) (c - q) + d (k_ego_warp; 0 outside the old grid).
 // ====================================================================================
-constexpr uint32_t FLAG_EGO = 0x20u;
+constexpr uint32_t FLAG_EGO = 0x20u, FLAG_FULL = 0x40u;
 
 __global__ void k_set_ego(DevCtl *ctl, uint32_t on, float c, float s, float dx, float dy) {
   ctl->ego_on = on;
@@ -1332,6 +1345,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
   uint32_t tgs[CELL_ITEMS];
   float mFs[CELL_ITEMS], zOs[CELL_ITEMS], zFs[CELL_ITEMS], m0s[CELL_ITEMS];
   unsigned long long Ss[CELL_ITEMS];
+  const bool full = !RADAR && (P.flags & FLAG_FULL) != 0u;  // the PHD/MIB filter of Sect. VI
 #pragma unroll
   for (int it = 0; it < CELL_ITEMS; ++it) {
     const uint32_t c = tile * CELL_TILE + warp * (32 * CELL_ITEMS) + it * 32 + lane;
@@ -1365,18 +1379,53 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
       const unsigned long long S = Ss[it];
       const float Sf = fx40_to_f(S);
       const float mp = fminf(Sf, 1.0f);
-      float mO, mF, rb;
-      cell_update(P, mp, mFs[it], zOs[it], zFs[it], mO, mF, rb);
-      const float rp = __fsub_rn(mO, rb);
+      float mO, mF, rb, rp, alloc;
+      float muA = 0.0f, pa = 0.0f;
+      if (full) {
+        // predicted Bernoulli RFS: persistent existence r_p = min(S, 1) (the weights of a cell
+        // whose sum exceeds 1 are scaled to sum 1), newborn r_b = p_B (1 - r_p) (Eq.
+        // pred_birth_prob); the Bernoulli update (Eq. filter_update, normalization_empty,
+        // normalization_meas) with the single-object likelihood 1 multiplies every particle
+        // weight of the cell by one factor f (Eq. updateParticleWeightsUnnormalized,
+        // applyNormalization, updateParticleWeightsEmpty)
+        const float rbp = __fmul_rn(P.p_B, __fsub_rn(1.0f, mp));
+        const float r = __fadd_rn(mp, rbp);
+        const float omr = __fsub_rn(1.0f, r);
+        const float ptp = zFs[it], pfp = B.zv[c];
+        float f;
+        if (zOs[it] != 0.0f) {
+          const float pa_ = B.pA[c], pc = B.sgv[c];
+          const float gam = __fadd_rn(pa_, __fmul_rn(__fsub_rn(1.0f, pa_), pc));
+          const float num = __fmul_rn(ptp, gam);
+          const float Nz = __fadd_rn(__fmul_rn(__fmul_rn(pfp, pc), omr), __fmul_rn(num, r));
+          f = __fdiv_rn(num, Nz);
+        } else {
+          const float a = __fsub_rn(1.0f, ptp);
+          const float Ne = __fadd_rn(__fmul_rn(a, r), __fmul_rn(__fsub_rn(1.0f, pfp), omr));
+          f = __fdiv_rn(a, Ne);
+        }
+        rp = __fmul_rn(f, mp);
+        rb = __fmul_rn(f, rbp);
+        mO = __fadd_rn(rp, rb);       // posterior existence = occupancy probability
+        mF = __fsub_rn(1.0f, mO);
+        alloc = rbp;                  // newborn slots follow the predicted newborn existence
+        muA = f;                      // newborn weights f r_b / n (k_birth_prep)
+        B.rb_pred[c] = rbp;
+        B.pO[c] = mO;
+        B.muU[c] = (S > 0ull) ? (Sf > 1.0f ? __fdiv_rn(f, Sf) : f) : 0.0f;
+      } else {
+        cell_update(P, mp, mFs[it], zOs[it], zFs[it], mO, mF, rb);
+        rp = __fsub_rn(mO, rb);
+        alloc = rb;
+        B.pO[c] = __fadd_rn(mO, __fmul_rn(0.5f, __fsub_rn(__fsub_rn(1.0f, mO), mF)));
+        B.muU[c] = (S > 0ull) ? __fdiv_rn(rp, Sf) : 0.0f;
+      }
       B.mpred[c] = mp;
       B.mO[c] = mO;
       B.mF[c] = mF;
       B.rho_b[c] = rb;
       B.rho_p[c] = rp;
-      B.pO[c] = __fadd_rn(mO, __fmul_rn(0.5f, __fsub_rn(__fsub_rn(1.0f, mO), mF)));
-      B.muU[c] = (S > 0ull) ? __fdiv_rn(rp, Sf) : 0.0f;
       B.rinv[c] = rp > 0.0f ? __fdiv_rn(1.0f, rp) : 0.0f;
-      float muA = 0.0f, pa = 0.0f;
       if constexpr (RADAR) {
         unsigned long long A = 0ull;
         if (cross) {
@@ -1423,7 +1472,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
       } else if (!occ) {
         B.mean_x[c] = 0.0f; B.mean_y[c] = 0.0f; B.var_x[c] = 0.0f; B.var_y[c] = 0.0f; B.cov[c] = 0.0f;
       }
-      qb = q40(rb);
+      qb = q40(alloc);
     }
     has[it] = qb > 0ull;
     // position among the warp's cells with newborn mass (ballot) and the inclusive prefix
@@ -1541,7 +1590,8 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_birth_prep(KParams P, DevBufs B)
     const uint32_t first = floor_muldiv(P.nu_b, Rex, R);
     const uint32_t last = floor_muldiv(P.nu_b, Rin, R);
     const uint32_t n = last > first ? last - first : 0u;
-    const float rb = B.rho_b[c];
+    const bool full = !RADAR && (P.flags & FLAG_FULL) != 0u;
+    const float rb = full ? B.rb_pred[c] : B.rho_b[c];
     const float pA = RADAR ? B.pA[c] : 0.0f;
     uint32_t nA = (uint32_t)__fadd_rn(__fmul_rn((float)n, pA), 0.5f);
     if (nA > n) nA = n;
@@ -1553,6 +1603,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_birth_prep(KParams P, DevBufs B)
     } else if (n > 0u) {
       wA = wUA = __fdiv_rn(rb, (float)n);
     }
+    if (full) wA = wUA = __fmul_rn(B.muA[c], wUA);  // predicted r_b / n, updated by f
     const uint32_t G = G0 + e;
     B.bl_first[G] = first;
     B.bl_gcell[G] = c;

@@ -46,7 +46,16 @@ class DogFilter:
     def set_measurement_grid(self, m_occ, m_free, p_A=None, z_vr=None, sigma_vr=None):
         """numpy arrays (host) or CUDA tensors (device) of C float32 values each."""
         arrs = dict(m_occ=m_occ, m_free=m_free, p_A=p_A, z_vr=z_vr, sigma_vr=sigma_vr)
-        on_dev = isinstance(m_occ, torch.Tensor) and m_occ.is_cuda
+        self._set_grid(arrs, N.dog_set_measurement_grid)
+
+    def set_bernoulli_grid(self, z, p_tp, p_fp, p_a, p_c):
+        """Bernoulli observation per cell (filters created with DOG_FULL): numpy arrays
+        (host) or CUDA tensors (device) of C float32 values each."""
+        self._set_grid(dict(z=z, p_tp=p_tp, p_fp=p_fp, p_a=p_a, p_c=p_c), N.dog_set_bernoulli_grid)
+
+    def _set_grid(self, arrs, call):
+        first = next(a for a in arrs.values() if a is not None)
+        on_dev = isinstance(first, torch.Tensor) and first.is_cuda
         ptrs, keep = {}, []
         for k, a in arrs.items():
             if a is None:
@@ -65,7 +74,7 @@ class DogFilter:
             self.stream.wait_stream(torch.cuda.current_stream(self.device))
             for t in keep:
                 t.record_stream(self.stream)
-        N.dog_set_measurement_grid(self.h, ptrs, N.DOG_DEVICE if on_dev else N.DOG_HOST)
+        call(self.h, ptrs, N.DOG_DEVICE if on_dev else N.DOG_HOST)
         self._keep = keep
 
     def set_ego_motion(self, dx: float, dy: float, dyaw: float):

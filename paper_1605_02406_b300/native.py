@@ -15,7 +15,7 @@ DOG_OK = 0
 DOG_ERR = {-1: "DOG_ERR_INVALID_ARG", -2: "DOG_ERR_WORKSPACE_TOO_SMALL", -3: "DOG_ERR_CUDA",
            -4: "DOG_ERR_DEVICE", -5: "DOG_ERR_INPUT", -6: "DOG_ERR_BAD_STATE",
            -7: "DOG_ERR_UNSUPPORTED"}
-DOG_NO_RESAMPLE, DOG_RECORD, DOG_NO_GRAPH, DOG_PROFILE, DOG_EGO = 0x2, 0x4, 0x8, 0x10, 0x20
+DOG_NO_RESAMPLE, DOG_RECORD, DOG_NO_GRAPH, DOG_PROFILE, DOG_EGO, DOG_FULL = 0x2, 0x4, 0x8, 0x10, 0x20, 0x40
 DOG_HOST, DOG_DEVICE, DOG_HOST_ASYNC = 0, 1, 2
 
 DBG = ["PRED_X", "PRED_Y", "PRED_VX", "PRED_VY", "PRED_W", "KEY", "PERM", "CELL_START",
@@ -30,7 +30,7 @@ SYMBOLS = ["dog_workspace_bytes", "dog_create", "dog_set_measurement_grid", "dog
            "dog_profile_read", "dog_kernels_per_step", "dog_destroy", "dog_error_string",
            "dog_assign_cells_noalloc", "dog_batch_create", "dog_batch_step", "dog_batch_destroy",
            "dog_last_cuda_error", "dog_eval_clusters", "dog_eval_mahalanobis",
-           "dog_get_cells_async", "dog_wait_cells", "dog_set_ego_motion"]
+           "dog_get_cells_async", "dog_wait_cells", "dog_set_ego_motion", "dog_set_bernoulli_grid"]
 DOG_NOALLOC_MAX_PARTICLES, DOG_NOALLOC_MAX_CELLS = 1 << 19, 1 << 22
 
 
@@ -45,6 +45,13 @@ class dog_params(C.Structure):
 
 class dog_meas_grid(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("m_occ", "m_free", "p_A", "z_vr", "sigma_vr")]
+
+
+BERN_FIELDS = ("z", "p_tp", "p_fp", "p_a", "p_c")
+
+
+class dog_bern_grid(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in BERN_FIELDS]
 
 
 CELL_FIELDS = ["m_occ", "m_free", "rho_p", "rho_b", "p_occ", "mean_vx", "mean_vy", "var_vx",
@@ -85,6 +92,7 @@ def lib() -> C.CDLL:
         L.dog_workspace_bytes.argtypes = [C.POINTER(dog_params), C.POINTER(sz)]
         L.dog_create.argtypes = [C.POINTER(dog_params), vp, sz, vp, C.POINTER(vp)]
         L.dog_set_measurement_grid.argtypes = [vp, C.POINTER(dog_meas_grid), C.c_int]
+        L.dog_set_bernoulli_grid.argtypes = [vp, C.POINTER(dog_bern_grid), C.c_int]
         L.dog_step.argtypes = [vp, C.c_float]
         L.dog_get_cells.argtypes = [vp, C.POINTER(dog_cells), C.c_int]
         L.dog_get_state.argtypes = [vp, C.POINTER(dog_state), C.c_int, C.POINTER(C.c_uint32)]
@@ -150,6 +158,11 @@ def dog_create(params: dog_params, workspace_ptr: int, nbytes: int, stream_ptr: 
 def dog_set_measurement_grid(h: int, ptrs: dict, mem_kind: int) -> None:
     g = dog_meas_grid(**{k: ptrs.get(k) for k in ("m_occ", "m_free", "p_A", "z_vr", "sigma_vr")})
     check("dog_set_measurement_grid", lib().dog_set_measurement_grid(h, C.byref(g), mem_kind))
+
+
+def dog_set_bernoulli_grid(h: int, ptrs: dict, mem_kind: int) -> None:
+    g = dog_bern_grid(**{k: ptrs.get(k) for k in BERN_FIELDS})
+    check("dog_set_bernoulli_grid", lib().dog_set_bernoulli_grid(h, C.byref(g), mem_kind))
 
 
 def dog_step(h: int, dt: float) -> None:

@@ -25,7 +25,7 @@ from paper_1605_02406_b300 import scene
 
 pytestmark = pytest.mark.gpu
 
-NO_RESAMPLE, RECORD, NO_GRAPH, EGO = 0x2, 0x4, 0x8, 0x20
+NO_RESAMPLE, RECORD, NO_GRAPH, EGO, FULL = 0x2, 0x4, 0x8, 0x20, 0x40
 MASS_FIELDS = ["m_occ", "m_free", "rho_p", "rho_b", "p_occ"]
 MOMENT_FIELDS = ["mean_vx", "mean_vy", "var_vx", "var_vy", "cov_vxy"]
 
@@ -229,6 +229,56 @@ def test_ego_motion_frames(flags):
                 f.set_ego_motion(*m)
             f.step(0.1)
         compare_frame(g, o, what=f"frame {k}: ")
+
+
+def _bern_grid(rng, W, H):
+    C = W * H
+    return dict(z=(rng.uniform(0, 1, C) < 0.3).astype(np.float32),
+                p_tp=rng.uniform(0.55, 0.95, C).astype(np.float32),
+                p_fp=rng.uniform(0.05, 0.45, C).astype(np.float32),
+                p_a=rng.uniform(0, 1, C).astype(np.float32),
+                p_c=rng.uniform(0.2, 5.0, C).astype(np.float32))
+
+
+@pytest.mark.parametrize("flags", [RECORD | FULL, RECORD | FULL | NO_GRAPH])
+def test_phdmib_frames(flags):
+    """The PHD/MIB filter of Sect. VI (Bernoulli observation per cell) bit for bit against
+    the oracle: predicted existence, newborn slots and weights, the per-cell update factor,
+    normalised weights, resampling, cell outputs, over several frames from a random state."""
+    p = small(48, 37, nu=3 * 4096 + 1234, nu_b=2 * 2048 + 77, flags=flags)
+    rng = np.random.default_rng(16)
+    st = scene.random_state(p, rng, occupied_frac=0.1)
+    grids = [_bern_grid(rng, 48, 37) for _ in range(3)]
+    g, o = _gpu(p), OracleFilter(p, "f32")
+    g.set_state(st)
+    o.set_state(st)
+    for k in range(4):
+        for f in (g, o):
+            f.set_bernoulli_grid(**grids[k % 3])
+            f.step(0.1)
+        compare_frame(g, o, what=f"frame {k}: ")
+
+
+def test_phdmib_grid_errors():
+    from paper_1605_02406_b300 import native as N
+    rng = np.random.default_rng(5)
+    full = _gpu(small(8, 8, nu=256, nu_b=16, flags=FULL))
+    ds = _gpu(small(8, 8, nu=256, nu_b=16))
+    bg = _bern_grid(rng, 8, 8)
+    with pytest.raises(N.DogError) as e:
+        full.set_measurement_grid(np.zeros(64, np.float32), np.zeros(64, np.float32))
+    assert e.value.code == -6
+    with pytest.raises(N.DogError) as e:
+        ds.set_bernoulli_grid(**bg)
+    assert e.value.code == -6
+    bad = dict(bg, z=np.full(64, 0.5, np.float32))  # z must be 0 or 1
+    full.set_bernoulli_grid(**bad)
+    with pytest.raises(N.DogError) as e:
+        full.sync()
+    assert e.value.code == -5
+    full.set_bernoulli_grid(**bg)
+    full.step(0.1)
+    full.sync()
 
 
 def test_ego_motion_call_errors():
