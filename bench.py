@@ -330,6 +330,35 @@ def ego_rate(steps: int, warmup: int) -> dict:
     return out
 
 
+def phdmib_rate(steps: int, warmup: int) -> dict:
+    """Device-resident step rate of the PHD/MIB filter (Sect. VI) on the 1024x1024 workload,
+    its Bernoulli grids derived from the same lidar scenes (scene.bernoulli_grid)."""
+    import torch
+
+    from paper_1605_02406_b300 import native as N
+    from paper_1605_02406_b300.filter import DogFilter
+    cfg = scene.CONFIGS["automotive_1024"]
+    grids = [scene.bernoulli_grid(g) for g in scene.frame_sequence(cfg, 8, 1002)]
+    dev = [{k: torch.tensor(v, device="cuda") for k, v in g.items()} for g in grids]
+    params = scene.filter_params(cfg, flags=N.DOG_FULL)
+    f = DogFilter(params)
+    for k in range(warmup):
+        f.set_bernoulli_grid(**dev[k % 8])
+        f.step(cfg["dt"])
+    f.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(f.stream)
+    for k in range(steps):
+        f.set_bernoulli_grid(**dev[(warmup + k) % 8])
+        f.step(cfg["dt"])
+    e1.record(f.stream)
+    f.sync()
+    ms = e0.elapsed_time(e1) / steps
+    f.close()
+    return {"workload": cfg["name"] + ", PHD/MIB filter (Bernoulli observation)", "steps": steps,
+            "ms_per_step": ms, "value": params["nu"] / (ms * 1e-3), "unit": "particle-updates/s"}
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -342,6 +371,7 @@ def main() -> None:
     ap.add_argument("--no-evaluation", action="store_true", help="skip timing the evaluation calls")
     ap.add_argument("--no-serving", action="store_true", help="skip the 3 s serving-loop run")
     ap.add_argument("--no-ego", action="store_true", help="skip the ego-motion workload")
+    ap.add_argument("--no-phdmib", action="store_true", help="skip the PHD/MIB filter workload")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -490,6 +520,7 @@ def main() -> None:
     if not args.no_fusion:
         fusion = fusion_rate(steps=min(args.steps, 100), warmup=args.warmup)
     ego = None if args.no_ego else ego_rate(steps=min(args.steps, 200), warmup=args.warmup)
+    phdmib = None if args.no_phdmib else phdmib_rate(steps=min(args.steps, 200), warmup=args.warmup)
     batched = {"workload": None}
     if not args.no_batched:
         batched = batched_latency(frames=min(args.steps, 50), warmup=args.warmup)
@@ -523,6 +554,7 @@ def main() -> None:
         "cpu_baseline": cpu,
         "fusion": fusion,
         "ego": ego,
+        "phdmib": phdmib,
         "evaluation": evaluation,
         "serving": serving,
     }

@@ -373,6 +373,20 @@ def random_measurement_grid(W: int, H: int, rng: np.random.Generator, radar: boo
     return out
 
 
+def bernoulli_grid(grid: dict, p_tp: float = 0.9, p_fp: float = 0.1, p_a: float = 0.9) -> dict:
+    """Bernoulli observation per cell for the PHD/MIB filter from a lidar measurement grid of
+    this module: a cell with a hit (m_occ > 0) is measured (z = 1); cells the beams saw (a hit
+    or free space) get the sensor's true / false positive probabilities, unseen cells
+    p_TP = p_FP = 0.5 (no information); p_c = 1 (clutter as likely as the object over the
+    cell)."""
+    occ = np.asarray(grid["m_occ"]) > 0
+    seen = occ | (np.asarray(grid["m_free"]) > 0)
+    f32 = np.float32
+    return dict(z=occ.astype(f32), p_tp=np.where(seen, f32(p_tp), f32(0.5)).astype(f32),
+                p_fp=np.where(seen, f32(p_fp), f32(0.5)).astype(f32),
+                p_a=np.full(occ.size, f32(p_a)), p_c=np.ones(occ.size, f32))
+
+
 def random_state(params: dict, rng: np.random.Generator, occupied_frac: float = 0.05,
                  frame: int = 7) -> dict:
     """A posterior-like particle state: most particles clustered in a few cells (per-cell
