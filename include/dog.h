@@ -53,6 +53,8 @@ typedef enum dog_status {
 #define DOG_EGO 0x20u        /* the grid moves with the vehicle: dog_set_ego_motion         */
 #define DOG_FULL 0x40u       /* the PHD/MIB filter of Sect. VI with its Bernoulli observation
                                 (dog_set_bernoulli_grid) instead of the DS approximation */
+#define DOG_AUTOTUNE 0x80u   /* reserve the buffers of a sort with one pass more, so that
+                                dog_autotune / dog_set_sort_config may choose it */
 
 /* memory kind of caller buffers */
 #define DOG_HOST 0
@@ -205,6 +207,27 @@ int dog_wait_cells(dog_filter *f);
  * its copies completed. */
 int dog_get_state(dog_filter *f, const dog_state *out, int mem_kind, uint32_t *frame);
 int dog_set_state(dog_filter *f, const dog_state *in, int mem_kind, uint32_t frame);
+
+/* Sort configuration (Alg. 2: the LSD radix sort of particles by cell index): the number of
+ * digit passes (the digit width is ceil(key bits / passes), at most 11) and the number of
+ * sort tiles that one block of the digit-counting kernel takes (1, 2, 4 or 8).  Every
+ * configuration sorts to the same order, so results are the same bit for bit; only the
+ * speed differs.  The default is the fewest passes and the tiles per block that leave two
+ * blocks per SM.
+ *
+ * dog_autotune times every configuration the workspace allows (the default number of
+ * passes, and one more with DOG_AUTOTUNE) on the predicted keys of the last step, on the
+ * filter's stream (it synchronises), and keeps the fastest; the choice is also cached for
+ * the process by the size class (ceil log2 num_particles, ceil log2 cells) and applied to
+ * filters of that class created later.  The filter's state and outputs are unchanged.  A
+ * batch keeps the configuration its filters had when it was created.
+ * Errors: BAD_STATE (no step yet), CUDA.
+ * dog_set_sort_config sets one explicitly.  Errors: INVALID_ARG, UNSUPPORTED (a
+ * configuration the workspace does not hold or an invalid tile count).
+ * dog_sort_config reads the current one (any output pointer may be NULL). */
+int dog_autotune(dog_filter *f);
+int dog_set_sort_config(dog_filter *f, int passes, int count_tiles);
+int dog_sort_config(const dog_filter *f, int *passes, int *digit_bits, int *count_tiles);
 
 /* Wait for the filter's stream; return a latched device error, else DOG_OK. */
 int dog_sync(dog_filter *f);

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -80,11 +81,13 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
   uint32_t **pu[] = {&B->key_pred, &B->key_sorted, &B->perm};
   for (auto q : pu) *q = (uint32_t *)take(4 * nu);
   B->key_t0 = B->val_t0 = B->key_t1 = B->val_t1 = nullptr;
-  if (d.passes >= 2) {
+  // DOG_AUTOTUNE: also the ping-pong buffers of a sort with one pass more
+  const int max_passes = (p.flags & DOG_AUTOTUNE) ? (d.passes < 3 ? d.passes + 1 : 3) : d.passes;
+  if (max_passes >= 2) {
     B->key_t0 = (uint32_t *)take(4 * nu);
     B->val_t0 = (uint32_t *)take(4 * nu);
   }
-  if (d.passes >= 3) {
+  if (max_passes >= 3) {
     B->key_t1 = (uint32_t *)take(4 * nu);
     B->val_t1 = (uint32_t *)take(4 * nu);
   }
@@ -114,7 +117,7 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
   B->bl_wA = (float *)take(4 * CL);
   B->bl_wUA = (float *)take(4 * CL);
   B->birth_block_entry = (uint32_t *)take(4 * ((nb + BIRTH_SLOTS - 1) / BIRTH_SLOTS + 1));
-  B->hist = (uint32_t *)take(4 * 2048 * (size_t)d.passes);
+  B->hist = (uint32_t *)take(4 * 2048 * (size_t)max_passes);
   B->dcnt = (uint32_t *)take(4 * (size_t)d.passes * d.tiles_sort * d.radix);
   B->S_piece = (unsigned long long *)take(8 * C);
   B->A_piece = (unsigned long long *)take(8 * C);
@@ -389,6 +392,8 @@ int issue_ego(dog_filter *f, cudaStream_t st) {
 }
 }  // namespace
 
+static void apply_cached_sort_cfg(dog_filter *f);
+
 int dog_create(const dog_params *params, void *d_workspace, size_t workspace_bytes, void *cuda_stream,
                dog_filter **out) {
   if (!out || !d_workspace) return DOG_ERR_INVALID_ARG;
@@ -442,6 +447,7 @@ int dog_create(const dog_params *params, void *d_workspace, size_t workspace_byt
   f->birth_grid = (int)((params->num_birth + BIRTH_SLOTS - 1) / BIRTH_SLOTS);
   f->count_ct = count_tiles_per_block(d.tiles_sort, sms);
   if (f->birth_grid < 1) f->birth_grid = 1;
+  apply_cached_sort_cfg(f);
   // the attribute is per kernel, shared by all filters: allow the largest digit's need
   cudaError_t e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sort_smem_bytes(2048));
@@ -896,7 +902,7 @@ int dog_profile_read(dog_filter *f, float *ms, const char **names, int max, int 
   slot_kind[nk++] = 1;
   slot_kind[nk++] = 2;
   slot_kind[nk++] = 3;
-  for (int p = 1; p < f->d.passes; ++p) {
+  for (int p = 1; p < f->K.passes; ++p) {
     slot_kind[nk++] = 1 + 3 * p;
     slot_kind[nk++] = 2 + 3 * p;
     slot_kind[nk++] = 3 + 3 * p;
@@ -1069,4 +1075,147 @@ extern "C" int dog_assign_cells_noalloc(const uint32_t *d_keys, uint32_t n, uint
   const uint32_t rgrid = (n + 255) / 256 < 2048u ? (n + 255) / 256 : 2048u;
   k_na_ranges<<<rgrid, 256, 0, st>>>(key_sorted, n, num_cells, d_cell_start, d_cell_end);
   return cuda_fail(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------------------------
+// Sort configuration (passes and digit width, sort tiles per counting block) and its
+// autotuning.  Every configuration sorts to the same order, so the choice changes speed
+// only.  Tuned choices are cached for the process by the size class (ceil log2 nu,
+// ceil log2 C) and given to filters created later in the same class.
+// ------------------------------------------------------------------------------------
+namespace {
+struct SortCfg {
+  int passes;
+  uint32_t ct;
+};
+std::mutex g_tune_mutex;
+std::map<std::pair<int, int>, SortCfg> g_tune_cache;
+
+int ceil_log2(uint64_t x) {
+  int b = 0;
+  while ((1ull << b) < x) ++b;
+  return b;
+}
+std::pair<int, int> size_class(const dog_filter *f) {
+  return {ceil_log2(f->p.num_particles), ceil_log2(f->d.C)};
+}
+
+// whether the filter's workspace holds a sort of `passes` passes (ping-pong buffers, digit
+// histograms, per-tile digit counts) and ct is a valid number of tiles per counting block
+bool sort_cfg_ok(const dog_filter *f, int passes, uint32_t ct) {
+  if (passes < 1 || passes > 3) return false;
+  const int dbits = (f->d.key_bits + passes - 1) / passes;
+  if (dbits < 1 || dbits > 11) return false;
+  if (passes >= 2 && !f->B.key_t0) return false;
+  if (passes >= 3 && !f->B.key_t1) return false;
+  const size_t need = (size_t)passes * f->d.tiles_sort * (1u << dbits);
+  if (need > (size_t)f->d.passes * f->d.tiles_sort * f->d.radix) return false;
+  return ct == 1u || ct == 2u || ct == 4u || ct == 8u;
+}
+
+void set_sort_cfg(dog_filter *f, int passes, uint32_t ct) {
+  const int dbits = (f->d.key_bits + passes - 1) / passes;
+  f->K.passes = passes;
+  f->K.dbits = dbits;
+  f->K.radix = 1u << dbits;
+  f->count_ct = ct;
+  f->nk = 9 + 3 * passes;
+  for (auto &g : f->gexec)  // the next step captures the frame again
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+// the sort of the filter's current predicted keys with configuration (passes, ct); the
+// first pass's digit counts come from the keys themselves (in a frame, from k_predict)
+int enqueue_sort(dog_filter *f, int passes, uint32_t ct, cudaEvent_t e0, cudaEvent_t e1) {
+  KParams K = f->K;
+  K.dbits = (f->d.key_bits + passes - 1) / passes;
+  K.passes = passes;
+  K.radix = 1u << K.dbits;
+  const DevBufs &B = f->B;
+  cudaStream_t st = f->st;
+  DOG_CUDA(cudaMemsetAsync(B.hist, 0, 4 * 2048 * (size_t)passes, st));
+  k_na_hist<<<K.tiles_sort, 256, 4u * K.passes * K.radix, st>>>(B.key_pred, K, B);
+  DOG_CUDA(cudaEventRecord(e0, st));
+  const size_t ssm = sort_smem_bytes(K.radix);
+  const uint32_t *kin = B.key_pred, *vin = nullptr;
+  for (int p = 0; p < passes; ++p) {
+    uint32_t *kout = p == passes - 1 ? B.key_sorted : (p == 0 ? B.key_t0 : B.key_t1);
+    uint32_t *vout = p == passes - 1 ? B.perm : (p == 0 ? B.val_t0 : B.val_t1);
+    if (p > 0)
+      k_sort_count<<<(K.tiles_sort + ct - 1) / ct, COUNT_BLOCK, count_smem_bytes(K.radix, ct), st>>>(K, B, kin,
+                                                                                                      p, ct);
+    k_sort_offsets<<<K.radix, OFF_BLOCK, 0, st>>>(K, B, p);
+    k_sort_pass<<<K.tiles_sort, SORT_BLOCK, ssm, st>>>(K, B, kin, vin, kout, vout, p);
+    kin = kout;
+    vin = vout;
+  }
+  DOG_CUDA(cudaEventRecord(e1, st));
+  return cuda_fail(cudaGetLastError());
+}
+}  // namespace
+
+static void apply_cached_sort_cfg(dog_filter *f) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  const auto it = g_tune_cache.find(size_class(f));
+  if (it != g_tune_cache.end() && sort_cfg_ok(f, it->second.passes, it->second.ct))
+    set_sort_cfg(f, it->second.passes, it->second.ct);
+}
+
+int dog_sort_config(const dog_filter *f, int *passes, int *digit_bits, int *count_tiles) {
+  if (!f) return DOG_ERR_INVALID_ARG;
+  if (passes) *passes = f->K.passes;
+  if (digit_bits) *digit_bits = f->K.dbits;
+  if (count_tiles) *count_tiles = (int)f->count_ct;
+  return DOG_OK;
+}
+
+int dog_set_sort_config(dog_filter *f, int passes, int count_tiles) {
+  if (!f || count_tiles < 1) return DOG_ERR_INVALID_ARG;
+  if (!sort_cfg_ok(f, passes, (uint32_t)count_tiles)) return DOG_ERR_UNSUPPORTED;
+  set_sort_cfg(f, passes, (uint32_t)count_tiles);
+  return DOG_OK;
+}
+
+int dog_autotune(dog_filter *f) {
+  if (!f) return DOG_ERR_INVALID_ARG;
+  if (f->frame == 0) return DOG_ERR_BAD_STATE;  // times the keys of a frame
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  DOG_CUDA(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(ce);
+  }
+  SortCfg best{f->K.passes, f->count_ct};
+  float best_ms = 3.0e38f;
+  int rc = DOG_OK;
+  for (int passes = f->d.passes; passes <= f->d.passes + 1 && rc == DOG_OK; ++passes)
+    for (uint32_t ct = 1; ct <= (uint32_t)COUNT_TILES && rc == DOG_OK; ct *= 2) {
+      if (!sort_cfg_ok(f, passes, ct) || (passes == 1 && ct > 1)) continue;  // ct: later passes
+      float ms = 3.0e38f;
+      for (int rep = 0; rep < 5 && rc == DOG_OK; ++rep) {  // the best of five
+        rc = enqueue_sort(f, passes, ct, e0, e1);
+        if (rc == DOG_OK) {
+          ce = cudaEventSynchronize(e1);
+          float t = 0.0f;
+          if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+          if (ce != cudaSuccess) rc = cuda_fail(ce);
+          if (t < ms) ms = t;
+        }
+      }
+      if (rc == DOG_OK && ms < best_ms) {
+        best_ms = ms;
+        best = SortCfg{passes, ct};
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  set_sort_cfg(f, best.passes, best.ct);
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune_cache[size_class(f)] = best;
+  return DOG_OK;
 }

@@ -77,6 +77,17 @@ class DogFilter:
         call(self.h, ptrs, N.DOG_DEVICE if on_dev else N.DOG_HOST)
         self._keep = keep
 
+    def autotune(self) -> dict:
+        """Time the sort configurations on the last step's keys and keep the fastest."""
+        N.dog_autotune(self.h)
+        return self.sort_config()
+
+    def sort_config(self) -> dict:
+        return N.dog_sort_config(self.h)
+
+    def set_sort_config(self, passes: int, count_tiles: int):
+        N.dog_set_sort_config(self.h, passes, count_tiles)
+
     def set_ego_motion(self, dx: float, dy: float, dyaw: float):
         """Vehicle motion since the previous frame (filters created with DOG_EGO): moved by
         (dx, dy) m in the previous grid's axes, turned by dyaw rad about the sensor."""

@@ -15,7 +15,8 @@ DOG_OK = 0
 DOG_ERR = {-1: "DOG_ERR_INVALID_ARG", -2: "DOG_ERR_WORKSPACE_TOO_SMALL", -3: "DOG_ERR_CUDA",
            -4: "DOG_ERR_DEVICE", -5: "DOG_ERR_INPUT", -6: "DOG_ERR_BAD_STATE",
            -7: "DOG_ERR_UNSUPPORTED"}
-DOG_NO_RESAMPLE, DOG_RECORD, DOG_NO_GRAPH, DOG_PROFILE, DOG_EGO, DOG_FULL = 0x2, 0x4, 0x8, 0x10, 0x20, 0x40
+DOG_NO_RESAMPLE, DOG_RECORD, DOG_NO_GRAPH, DOG_PROFILE = 0x2, 0x4, 0x8, 0x10
+DOG_EGO, DOG_FULL, DOG_AUTOTUNE = 0x20, 0x40, 0x80
 DOG_HOST, DOG_DEVICE, DOG_HOST_ASYNC = 0, 1, 2
 
 DBG = ["PRED_X", "PRED_Y", "PRED_VX", "PRED_VY", "PRED_W", "KEY", "PERM", "CELL_START",
@@ -30,7 +31,8 @@ SYMBOLS = ["dog_workspace_bytes", "dog_create", "dog_set_measurement_grid", "dog
            "dog_profile_read", "dog_kernels_per_step", "dog_destroy", "dog_error_string",
            "dog_assign_cells_noalloc", "dog_batch_create", "dog_batch_step", "dog_batch_destroy",
            "dog_last_cuda_error", "dog_eval_clusters", "dog_eval_mahalanobis",
-           "dog_get_cells_async", "dog_wait_cells", "dog_set_ego_motion", "dog_set_bernoulli_grid"]
+           "dog_get_cells_async", "dog_wait_cells", "dog_set_ego_motion", "dog_set_bernoulli_grid",
+           "dog_autotune", "dog_set_sort_config", "dog_sort_config"]
 DOG_NOALLOC_MAX_PARTICLES, DOG_NOALLOC_MAX_CELLS = 1 << 19, 1 << 22
 
 
@@ -93,6 +95,9 @@ def lib() -> C.CDLL:
         L.dog_create.argtypes = [C.POINTER(dog_params), vp, sz, vp, C.POINTER(vp)]
         L.dog_set_measurement_grid.argtypes = [vp, C.POINTER(dog_meas_grid), C.c_int]
         L.dog_set_bernoulli_grid.argtypes = [vp, C.POINTER(dog_bern_grid), C.c_int]
+        L.dog_autotune.argtypes = [vp]
+        L.dog_set_sort_config.argtypes = [vp, C.c_int, C.c_int]
+        L.dog_sort_config.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.dog_step.argtypes = [vp, C.c_float]
         L.dog_get_cells.argtypes = [vp, C.POINTER(dog_cells), C.c_int]
         L.dog_get_state.argtypes = [vp, C.POINTER(dog_state), C.c_int, C.POINTER(C.c_uint32)]
@@ -163,6 +168,20 @@ def dog_set_measurement_grid(h: int, ptrs: dict, mem_kind: int) -> None:
 def dog_set_bernoulli_grid(h: int, ptrs: dict, mem_kind: int) -> None:
     g = dog_bern_grid(**{k: ptrs.get(k) for k in BERN_FIELDS})
     check("dog_set_bernoulli_grid", lib().dog_set_bernoulli_grid(h, C.byref(g), mem_kind))
+
+
+def dog_autotune(h: int) -> None:
+    check("dog_autotune", lib().dog_autotune(h))
+
+
+def dog_set_sort_config(h: int, passes: int, count_tiles: int) -> None:
+    check("dog_set_sort_config", lib().dog_set_sort_config(h, int(passes), int(count_tiles)))
+
+
+def dog_sort_config(h: int) -> dict:
+    a, b, c = C.c_int(), C.c_int(), C.c_int()
+    check("dog_sort_config", lib().dog_sort_config(h, C.byref(a), C.byref(b), C.byref(c)))
+    return {"passes": a.value, "digit_bits": b.value, "count_tiles": c.value}
 
 
 def dog_step(h: int, dt: float) -> None:
