@@ -163,3 +163,40 @@ def test_batch_with_ego_motion_equals_single_filters():
                     va, vb = va.astype(np.float32).view(np.uint32), vb.astype(np.float32).view(np.uint32)
                 assert np.array_equal(va, vb), f"frame {frame}, filter {i}: {k} differs"
     batch.close()
+
+
+def test_batch_with_phdmib_filter_equals_single_filters():
+    """A PHD/MIB filter (Sect. VI, Bernoulli observation) next to a DS filter in a batch."""
+    import torch
+
+    from paper_1605_02406_b300.filter import DogBatch, DogFilter
+    cases = [dict(CASES[1], flags=0x40), CASES[0]]
+    shared = torch.cuda.Stream()
+    batched = [DogFilter(p, stream=shared) for p in cases]
+    single = [DogFilter(p) for p in cases]
+    rng = np.random.default_rng(19)
+    grids = []
+    for fb, fs, p in zip(batched, single, cases):
+        st = scene.random_state(p, rng, occupied_frac=0.1)
+        fb.set_state(st)
+        fs.set_state(st)
+        grids.append([scene.random_measurement_grid(p["width"], p["height"], rng) for _ in range(3)])
+    grids[0] = [scene.bernoulli_grid(g) for g in grids[0]]
+    batch = DogBatch(batched)
+    for frame in range(3):
+        for i in range(2):
+            for f in (batched[i], single[i]):
+                if i == 0:
+                    f.set_bernoulli_grid(**grids[i][frame])
+                else:
+                    f.set_measurement_grid(**grids[i][frame])
+            single[i].step(0.1)
+        batch.step([0.1, 0.1])
+        for i in range(2):
+            a, b = _snapshot(batched[i]), _snapshot(single[i])
+            for k in a:
+                va, vb = np.asarray(a[k]), np.asarray(b[k])
+                if va.dtype.kind == "f":
+                    va, vb = va.astype(np.float32).view(np.uint32), vb.astype(np.float32).view(np.uint32)
+                assert np.array_equal(va, vb), f"frame {frame}, filter {i}: {k} differs"
+    batch.close()

@@ -240,11 +240,12 @@ def _bern_grid(rng, W, H):
                 p_c=rng.uniform(0.2, 5.0, C).astype(np.float32))
 
 
-@pytest.mark.parametrize("flags", [RECORD | FULL, RECORD | FULL | NO_GRAPH])
+@pytest.mark.parametrize("flags", [RECORD | FULL, RECORD | FULL | NO_GRAPH, RECORD | FULL | EGO])
 def test_phdmib_frames(flags):
     """The PHD/MIB filter of Sect. VI (Bernoulli observation per cell) bit for bit against
     the oracle: predicted existence, newborn slots and weights, the per-cell update factor,
-    normalised weights, resampling, cell outputs, over several frames from a random state."""
+    normalised weights, resampling, cell outputs, over several frames from a random state
+    (with ego motion on some frames when the filter compensates it)."""
     p = small(48, 37, nu=3 * 4096 + 1234, nu_b=2 * 2048 + 77, flags=flags)
     rng = np.random.default_rng(16)
     st = scene.random_state(p, rng, occupied_frac=0.1)
@@ -252,9 +253,12 @@ def test_phdmib_frames(flags):
     g, o = _gpu(p), OracleFilter(p, "f32")
     g.set_state(st)
     o.set_state(st)
+    motions = [(0.3, 0.2, 0.04), None, (-0.5, 0.0, -0.02), None]
     for k in range(4):
         for f in (g, o):
             f.set_bernoulli_grid(**grids[k % 3])
+            if flags & EGO and motions[k] is not None:
+                f.set_ego_motion(*motions[k])
             f.step(0.1)
         compare_frame(g, o, what=f"frame {k}: ")
 
