@@ -911,6 +911,7 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
   // left the grid (flagged in the particle index), so only the record is gathered
   const bool uniform = B.ctl->post_mode == POST_RESAMPLED;
   const float wu = __fmul_rn(P.p_S, B.ctl->w_new);
+  const unsigned long long qwu = q40(wu);  // the fixed-point weight of every in-grid particle
   uint32_t gi[SEG_ITEMS];
 #pragma unroll
   for (int it = 0; it < SEG_ITEMS; ++it) {
@@ -937,7 +938,7 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
     if (j < P.nu) {
       B.Os[j] = st[it];
       B.Ow[j] = w[it];
-      q = q40(w[it]);
+      q = uniform ? (w[it] > 0.0f ? qwu : 0ull) : q40(w[it]);
       if constexpr (RADAR) {
         const uint32_t c = __ldg(B.key_sorted + j);
         float g = 0.0f;
@@ -1035,6 +1036,9 @@ __global__ void __launch_bounds__(SEG_BLOCK, 4) k_segsum_lidar(KParams P, DevBuf
   // sort carries that flag in the particle index), so only the record is gathered.
   const bool uniform = B.ctl->post_mode == POST_RESAMPLED;
   const float wu = __fmul_rn(P.p_S, B.ctl->w_new);
+  // the fixed-point weight: after a resampled frame a weight is wu or 0, so q40(wu) or 0
+  const unsigned long long qwu = q40(wu);
+  const auto qw = [&](float w) { return uniform ? (w > 0.0f ? qwu : 0ull) : q40(w); };
   uint32_t gi[SEG_ITEMS];
 #pragma unroll
   for (int it = 0; it < SEG_ITEMS; ++it) {
@@ -1088,7 +1092,7 @@ __global__ void __launch_bounds__(SEG_BLOCK, 4) k_segsum_lidar(KParams P, DevBuf
     const uint32_t m = pad8(threadIdx.x * SEG_ITEMS + it);
     SegQM e;
     e.f = h;
-    e.q = q40(s_x[0][m]);
+    e.q = qw(s_x[0][m]);
     moment_terms(s_x[0][m], s_x[1][m], s_x[2][m], e.m);
     agg = seg_combine(agg, e);
   }
@@ -1109,7 +1113,7 @@ __global__ void __launch_bounds__(SEG_BLOCK, 4) k_segsum_lidar(KParams P, DevBuf
     if (j >= P.nu) break;
     const bool h = (head >> it) & 1u, t = (tail >> it) & 1u;
     const uint32_t m = pad8(threadIdx.x * SEG_ITEMS + it);
-    const unsigned long long q = q40(s_x[0][m]);
+    const unsigned long long q = qw(s_x[0][m]);
     float mt[5];
     moment_terms(s_x[0][m], s_x[1][m], s_x[2][m], mt);
     rq = h ? q : rq + q;
