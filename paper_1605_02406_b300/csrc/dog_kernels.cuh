@@ -1866,10 +1866,12 @@ __global__ void __launch_bounds__(NORM_BLOCK) k_normalise_lidar(KParams P, DevBu
     load_runf<NORM_ITEMS>(B.Ow, j0, P.nu, ws);
 #pragma unroll
     for (int it = 0; it < NORM_ITEMS; ++it) cmu[it] = j0 + it < P.nu ? __ldg(B.muU + key[it]) : 0.0f;
+    unsigned long long qprev = 0ull;
 #pragma unroll
-    for (int it = 0; it < NORM_ITEMS; ++it) {
+    for (int it = 0; it < NORM_ITEMS; ++it) {  // neighbours mostly share a cell and so a weight
       wn[it] = __fmul_rn(cmu[it], ws[it]);
-      qsum += q40(wn[it]);
+      qprev = (it > 0 && wn[it] == wn[it - 1]) ? qprev : q40(wn[it]);
+      qsum += qprev;
     }
     store_run<NORM_ITEMS>(B.wn, j0, P.nu, wn);
   }
@@ -1971,8 +1973,8 @@ __global__ void __launch_bounds__(RES_BLOCK, 2) k_resample(KParams P, DevBufs B)
   }
   unsigned long long q[RES_ITEMS], loc = 0ull;
 #pragma unroll
-  for (int it = 0; it < RES_ITEMS; ++it) {
-    q[it] = q40(w[it]);
+  for (int it = 0; it < RES_ITEMS; ++it) {  // neighbours mostly share a cell and so a weight
+    q[it] = (it > 0 && w[it] == w[it - 1]) ? q[it - 1] : q40(w[it]);
     loc += q[it];
   }
   unsigned long long inc = loc;
