@@ -686,10 +686,14 @@ __global__ void __launch_bounds__(SORT_BLOCK, 2)
 // the predicted particles in sorted order, so later kernels stream them contiguously.  No block waits for
 // another block.
 // ====================================================================================
-constexpr int SEG_BLOCK = 256, SEG_ITEMS = 8, SEG_TILE = SEG_BLOCK * SEG_ITEMS;
+// 1024-position tiles: smaller tiles keep more blocks (and their gathers) in flight on
+// each SM than 2048-position ones, at the price of more cells crossing a tile edge
+constexpr int SEG_BLOCK = 256, SEG_ITEMS = 4, SEG_TILE = SEG_BLOCK * SEG_ITEMS;
 
-// shared-memory index padded by one element per 8 (blocked accesses hit distinct banks)
-__device__ __forceinline__ uint32_t pad8(uint32_t m) { return m + (m >> 3); }
+// shared-memory index padded by one element per SEG_ITEMS: a thread's blocked run starts
+// SEG_ITEMS + 1 elements after its neighbour's (odd, so a warp hits 32 distinct banks)
+__device__ __forceinline__ uint32_t seg_pad(uint32_t m) { return m + m / SEG_ITEMS; }
+constexpr int SEG_PADDED = SEG_TILE + SEG_TILE / SEG_ITEMS;
 
 template <int N, typename V = unsigned long long>
 struct Seg {
@@ -900,7 +904,7 @@ template <bool RADAR>
 __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
   constexpr int N = RADAR ? 2 : 1;
   __shared__ Seg<N> s_w[SEG_BLOCK / 32 + 1];
-  __shared__ unsigned long long s_q[N][SEG_TILE + SEG_TILE / 8];  // padded: m -> m + m/8
+  __shared__ unsigned long long s_q[N][SEG_PADDED];
   const uint32_t tile = blockIdx.x, frame = B.ctl->frame;
   const uint32_t base = tile * SEG_TILE;
   const uint32_t last_valid = min(base + SEG_TILE, P.nu) - 1u;
@@ -949,8 +953,8 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
         B.wn[j] = g;  // kept for k_normalise, which overwrites it with the normalised weight
       }
     }
-    s_q[0][pad8(m)] = q;
-    if constexpr (RADAR) s_q[N - 1][pad8(m)] = gq;
+    s_q[0][seg_pad(m)] = q;
+    if constexpr (RADAR) s_q[N - 1][seg_pad(m)] = gq;
   }
   __syncthreads();
   // scan phase, blocked: a thread owns ITEMS consecutive positions
@@ -976,7 +980,7 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
     head |= (uint32_t)h << it;
     tail |= (uint32_t)t << it;
 #pragma unroll
-    for (int k = 0; k < N; ++k) v[it][k] = s_q[k][pad8(threadIdx.x * SEG_ITEMS + it)];
+    for (int k = 0; k < N; ++k) v[it][k] = s_q[k][seg_pad(threadIdx.x * SEG_ITEMS + it)];
     Seg<N> e;
     e.f = h;
 #pragma unroll
@@ -1025,9 +1029,9 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
 // scan; a cell inside the tile is finished here; a cell spread over tiles adds the pieces
 // of S in exact 2^-40 fixed point and leaves its binary32 moment pieces in per-tile slots,
 // which k_cell adds in tile order.
-__global__ void __launch_bounds__(SEG_BLOCK, 4) k_segsum_lidar(KParams P, DevBufs B) {
+__global__ void __launch_bounds__(SEG_BLOCK, 6) k_segsum_lidar(KParams P, DevBufs B) {
   __shared__ SegQM s_wqm[SEG_BLOCK / 32 + 1];
-  __shared__ float s_x[3][SEG_TILE + SEG_TILE / 8];  // w, vx, vy in tile order (padded)
+  __shared__ float s_x[3][SEG_PADDED];  // w, vx, vy in tile order (padded)
   const uint32_t tile = blockIdx.x, frame = B.ctl->frame;
   const uint32_t base = tile * SEG_TILE;
   const uint32_t last_valid = min(base + SEG_TILE, P.nu) - 1u;
@@ -1065,9 +1069,9 @@ __global__ void __launch_bounds__(SEG_BLOCK, 4) k_segsum_lidar(KParams P, DevBuf
       B.Os[j] = st[it];
       B.Ow[j] = w[it];
     }
-    s_x[0][pad8(m)] = w[it];
-    s_x[1][pad8(m)] = st[it].z;
-    s_x[2][pad8(m)] = st[it].w;
+    s_x[0][seg_pad(m)] = w[it];
+    s_x[1][seg_pad(m)] = st[it].z;
+    s_x[2][seg_pad(m)] = st[it].w;
   }
   __syncthreads();
   // scan phase, blocked: a thread owns ITEMS consecutive positions
@@ -1089,7 +1093,7 @@ __global__ void __launch_bounds__(SEG_BLOCK, 4) k_segsum_lidar(KParams P, DevBuf
     const bool t = ok && (j == P.nu - 1 || key[it] != kn);
     head |= (uint32_t)h << it;
     tail |= (uint32_t)t << it;
-    const uint32_t m = pad8(threadIdx.x * SEG_ITEMS + it);
+    const uint32_t m = seg_pad(threadIdx.x * SEG_ITEMS + it);
     SegQM e;
     e.f = h;
     e.q = qw(s_x[0][m]);
@@ -1112,7 +1116,7 @@ __global__ void __launch_bounds__(SEG_BLOCK, 4) k_segsum_lidar(KParams P, DevBuf
     const uint32_t j = j0 + it;
     if (j >= P.nu) break;
     const bool h = (head >> it) & 1u, t = (tail >> it) & 1u;
-    const uint32_t m = pad8(threadIdx.x * SEG_ITEMS + it);
+    const uint32_t m = seg_pad(threadIdx.x * SEG_ITEMS + it);
     const unsigned long long q = qw(s_x[0][m]);
     float mt[5];
     moment_terms(s_x[0][m], s_x[1][m], s_x[2][m], mt);

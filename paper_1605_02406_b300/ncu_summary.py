@@ -2,6 +2,7 @@
 
     python -m paper_1605_02406_b300.ncu_summary launches LOG.csv      # markdown table
     python -m paper_1605_02406_b300.ncu_summary traffic LOG.csv OUT.json --steps-from LOG
+    python -m paper_1605_02406_b300.ncu_summary kernel RAW.csv ALG_BYTES    # one --set full launch
 
 `launches` reads a `--metrics gpu__time_duration.sum --csv` log (one row per launch) and
 prints, per kernel, its launches, total time and share of the total.  `traffic` reads a
@@ -90,9 +91,64 @@ def traffic(path: str) -> dict:
     return {k: sum(v) / len(v) for k, v in per.items()}
 
 
+# metrics of a `--set full` capture worth reading for this memory- and issue-bound code
+KERNEL_METRICS = [
+    ("gpu__time_duration.sum", "duration"),
+    ("dram__bytes_read.sum", "DRAM read"),
+    ("dram__bytes_write.sum", "DRAM write"),
+    ("gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed", "DRAM throughput % of peak"),
+    ("lts__t_bytes.sum", "L2 bytes"),
+    ("sm__throughput.avg.pct_of_peak_sustained_elapsed", "SM throughput % of peak"),
+    ("smsp__issue_active.avg.pct_of_peak_sustained_active", "issue active %"),
+    ("sm__warps_active.avg.pct_of_peak_sustained_active", "warps active % (occupancy)"),
+    ("launch__registers_per_thread", "registers / thread"),
+    ("launch__block_size", "block size"),
+    ("launch__grid_size", "grid size"),
+    ("smsp__inst_executed.sum", "warp instructions"),
+    ("l1tex__t_sectors_pipe_lsu_mem_global_op_ld.sum", "global load sectors"),
+    ("l1tex__t_requests_pipe_lsu_mem_global_op_ld.sum", "global load requests"),
+    ("l1tex__data_bank_conflicts_pipe_lsu_mem_shared.sum", "shared bank conflicts"),
+]
+
+
+def kernel(path: str, alg_bytes: float) -> str:
+    """Markdown of one launch of a `ncu --set full` report exported with
+    `ncu -i REPORT --page raw --csv`: the metrics above, the top warp stall reasons, and the
+    achieved algorithmic bandwidth (alg_bytes / duration)."""
+    lines = open(path).read().splitlines()
+    start = next(k for k, line in enumerate(lines) if line.startswith('"ID"'))
+    rs = list(csv.reader(io.StringIO("\n".join(lines[start:]))))
+    head, units, row = rs[0], rs[1], rs[2]
+    col = {h: i for i, h in enumerate(head)}
+
+    def val(m):
+        v = row[col[m]].replace(",", "")
+        return float(v) if v else 0.0
+
+    out = [f"Kernel: `{kernel_name(row[col['Kernel Name']])}`", "", "| metric | value | unit |", "|---|---|---|"]
+    for m, name in KERNEL_METRICS:
+        if m in col:
+            out.append(f"| {name} (`{m}`) | {row[col[m]]} | {units[col[m]]} |")
+    stalls = sorted(((val(h), h) for h in head if h.startswith("smsp__average_warps_issue_stalled_")
+                     and h.endswith("_per_issue_active.ratio")), reverse=True)[:6]
+    out += ["", "Top warp stalls (cycles per issued instruction): " + ", ".join(
+        f"{h.replace('smsp__average_warps_issue_stalled_', '').replace('_per_issue_active.ratio', '')} "
+        f"{v:.2f}" for v, h in stalls)]
+    dur = val("gpu__time_duration.sum")
+    unit = units[col["gpu__time_duration.sum"]]
+    dur_s = dur * {"nsecond": 1e-9, "ns": 1e-9, "usecond": 1e-6, "us": 1e-6, "msecond": 1e-3,
+                     "ms": 1e-3}.get(unit, 1e-9)
+    if alg_bytes > 0 and dur_s > 0:
+        out.append(f"Algorithmic bytes {alg_bytes / 1e6:.1f} MB / {dur_s * 1e6:.1f} µs = "
+                   f"{alg_bytes / dur_s / 1e9:.0f} GB/s under the profiler (cold L2, clocks as found).")
+    return "\n".join(out)
+
+
 def main(argv: list) -> None:
     if argv[0] == "launches":
         print(launches(argv[1]))
+    elif argv[0] == "kernel":
+        print(kernel(argv[1], float(argv[2]) if len(argv) > 2 else 0.0))
     elif argv[0] == "traffic":
         kern = traffic(argv[1])
         json.dump({"csrc_hash": csrc_hash(), "source": os.path.basename(argv[1]),

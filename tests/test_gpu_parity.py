@@ -7,13 +7,13 @@ kernel's arithmetic:
 The kernel sums the terms w v, w v^2, w vx vy (Eq. mean_x, var_x, covar_xy; for the lidar
 filter w'/rho_p = w/S_c exactly, so it uses the predicted weights w and divides by the
 fixed-point S_c; with a radar likelihood it sums u v, ... with u = w' (1/rho_p)) in binary32
-over a binary tree of depth <= 11 inside a 2048-particle tile and scales by one rounded
+over a binary tree of depth <= 10 inside a 1024-particle tile and scales by one rounded
 reciprocal; the oracle sums w' v, ... in binary64 from its binary32 w' (one more rounding
 per term).  A lidar cell spread over p tiles adds its p binary32 pieces in tile order (p - 1
 more roundings); a radar cell adds its pieces of the normalised terms (whose |sum| is
 E|v|) in 2^-40 fixed point, one unit per piece.  Each normalised sum is therefore off by at
-most (11 + p + 4) 2^-24 of the sum of |terms| (+ p 2^-40 for radar), i.e. for p <= 100,
-|err(mean)| <= 115 * 2^-24 * E|v| + 1e-10 <= 7e-6 sqrt(E[v^2]).  The tolerances below are
+most (10 + p + 4) 2^-24 of the sum of |terms| (+ p 2^-40 for radar), i.e. for p <= 100,
+|err(mean)| <= 114 * 2^-24 * E|v| + 1e-10 <= 7e-6 sqrt(E[v^2]).  The tolerances below are
 that bound with headroom (the cells of these cases span far fewer tiles):
 mean: 1e-5 (1 + sqrt(E[v^2])); variance and covariance: 1e-5 (1 + E[v^2]).
 """
