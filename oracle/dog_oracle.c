@@ -123,8 +123,9 @@ static real unif_co(uint32_t r) { return (real)(r >> 8) * R(0x1p-24); }
 static real unif_oc(uint32_t r) { return (real)((r >> 8) + 1u) * R(0x1p-24); }
 
 /* ------------------------------------------------------------------------------------
- * Transcendentals.  FP32 mirror: own routines from their textbook series, every product
- * and sum rounded separately.  FP64: libm.
+ * Transcendentals.  FP32 mirror: own routines from their textbook series, each Horner
+ * step one fused multiply-add (fmaf: a single rounding), every other product and sum
+ * rounded separately.  FP64: libm.
  * ------------------------------------------------------------------------------------ */
 #ifdef ORACLE_F32
 static float bits2f(uint32_t b) { float f; memcpy(&f, &b, 4); return f; }
@@ -143,18 +144,16 @@ float oracle_ln_f32(float u) {
   float s = f / t;
   float z = s * s;
   float p = 0x1.745d18p-4f;            /* 1/11 */
-  p = p * z; p = p + 0x1.c71c72p-4f;   /* 1/9 */
-  p = p * z; p = p + 0x1.24924ap-3f;   /* 1/7 */
-  p = p * z; p = p + 0x1.99999ap-3f;   /* 1/5 */
-  p = p * z; p = p + 0x1.555556p-2f;   /* 1/3 */
-  p = p * z; p = p + 1.0f;
+  p = fmaf(p, z, 0x1.c71c72p-4f);      /* 1/9 */
+  p = fmaf(p, z, 0x1.24924ap-3f);      /* 1/7 */
+  p = fmaf(p, z, 0x1.99999ap-3f);      /* 1/5 */
+  p = fmaf(p, z, 0x1.555556p-2f);      /* 1/3 */
+  p = fmaf(p, z, 1.0f);
   float s2 = s + s;
   float lnm = s2 * p;
   float ef = (float)e;
-  float a = ef * 0x1.7f7d1cp-20f;      /* e * ln2_lo */
-  float c = lnm + a;
-  float d = ef * 0x1.62e4p-1f;         /* e * ln2_hi */
-  return d + c;
+  float c = fmaf(ef, 0x1.7f7d1cp-20f, lnm);  /* lnm + e * ln2_lo */
+  return fmaf(ef, 0x1.62e4p-1f, c);          /* + e * ln2_hi */
 }
 
 /* sin and cos of 2 pi u for u = k 2^-24 in [0,1): octant k = floor(8u), t = 8u - k,
@@ -168,17 +167,17 @@ void oracle_sincos2pi_f32(float u, float *sn, float *cs) {
   float th = tt * 0x1.921fb6p-1f; /* pi/4 */
   float z = th * th;
   float ps = 0x1.71de3ap-19f;               /* 1/9! */
-  ps = ps * z; ps = ps + -0x1.a01a02p-13f;  /* -1/7! */
-  ps = ps * z; ps = ps + 0x1.111112p-7f;    /* 1/5! */
-  ps = ps * z; ps = ps + -0x1.555556p-3f;   /* -1/3! */
-  ps = ps * z; ps = ps + 1.0f;
+  ps = fmaf(ps, z, -0x1.a01a02p-13f);       /* -1/7! */
+  ps = fmaf(ps, z, 0x1.111112p-7f);         /* 1/5! */
+  ps = fmaf(ps, z, -0x1.555556p-3f);        /* -1/3! */
+  ps = fmaf(ps, z, 1.0f);
   float S = th * ps;
   float pc = -0x1.27e4fcp-22f;              /* -1/10! */
-  pc = pc * z; pc = pc + 0x1.a01a02p-16f;   /* 1/8! */
-  pc = pc * z; pc = pc + -0x1.6c16c2p-10f;  /* -1/6! */
-  pc = pc * z; pc = pc + 0x1.555556p-5f;    /* 1/4! */
-  pc = pc * z; pc = pc + -0.5f;             /* -1/2! */
-  pc = pc * z; pc = pc + 1.0f;
+  pc = fmaf(pc, z, 0x1.a01a02p-16f);        /* 1/8! */
+  pc = fmaf(pc, z, -0x1.6c16c2p-10f);       /* -1/6! */
+  pc = fmaf(pc, z, 0x1.555556p-5f);         /* 1/4! */
+  pc = fmaf(pc, z, -0.5f);                  /* -1/2! */
+  pc = fmaf(pc, z, 1.0f);
   float Cv = pc;
   switch (k) {
     case 0: *sn = S; *cs = Cv; break;
@@ -197,22 +196,19 @@ void oracle_sincos2pi_f32(float u, float *sn, float *cs) {
  * Below -87 the result is flushed to 0. */
 float oracle_exp_f32(float x) {
   if (!(x > -87.0f)) return 0.0f;
-  float t = x * 0x1.715476p+0f; /* 1/ln2 */
-  t = t + 0.5f;
+  float t = fmaf(x, 0x1.715476p+0f, 0.5f); /* x/ln2 + 1/2 */
   float kf = floorf(t);
   int k = (int)kf;
-  float a = kf * 0x1.62e4p-1f;
-  float r1 = x - a;
-  float b = kf * 0x1.7f7d1cp-20f;
-  float r = r1 - b;
+  float r1 = fmaf(-kf, 0x1.62e4p-1f, x);    /* x - k ln2_hi (k ln2_hi exact) */
+  float r = fmaf(-kf, 0x1.7f7d1cp-20f, r1); /* - k ln2_lo */
   float p = 0x1.a01a02p-13f;            /* 1/7! */
-  p = p * r; p = p + 0x1.6c16c2p-10f;   /* 1/6! */
-  p = p * r; p = p + 0x1.111112p-7f;    /* 1/5! */
-  p = p * r; p = p + 0x1.555556p-5f;    /* 1/4! */
-  p = p * r; p = p + 0x1.555556p-3f;    /* 1/3! */
-  p = p * r; p = p + 0.5f;              /* 1/2! */
-  p = p * r; p = p + 1.0f;
-  p = p * r; p = p + 1.0f;
+  p = fmaf(p, r, 0x1.6c16c2p-10f);      /* 1/6! */
+  p = fmaf(p, r, 0x1.111112p-7f);       /* 1/5! */
+  p = fmaf(p, r, 0x1.555556p-5f);       /* 1/4! */
+  p = fmaf(p, r, 0x1.555556p-3f);       /* 1/3! */
+  p = fmaf(p, r, 0.5f);                 /* 1/2! */
+  p = fmaf(p, r, 1.0f);
+  p = fmaf(p, r, 1.0f);
   float sc = bits2f((uint32_t)(k + 127) << 23);
   return p * sc;
 }

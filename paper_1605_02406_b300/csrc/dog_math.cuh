@@ -1,10 +1,11 @@
 // dog_math.cuh -- device arithmetic shared by the filter kernels.
 //
 // Every floating-point operation on the filter's path is an explicit IEEE binary32
-// round-to-nearest intrinsic (__fadd_rn, __fmul_rn, ...), so no multiply-add is ever
-// contracted and the sequence of roundings is fixed.  The transcendentals the filter needs
-// (ln and sin/cos of 2 pi u for Box-Muller, exp for the radar likelihood) are this file's
-// own series evaluations, not CUDA's math library.
+// round-to-nearest intrinsic (__fadd_rn, __fmul_rn, ...; the code is compiled without
+// contraction), so the sequence of roundings is fixed.  The transcendentals the filter
+// needs (ln and sin/cos of 2 pi u for Box-Muller, exp for the radar likelihood) are this
+// file's own series evaluations, not CUDA's math library; their Horner steps are explicit
+// fused multiply-adds (__fmaf_rn, one rounding each, as C's fmaf).
 #pragma once
 #include <cstdint>
 
@@ -54,15 +55,15 @@ __device__ __forceinline__ float ln_f(float u) {
   const float s = __fdiv_rn(f, __fadd_rn(2.0f, f));
   const float z = __fmul_rn(s, s);
   float p = 0x1.745d18p-4f;
-  p = __fadd_rn(__fmul_rn(p, z), 0x1.c71c72p-4f);
-  p = __fadd_rn(__fmul_rn(p, z), 0x1.24924ap-3f);
-  p = __fadd_rn(__fmul_rn(p, z), 0x1.99999ap-3f);
-  p = __fadd_rn(__fmul_rn(p, z), 0x1.555556p-2f);
-  p = __fadd_rn(__fmul_rn(p, z), 1.0f);
+  p = __fmaf_rn(p, z, 0x1.c71c72p-4f);
+  p = __fmaf_rn(p, z, 0x1.24924ap-3f);
+  p = __fmaf_rn(p, z, 0x1.99999ap-3f);
+  p = __fmaf_rn(p, z, 0x1.555556p-2f);
+  p = __fmaf_rn(p, z, 1.0f);
   const float lnm = __fmul_rn(__fadd_rn(s, s), p);
   const float ef = (float)e;
-  const float lo = __fadd_rn(lnm, __fmul_rn(ef, 0x1.7f7d1cp-20f));
-  return __fadd_rn(__fmul_rn(ef, 0x1.62e4p-1f), lo);
+  const float lo = __fmaf_rn(ef, 0x1.7f7d1cp-20f, lnm);
+  return __fmaf_rn(ef, 0x1.62e4p-1f, lo);  // e ln2_hi is exact: one rounding either way
 }
 
 // sin and cos of 2*pi*u, u = k 2^-24 in [0,1): octant by the exact value 8u, reduced angle
@@ -76,17 +77,17 @@ __device__ __forceinline__ void sincos2pi_f(float u, float &sn, float &cs) {
   const float th = __fmul_rn(tt, 0x1.921fb6p-1f);
   const float z = __fmul_rn(th, th);
   float ps = 0x1.71de3ap-19f;
-  ps = __fadd_rn(__fmul_rn(ps, z), -0x1.a01a02p-13f);
-  ps = __fadd_rn(__fmul_rn(ps, z), 0x1.111112p-7f);
-  ps = __fadd_rn(__fmul_rn(ps, z), -0x1.555556p-3f);
-  ps = __fadd_rn(__fmul_rn(ps, z), 1.0f);
+  ps = __fmaf_rn(ps, z, -0x1.a01a02p-13f);
+  ps = __fmaf_rn(ps, z, 0x1.111112p-7f);
+  ps = __fmaf_rn(ps, z, -0x1.555556p-3f);
+  ps = __fmaf_rn(ps, z, 1.0f);
   const float S = __fmul_rn(th, ps);
   float pc = -0x1.27e4fcp-22f;
-  pc = __fadd_rn(__fmul_rn(pc, z), 0x1.a01a02p-16f);
-  pc = __fadd_rn(__fmul_rn(pc, z), -0x1.6c16c2p-10f);
-  pc = __fadd_rn(__fmul_rn(pc, z), 0x1.555556p-5f);
-  pc = __fadd_rn(__fmul_rn(pc, z), -0.5f);
-  pc = __fadd_rn(__fmul_rn(pc, z), 1.0f);
+  pc = __fmaf_rn(pc, z, 0x1.a01a02p-16f);
+  pc = __fmaf_rn(pc, z, -0x1.6c16c2p-10f);
+  pc = __fmaf_rn(pc, z, 0x1.555556p-5f);
+  pc = __fmaf_rn(pc, z, -0.5f);
+  pc = __fmaf_rn(pc, z, 1.0f);
   const float Cc = pc;
   // octant k: (sin, cos) = k0 (S, C)  k1 (C, S)  k2 (C,-S)  k3 (S,-C)
   //                        k4 (-S,-C) k5 (-C,-S) k6 (-C, S) k7 (-S, C)
@@ -101,17 +102,18 @@ __device__ __forceinline__ void sincos2pi_f(float u, float &sn, float &cs) {
 // series of e^r to r^7, scaled by 2^k through the exponent field; 0 below -87.
 __device__ __forceinline__ float exp_f(float x) {
   if (!(x > -87.0f)) return 0.0f;
-  const float kf = floorf(__fadd_rn(__fmul_rn(x, 0x1.715476p+0f), 0.5f));
+  const float kf = floorf(__fmaf_rn(x, 0x1.715476p+0f, 0.5f));
   const int k = (int)kf;
-  const float r = __fsub_rn(__fsub_rn(x, __fmul_rn(kf, 0x1.62e4p-1f)), __fmul_rn(kf, 0x1.7f7d1cp-20f));
+  // k ln2_hi is exact, so x - k ln2_hi rounds once either way
+  const float r = __fmaf_rn(-kf, 0x1.7f7d1cp-20f, __fmaf_rn(-kf, 0x1.62e4p-1f, x));
   float p = 0x1.a01a02p-13f;
-  p = __fadd_rn(__fmul_rn(p, r), 0x1.6c16c2p-10f);
-  p = __fadd_rn(__fmul_rn(p, r), 0x1.111112p-7f);
-  p = __fadd_rn(__fmul_rn(p, r), 0x1.555556p-5f);
-  p = __fadd_rn(__fmul_rn(p, r), 0x1.555556p-3f);
-  p = __fadd_rn(__fmul_rn(p, r), 0.5f);
-  p = __fadd_rn(__fmul_rn(p, r), 1.0f);
-  p = __fadd_rn(__fmul_rn(p, r), 1.0f);
+  p = __fmaf_rn(p, r, 0x1.6c16c2p-10f);
+  p = __fmaf_rn(p, r, 0x1.111112p-7f);
+  p = __fmaf_rn(p, r, 0x1.555556p-5f);
+  p = __fmaf_rn(p, r, 0x1.555556p-3f);
+  p = __fmaf_rn(p, r, 0.5f);
+  p = __fmaf_rn(p, r, 1.0f);
+  p = __fmaf_rn(p, r, 1.0f);
   return __fmul_rn(p, __uint_as_float((uint32_t)(k + 127) << 23));
 }
 

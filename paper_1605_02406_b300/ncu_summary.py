@@ -3,6 +3,7 @@
     python -m paper_1605_02406_b300.ncu_summary launches LOG.csv      # markdown table
     python -m paper_1605_02406_b300.ncu_summary traffic LOG.csv OUT.json --steps-from LOG
     python -m paper_1605_02406_b300.ncu_summary kernel RAW.csv ALG_BYTES    # one --set full launch
+    python -m paper_1605_02406_b300.ncu_summary first-step LOG.csv    # ncu -s past the autotuner
 
 `launches` reads a `--metrics gpu__time_duration.sum --csv` log (one row per launch) and
 prints, per kernel, its launches, total time and share of the total.  `traffic` reads a
@@ -39,26 +40,49 @@ def rows(path: str) -> list:
 
 
 def kernel_name(full: str) -> str:
-    """'void k_segsum<0>(dog::KParams, ...)' -> 'k_segsum'"""
-    n = full.split("(")[0].replace("void ", "").strip()
+    """'void k_segsum<0>(dog::KParams, ...)' -> 'k_segsum'; '<unnamed>::k_na_hist(...)' ->
+    'k_na_hist'"""
+    n = full.split("(")[0].replace("void ", "").replace("<unnamed>::", "").strip()
     return n.split("<")[0].split("::")[-1]
 
 
-def launches(path: str) -> str:
-    n = collections.Counter()
-    t = collections.defaultdict(float)
+def first_step_after_tuning(names: list) -> int:
+    """Index of the first launch of the frames that follow the sort autotuner's trials (each
+    trial starts with k_na_hist): the next grid take-over or frame tick; 0 without trials."""
+    trials = [i for i, k in enumerate(names) if k == "k_na_hist"]
+    if not trials:
+        return 0
+    return next(i for i in range(trials[-1], len(names)) if names[i] in ("k_take_grid", "k_tick"))
+
+
+def _durations(path: str) -> list:
+    out = []
     for r in rows(path):
         if r["Metric Name"] != "gpu__time_duration.sum":
             continue
-        k = kernel_name(r["Kernel Name"])
         scale = {"ns": 1e-3, "us": 1.0, "usecond": 1.0, "ms": 1e3, "msecond": 1e3}.get(r["Metric Unit"], 1e-3)
+        out.append((kernel_name(r["Kernel Name"]), float(r["Metric Value"].replace(",", "")) * scale))
+    return out
+
+
+def launches(path: str) -> str:
+    """Per kernel: launches, total time, share, over the frames after the autotuner's
+    trials; the launches before them (initial state, first frame, trials) in one line."""
+    d = _durations(path)
+    s = first_step_after_tuning([k for k, _ in d])
+    n = collections.Counter()
+    t = collections.defaultdict(float)
+    for k, us in d[s:]:
         n[k] += 1
-        t[k] += float(r["Metric Value"].replace(",", "")) * scale
+        t[k] += us
     total = sum(t.values())
     out = ["| kernel | launches | total µs | µs / launch | share |", "|---|---|---|---|---|"]
     for k in sorted(t, key=lambda k: -t[k]):
         out.append(f"| {k} | {n[k]} | {t[k]:.1f} | {t[k] / n[k]:.1f} | {100 * t[k] / total:.1f} % |")
     out.append(f"| **all** | {sum(n.values())} | {total:.1f} | | 100 % |")
+    if s:
+        out += ["", f"Not in the table: the {s} launches before those frames (initial state, first "
+                f"frame, sort autotuning trials), {sum(us for _, us in d[:s]):.1f} µs."]
     return "\n".join(out)
 
 
@@ -147,6 +171,8 @@ def kernel(path: str, alg_bytes: float) -> str:
 def main(argv: list) -> None:
     if argv[0] == "launches":
         print(launches(argv[1]))
+    elif argv[0] == "first-step":  # launch index for ncu -s: the frames after the trials
+        print(first_step_after_tuning([k for k, _ in _durations(argv[1])]))
     elif argv[0] == "kernel":
         print(kernel(argv[1], float(argv[2]) if len(argv) > 2 else 0.0))
     elif argv[0] == "traffic":
