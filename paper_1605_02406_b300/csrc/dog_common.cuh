@@ -99,7 +99,7 @@ struct DevBufs {
   // associated slots and the two newborn weights
   uint32_t *bl_first, *bl_gcell, *bl_nA;
   float *bl_wA, *bl_wUA;
-  uint32_t *birth_block_entry;        // [ceil(nu_b / 2048)] entry owning each slot block's first slot
+  uint32_t *birth_block_entry;        // [ceil(nu_b / BIRTH_SLOTS) + 1] entry owning each slot block's first slot
   // scratch of the sort and the tile scans
   uint32_t *hist;                  // [passes][2048] digit histograms
   uint32_t *dcnt;                  // [passes][tiles_sort][radix] digit counts of each sort

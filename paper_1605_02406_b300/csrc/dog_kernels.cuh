@@ -1624,10 +1624,11 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_birth_prep(KParams P, DevBufs B)
   }
 }
 
-// k_birth: a block makes the newborns of BIRTH_SLOTS consecutive slots.  It starts from the
-// entry that owns its first slot, caches the first slots of the following entries in shared
-// memory, and each slot finds its entry (the last one whose first slot is <= the slot) by
-// bisection there.
+// k_birth: a block makes the newborns of BIRTH_SLOTS consecutive slots.  Its slots belong to
+// the entries from the one owning its first slot to the one owning the next block's first
+// slot; it caches those entries' first slots in shared memory (at most BIRTH_CACHE of them),
+// and each slot finds its entry (the last one whose first slot is <= the slot) by bisection
+// there.
 template <bool RADAR>
 __global__ void __launch_bounds__(BIRTH_BLOCK) k_birth(KParams P, DevBufs B) {
   __shared__ uint32_t s_first[BIRTH_CACHE + 1];
@@ -1645,7 +1646,9 @@ __global__ void __launch_bounds__(BIRTH_BLOCK) k_birth(KParams P, DevBufs B) {
   }
   const uint32_t nE = B.ctl->n_birth_cells;
   const uint32_t G0 = B.birth_block_entry[blockIdx.x];
-  const uint32_t ncache = min((uint32_t)BIRTH_CACHE, nE - G0);  // entries G0 .. G0 + ncache - 1
+  const uint32_t Glast = s1 < P.nu_b ? B.birth_block_entry[blockIdx.x + 1] : nE - 1u;
+  // entries G0 .. G0 + ncache - 1, and bl_first[G0 + ncache] (<= the sentinel at nE) after them
+  const uint32_t ncache = min((uint32_t)BIRTH_CACHE, Glast - G0 + 1u);
   for (uint32_t k = threadIdx.x; k <= ncache; k += BIRTH_BLOCK) s_first[k] = __ldg(B.bl_first + G0 + k);
   __syncthreads();
   const uint32_t cached_end = s_first[ncache];  // first slot after the cached entries
