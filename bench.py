@@ -46,9 +46,9 @@ ALG_BYTES = {
     # read key 4 + perm 4 + gathered record 16 (the weight follows from the out-of-grid flag
     # after a resampled frame); write sorted copy 20
     "k_segsum": (44, 0, 0),
-    # lidar: read the cell record 32 (S, tag, 5 moment sums), m_F, z_O, z_F 12; write 9 cell
-    # fields 36 and the 5 velocity moments 20
-    "k_cell": (0, 0, 100),
+    # lidar: read the cell record 32 (S, tag, 5 moment sums), m_F, z_O, z_F 12; write 6 cell
+    # fields 24 (m_O, m_F, rho_b, rho_p, p_occ, mu_UA) and the 5 velocity moments 20
+    "k_cell": (0, 0, 88),
     "k_birth": (0, 20, 0),        # write newborn state 16 + weight 4
     "k_normalise": (12, 4, 0),    # lidar: read key 4, w 4, write w' 4; newborn w 4
     "k_resample": (8, 4, 0),      # read w' 4; write the source index 4; newborn w 4

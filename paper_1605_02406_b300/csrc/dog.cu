@@ -830,7 +830,13 @@ int dog_get_debug(dog_filter *f, int which, void *out, int mem_kind) {
     case DOG_DBG_CELL_END: src = B.cend; bytes = 4 * C; masked = true; break;
     case DOG_DBG_SUM_W: src = &B.csum[0].S; bytes = 8 * C; masked = true; break;
     case DOG_DBG_SUM_GW: src = B.A; bytes = 8 * C; masked = true; break;
-    case DOG_DBG_M_OCC_PRED: src = B.mpred; bytes = 4 * C; break;
+    case DOG_DBG_M_OCC_PRED:  // recomputed from the cell records into scratch
+      k_mpred<<<(unsigned)((C + 255) / 256 < 4096 ? (C + 255) / 256 : 4096), 256, 0, f->st>>>(
+          B.csum, (uint32_t)C, f->frame, B.mpred);
+      DOG_CUDA(cudaGetLastError());
+      src = B.mpred;
+      bytes = 4 * C;
+      break;
     case DOG_DBG_MU_A: src = B.muA; bytes = 4 * C; break;
     case DOG_DBG_MU_UA: src = B.muU; bytes = 4 * C; break;
     case DOG_DBG_W_NORM: src = B.wn; bytes = 4 * nu; break;

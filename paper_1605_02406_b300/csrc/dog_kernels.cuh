@@ -111,6 +111,16 @@ __global__ void k_snapshot(CellSnap src, float *__restrict__ stage, uint32_t C, 
   }
 }
 
+// predicted occupied mass m_pred = min(S, 1) of every cell for the diagnostic read, from
+// the cell records (S and the frame tag) exactly as k_cell computes it; 0 where the cell
+// received no particle this frame
+__global__ void k_mpred(const CellSum *__restrict__ cs, uint32_t C, uint32_t frame, float *__restrict__ out) {
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+    const bool occ = frame != 0u && (cs[c].tag >> 1) == frame;
+    out[c] = occ ? fminf(fx40_to_f(cs[c].S), 1.0f) : 0.0f;
+  }
+}
+
 // ====================================================================================
 // the measurement grid of the next frame: copied into place from the staging buffer or the
 // caller's device arrays and validated in the same pass (m_O, m_F in [0, 1] with sum <= 1;
@@ -1428,12 +1438,12 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
         B.pO[c] = __fadd_rn(mO, __fmul_rn(0.5f, __fsub_rn(__fsub_rn(1.0f, mO), mF)));
         B.muU[c] = (S > 0ull) ? __fdiv_rn(rp, Sf) : 0.0f;
       }
-      B.mpred[c] = mp;
+      // (m_pred itself is not stored: the diagnostic read recomputes it from S, k_mpred)
       B.mO[c] = mO;
       B.mF[c] = mF;
       B.rho_b[c] = rb;
       B.rho_p[c] = rp;
-      B.rinv[c] = rp > 0.0f ? __fdiv_rn(1.0f, rp) : 0.0f;
+      if constexpr (RADAR) B.rinv[c] = rp > 0.0f ? __fdiv_rn(1.0f, rp) : 0.0f;  // radar moments
       if constexpr (RADAR) {
         unsigned long long A = 0ull;
         if (cross) {
@@ -1448,7 +1458,9 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
         }
         B.paeff[c] = pa;
       }
-      B.muA[c] = muA;
+      // mu_A: read by the radar normalisation and the PHD/MIB newborn weights; a lidar DS
+      // filter's stays 0 from the workspace's initialisation
+      if (RADAR || full) B.muA[c] = muA;
       if constexpr (!RADAR) {  // moments of the lidar filter (see k_segsum_lidar)
         float o[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
         if (cross) {  // the cell's pieces in tile order: first, whole tiles, last
