@@ -389,9 +389,8 @@ def main() -> None:
     from paper_1605_02406_b300 import native as N
     from paper_1605_02406_b300.filter import DogFilter
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1605_02406_b300 import replicas
+    world, rank, local = replicas.rank_env()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
@@ -401,7 +400,7 @@ def main() -> None:
             dist.barrier()
 
     cfg = scene.CONFIGS[CFG_ID]
-    params = scene.filter_params(cfg, seed=42 + rank)
+    params = scene.filter_params(cfg, seed=replicas.replica_seed(42, rank))
     n_grids = min(args.steps + args.warmup, 24)
     grids = scene.frame_sequence(cfg, n_grids, 1002)
     dev_grids = [{k: torch.tensor(v, device="cuda") for k, v in g.items()} for g in grids]
@@ -435,10 +434,7 @@ def main() -> None:
     clocks = clk.stop()
     per_step = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     ms_total = ev[0].elapsed_time(ev[-1])
-    t = torch.tensor([ms_total], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = replicas.slowest(ms_total, "cuda")
     value = world * params["nu"] * args.steps / (ms_max * 1e-3)
     launches = args.steps * (f.kernels_per_step() + 1)  # + the grid take-over kernel
     cells_check = f.cells(["m_occ"])["m_occ"]
@@ -478,10 +474,7 @@ def main() -> None:
     N.dog_wait_cells(fe.h)  # the last frame's cells are on the host
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * params["nu"] * ke / float(te.item())
+    e2e_value = replicas.job_throughput(params["nu"] * ke, e2e_s, "cuda")
     fe.close()
 
     # ------------------------------------------------------ per-kernel events (roofline)
