@@ -585,8 +585,7 @@ __global__ void __launch_bounds__(SORT_BLOCK, 2)
   const uint32_t radix = P.radix;
   const size_t big = sort_smem_bytes(radix) - (size_t)3 * radix * 4 - 128;
   uint16_t *s_whist = reinterpret_cast<uint16_t *>(smem);      // [warps][radix]
-  uint32_t *s_keys = reinterpret_cast<uint32_t *>(smem);       // [tile] (after ranking)
-  uint32_t *s_vals = s_keys + SORT_TILE;                       // [tile]
+  uint2 *s_kv = reinterpret_cast<uint2 *>(smem);               // [tile] (key, value), after ranking
   uint32_t *s_cnt = reinterpret_cast<uint32_t *>(smem + big);  // [radix]
   uint32_t *s_excl = s_cnt + radix;
   uint32_t *s_base = s_excl + radix;
@@ -644,19 +643,29 @@ __global__ void __launch_bounds__(SORT_BLOCK, 2)
     rk[k] = pre + __popc(peers & lt);
   }
   __syncthreads();
-  // per digit: exclusive offsets of the warps and the tile's count
+  // per digit: exclusive offsets of the warps and the tile's count.  Two neighbouring
+  // digits' u16 counters are scanned together as one u32 (a digit's count in a tile is at
+  // most 4096, so the low half never carries into the high one)
+  {
+    const uint32_t *wh = reinterpret_cast<const uint32_t *>(s_whist);
+    uint32_t *wh_out = reinterpret_cast<uint32_t *>(s_whist);
+    const uint32_t half = radix >> 1;  // digit pairs per warp row (radix >= 2)
+    for (uint32_t pr = tid; pr < half; pr += SORT_BLOCK) {
+      uint32_t run = 0;
+#pragma unroll 4
+      for (int w = 0; w < SORT_WARPS; ++w) {
+        const uint32_t c = wh[w * half + pr];
+        wh_out[w * half + pr] = run;
+        run += c;
+      }
+      s_cnt[2 * pr] = run & 0xffffu;
+      s_cnt[2 * pr + 1] = run >> 16;
+    }
+  }
 #pragma unroll
   for (int j = 0; j < DPT; ++j) {
     const uint32_t d = tid + j * SORT_BLOCK;
-    if (d >= radix) break;
-    uint32_t run = 0;
-    for (int w = 0; w < SORT_WARPS; ++w) {
-      const uint32_t c = s_whist[w * radix + d];
-      s_whist[w * radix + d] = (uint16_t)run;
-      run += c;
-    }
-    s_cnt[d] = run;
-    s_base[d] = offr[j];
+    if (d < radix) s_base[d] = offr[j];
   }
   __syncthreads();
   block_excl_scan_u32(s_cnt, s_excl, radix, s_misc);
@@ -670,18 +679,15 @@ __global__ void __launch_bounds__(SORT_BLOCK, 2)
   for (uint32_t d = tid; d < radix; d += SORT_BLOCK) s_base[d] -= s_excl[d];
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < SORT_ITEMS; ++k) {
-    s_keys[lpos[k]] = key[k];
-    s_vals[lpos[k]] = val[k];
-  }
+  for (int k = 0; k < SORT_ITEMS; ++k) s_kv[lpos[k]] = make_uint2(key[k], val[k]);
   __syncthreads();
   // scatter: runs of equal digits are contiguous in shared memory and in the output
   for (uint32_t p = tid; p < SORT_TILE; p += SORT_BLOCK) {
-    const uint32_t k = s_keys[p];
-    const uint32_t gp = s_base[(k >> shift) & mask] + p;
+    const uint2 kv = s_kv[p];
+    const uint32_t gp = s_base[(kv.x >> shift) & mask] + p;
     if (gp < P.nu) {
-      keys_out[gp] = k;
-      vals_out[gp] = s_vals[p];
+      keys_out[gp] = kv.x;
+      vals_out[gp] = kv.y;
     }
   }
 }
