@@ -99,11 +99,19 @@ struct CellSnap {
 __global__ void k_snapshot(CellSnap src, float *__restrict__ stage, uint32_t C, uint32_t *err,
                            uint32_t *err_snap) {
   const uint32_t stride = gridDim.x * blockDim.x;
+  // 16-byte accesses when every row starts on a 16-byte boundary (the cell arrays do; C % 4)
+  const bool vec = (C & 3u) == 0u;
 #pragma unroll
   for (int k = 0; k < 10; ++k) {
     if (!src.f[k]) continue;  // uniform
-    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += stride)
-      stage[(size_t)k * C + c] = __ldg(src.f[k] + c);
+    if (vec) {
+      const float4 *in = reinterpret_cast<const float4 *>(src.f[k]);
+      float4 *out = reinterpret_cast<float4 *>(stage + (size_t)k * C);
+      for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C / 4u; c += stride) out[c] = __ldg(in + c);
+    } else {
+      for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += stride)
+        stage[(size_t)k * C + c] = __ldg(src.f[k] + c);
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *err_snap = *err;
@@ -136,6 +144,25 @@ enum : int { GRID_LIDAR = 0, GRID_RADAR = 1, GRID_BERNOULLI = 2 };
 __global__ void k_take_grid(KParams P, DevBufs B, GridSrc src, int kind) {
   const uint32_t stride = gridDim.x * blockDim.x;
   bool bad = false;
+  // lidar grids on 16-byte boundaries (the staging buffer always; a caller's device arrays
+  // usually): four cells per thread and access
+  bool vec = kind == GRID_LIDAR && (P.C & 3u) == 0u;
+  for (int k = 0; k < 2; ++k) vec = vec && (reinterpret_cast<uintptr_t>(src.f[k]) & 15u) == 0u;
+  if (vec) {
+    const float4 *o4 = reinterpret_cast<const float4 *>(src.f[0]);
+    const float4 *f4 = reinterpret_cast<const float4 *>(src.f[1]);
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < P.C / 4u; q += stride) {
+      const float4 a = __ldg(o4 + q), b = __ldg(f4 + q);
+      reinterpret_cast<float4 *>(B.zO)[q] = a;
+      reinterpret_cast<float4 *>(B.zF)[q] = b;
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        bad |= !(av[j] >= 0.0f && av[j] <= 1.0f && bv[j] >= 0.0f && bv[j] <= 1.0f && av[j] + bv[j] <= 1.000001f);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&B.ctl->err, ERR_INPUT);
+    return;
+  }
   for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < P.C; c += stride) {
     const float a = __ldg(src.f[0] + c), b = __ldg(src.f[1] + c);
     B.zO[c] = a;
