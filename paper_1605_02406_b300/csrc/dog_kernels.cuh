@@ -462,31 +462,41 @@ __global__ void __launch_bounds__(COUNT_BLOCK) k_sort_count(KParams P, DevBufs B
   const uint32_t t0 = blockIdx.x * ct;
   const uint32_t base = t0 * SORT_TILE;
   const uint32_t end = min(base + ct * SORT_TILE, P.nu);
-  // four consecutive keys per thread and step (the same tile: SORT_TILE % 4 == 0); equal
-  // neighbouring digits are added together
-  for (uint32_t i = base + 4 * threadIdx.x; i < end; i += 4 * COUNT_BLOCK) {
-    uint32_t k4[4];
-    if (i + 4 <= end) {
-      const uint4 v = __ldg(reinterpret_cast<const uint4 *>(keys + i));
-      k4[0] = v.x; k4[1] = v.y; k4[2] = v.z; k4[3] = v.w;
-    } else {
+  // four consecutive keys per thread and access (the same tile: SORT_TILE % 4 == 0), four
+  // such accesses loaded before any is counted; equal neighbouring digits are added together
+  constexpr int G = 4;
+  for (uint32_t i0 = base + 4 * threadIdx.x; i0 < end; i0 += G * 4 * COUNT_BLOCK) {
+    uint32_t k4[G][4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) k4[j] = i + j < end ? __ldg(keys + i + j) : 0xffffffffu;
-    }
-    uint32_t *cnt = sh_cnt + ((i - base) / SORT_TILE) * radix;
-    uint32_t cur = 0xffffffffu, run = 0u;
+    for (int g = 0; g < G; ++g) {
+      const uint32_t i = i0 + g * 4 * COUNT_BLOCK;
+      if (i + 4 <= end) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(keys + i));
+        k4[g][0] = v.x; k4[g][1] = v.y; k4[g][2] = v.z; k4[g][3] = v.w;
+      } else {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (k4[j] == 0xffffffffu) continue;  // past the end
-      const uint32_t d = (k4[j] >> shift) & mask;
-      if (d != cur) {
-        if (run) atomicAdd(cnt + cur, run);
-        cur = d;
-        run = 0u;
+        for (int j = 0; j < 4; ++j) k4[g][j] = i + j < end ? __ldg(keys + i + j) : 0xffffffffu;
       }
-      ++run;
     }
-    if (run) atomicAdd(cnt + cur, run);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const uint32_t i = i0 + g * 4 * COUNT_BLOCK;
+      if (i >= end) break;
+      uint32_t *cnt = sh_cnt + ((i - base) / SORT_TILE) * radix;
+      uint32_t cur = 0xffffffffu, run = 0u;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (k4[g][j] == 0xffffffffu) continue;  // past the end
+        const uint32_t d = (k4[g][j] >> shift) & mask;
+        if (d != cur) {
+          if (run) atomicAdd(cnt + cur, run);
+          cur = d;
+          run = 0u;
+        }
+        ++run;
+      }
+      if (run) atomicAdd(cnt + cur, run);
+    }
   }
   __syncthreads();
   uint32_t *col = B.dcnt + (size_t)pass * radix * P.tiles_sort;
