@@ -177,16 +177,23 @@ def run_reference(args) -> None:
     }), flush=True)
 
 
-def batched_latency(frames: int, warmup: int, dt: float = 0.1) -> dict:
+def batched_latency(frames: int, warmup: int, dt: float = 0.1, rank: int = 0, world: int = 1) -> dict:
     """p50/p99 GPU time of one frame of the 64-filter batched workload (uneven grids and
-    particle counts), stepped by a plain loop of dog_step calls vs one dog_batch_step."""
+    particle counts), stepped by a plain loop of dog_step calls vs one dog_batch_step.
+    Under several ranks each rank steps the filters placed on it by their HBM need; the
+    times are the slowest rank's, the throughput all filters' particles per that time."""
     import torch
 
+    from paper_1605_02406_b300 import native as N
+    from paper_1605_02406_b300 import replicas
     from paper_1605_02406_b300.filter import DogBatch, DogFilter
-    cfgs = scene.batched_configs(64)
+    cfgs_all = scene.batched_configs(64)
+    need = [N.dog_workspace_bytes(N.make_params(scene.filter_params(c))) for c in cfgs_all]
+    where = replicas.place_by_budget(need, world, 100e9)
+    mine = [(k, c) for k, (c, r) in enumerate(zip(cfgs_all, where)) if r == rank]
     shared = torch.cuda.Stream()
     filters = []
-    for k, c in enumerate(cfgs):
+    for k, c in mine:
         f = DogFilter(scene.filter_params(c, seed=100 + k), stream=shared)
         g = scene.frame_sequence(c, 1, 2000 + k)[0]
         f.set_measurement_grid(**{kk: torch.tensor(v, device="cuda") for kk, v in g.items()})
@@ -196,7 +203,6 @@ def batched_latency(frames: int, warmup: int, dt: float = 0.1) -> dict:
     for f in filters:
         f.step(dt)
         f.autotune()
-    batch = DogBatch(filters)
     dts = [dt] * len(filters)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * frames)]
 
@@ -215,18 +221,23 @@ def batched_latency(frames: int, warmup: int, dt: float = 0.1) -> dict:
         for f in filters:
             f.step(dt)
 
-    t_plain = run(plain)
-    t_batch = run(lambda: batch.step(dts))
-    nu_total = sum(int(c["nu"]) for c in cfgs)
-    batch.close()
+    t_plain = t_batch = [0.0]  # a rank without filters still joins the reductions
+    if filters:
+        batch = DogBatch(filters)
+        t_plain = run(plain)
+        t_batch = run(lambda: batch.step(dts))
+        batch.close()
+    nu_total = sum(int(c["nu"]) for c in cfgs_all)
     for f in filters:
         f.close()
-    return {"workload": "batched: 64 filters, sides 256-1024 at 0.1 m, 2^18-2^22 particles each "
-                        f"({nu_total:,} in total)",
-            "frames": frames,
-            "plain_p50": float(np.percentile(t_plain, 50)), "plain_p99": float(np.percentile(t_plain, 99)),
-            "batched_p50": float(np.percentile(t_batch, 50)), "batched_p99": float(np.percentile(t_batch, 99)),
-            "batched_particle_updates_per_s": nu_total / (float(np.median(t_batch)) * 1e-3)}
+    pct = {k: replicas.slowest(float(np.percentile(t, q)), "cuda")
+           for k, t, q in (("plain_p50", t_plain, 50), ("plain_p99", t_plain, 99),
+                           ("batched_p50", t_batch, 50), ("batched_p99", t_batch, 99))}
+    med = replicas.slowest(float(np.median(t_batch)), "cuda")
+    return dict({"workload": "batched: 64 filters, sides 256-1024 at 0.1 m, 2^18-2^22 particles each "
+                             f"({nu_total:,} in total)" + (f", placed on {world} GPUs by HBM need" if world > 1 else ""),
+                 "frames": frames}, **pct,
+                batched_particle_updates_per_s=nu_total / (med * 1e-3))
 
 
 def evaluation_time(reps: int = 50) -> dict:
@@ -510,23 +521,35 @@ def main() -> None:
             traffic = tj["kernels"][dom]
     achieved = kern_gbs[dom]
 
+    # workloads of independent filters: split over the ranks by HBM need, combined here
+    batched = {"workload": None}
+    if not args.no_batched:
+        batched = batched_latency(frames=min(args.steps, 50), warmup=args.warmup, rank=rank, world=world)
+    serving = None
+    if not args.no_serving:
+        from paper_1605_02406_b300 import serve
+        serving = serve.run(seconds=3.0, rank=rank, world=world)
+        if world > 1:
+            last = replicas.slowest(serving["last_completion_s"], "cuda")
+            updates = replicas.total(serving["updates"], "cuda")
+            serving.update(
+                streams_admitted=int(replicas.total(serving["streams_admitted"], "cuda")),
+                workspace_gb=replicas.total(serving["workspace_gb"], "cuda"),
+                requests=int(replicas.total(serving["requests"], "cuda")),
+                offered_particle_updates_per_s=replicas.total(serving["offered_particle_updates_per_s"], "cuda"),
+                served_particle_updates_per_s=updates / last,
+                latency_ms={k: replicas.slowest(v, "cuda") for k, v in serving["latency_ms"].items()},
+                workload=serving["workload"] + f" per GPU, {world} GPUs (slowest rank's latencies)")
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
     evaluation = None if args.no_evaluation else evaluation_time()
-    serving = None
-    if not args.no_serving:
-        from paper_1605_02406_b300 import serve
-        serving = serve.run(seconds=3.0)
     fusion = None
     if not args.no_fusion:
         fusion = fusion_rate(steps=min(args.steps, 100), warmup=args.warmup)
     ego = None if args.no_ego else ego_rate(steps=min(args.steps, 200), warmup=args.warmup)
     phdmib = None if args.no_phdmib else phdmib_rate(steps=min(args.steps, 200), warmup=args.warmup)
-    batched = {"workload": None}
-    if not args.no_batched:
-        batched = batched_latency(frames=min(args.steps, 50), warmup=args.warmup)
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_oracle_rate(scene.filter_params(cfg), grids[:8])

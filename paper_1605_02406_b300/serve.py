@@ -22,32 +22,33 @@ import numpy as np
 import torch
 
 from . import native as N
-from . import scene
+from . import replicas, scene
 from .filter import DogFilter
 
 
-def admit(cfgs: list, budget_bytes: float) -> tuple:
-    """Streams admitted in order while their workspaces fit the budget."""
-    used, admitted, rejected = 0, [], 0
-    for c in cfgs:
-        p = scene.filter_params(c)
-        need = N.dog_workspace_bytes(N.make_params(p)) + 8 * c["width"] * c["height"]  # + grid
-        if used + need <= budget_bytes:
-            used += need
-            admitted.append(c)
-        else:
-            rejected += 1
-    return admitted, rejected, used
+def admit(cfgs: list, budget_bytes: float, rank: int = 0, world: int = 1) -> tuple:
+    """Streams placed on this rank by their workspaces against a budget per rank (one rank:
+    admitted in order while they fit); also the number rejected on every rank and the bytes
+    used on this one."""
+    need = [N.dog_workspace_bytes(N.make_params(scene.filter_params(c))) + 8 * c["width"] * c["height"]
+            for c in cfgs]  # + the grid
+    where = replicas.place_by_budget(need, world, budget_bytes)
+    admitted = [dict(c, index=k) for k, (c, r) in enumerate(zip(cfgs, where)) if r == rank]
+    used = sum(b for b, r in zip(need, where) if r == rank)
+    return admitted, sum(1 for r in where if r < 0), used
 
 
 def run(n_streams: int = 256, seconds: float = 3.0, budget_gb: float = 120.0, seed: int = 7,
-        warm_frames: int = 2) -> dict:
+        warm_frames: int = 2, rank: int = 0, world: int = 1) -> dict:
+    """One rank's share of the serving workload (all of it on one rank); budget_gb is per
+    rank.  Besides the rates and latency percentiles, returns the raw counts (updates, the
+    last completion) from which several ranks' results combine."""
     cfgs = scene.serving_stream_configs(n_streams)
-    admitted, rejected, used = admit(cfgs, budget_gb * 1e9)
-    rng = np.random.default_rng(seed)
+    admitted, rejected, used = admit(cfgs, budget_gb * 1e9, rank, world)
+    rng = np.random.default_rng(seed + rank)
     filters, grids = [], []
-    for k, c in enumerate(admitted):
-        f = DogFilter(scene.filter_params(c, seed=500 + k))
+    for c in admitted:
+        f = DogFilter(scene.filter_params(c, seed=500 + c["index"]))
         g = scene.random_measurement_grid(c["width"], c["height"], rng)
         dg = {kk: torch.tensor(v, device="cuda") for kk, v in g.items()}
         f.set_measurement_grid(**dg)
@@ -98,6 +99,7 @@ def run(n_streams: int = 256, seconds: float = 3.0, budget_gb: float = 120.0, se
         "workspace_gb": used / 1e9, "seconds": seconds, "requests": len(done),
         "offered_particle_updates_per_s": sum(float(c["nu"]) * c["rate_hz"] for c in admitted),
         "served_particle_updates_per_s": updates / last,
+        "updates": updates, "last_completion_s": last,
         "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
                        "max": float(lat.max() * 1e3)},
         "wall_s": wall,
