@@ -1997,6 +1997,18 @@ __device__ __forceinline__ uint32_t first_above(const unsigned long long *Q, uin
   return lo;
 }
 
+// the same over a whole tile, Q[0 .. NORM_TILE) (entries past the tile's last source repeat
+// its Q, and some Q of the tile exceeds th): the count of entries <= th, by halving steps
+// of fixed number without a loop branch
+__device__ __forceinline__ uint32_t first_above_tile(const unsigned long long *Q, unsigned long long th) {
+  static_assert((NORM_TILE & (NORM_TILE - 1)) == 0, "power-of-two tile");
+  uint32_t y = 0u;
+#pragma unroll
+  for (uint32_t half = NORM_TILE / 2; half >= 1u; half >>= 1)
+    if (Q[y + half - 1u] <= th) y += half;
+  return y;
+}
+
 __global__ void __launch_bounds__(RES_BLOCK, 2) k_resample(KParams P, DevBufs B) {
   __shared__ unsigned long long s_Q[NORM_TILE];  // inclusive CDF at each source of the tile
   __shared__ unsigned long long s_wsum[RES_BLOCK / 32];
@@ -2064,7 +2076,7 @@ __global__ void __launch_bounds__(RES_BLOCK, 2) k_resample(KParams P, DevBufs B)
   for (uint32_t x0 = o_lo + RES_RUN * threadIdx.x; x0 < o_hi; x0 += RES_RUN * RES_BLOCK) {
     uint32_t rem;
     unsigned long long th = theta_at(T, x0, &rem);
-    uint32_t y = first_above(s_Q, 0u, nS - 1u, th);
+    uint32_t y = min(first_above_tile(s_Q, th), nS - 1u);
     B.Bsrc[x0] = base + y;
 #pragma unroll
     for (int k = 1; k < RES_RUN; ++k) {
