@@ -641,8 +641,9 @@ __global__ void __launch_bounds__(SORT_BLOCK, 2)
     const uint32_t d = tid + j * SORT_BLOCK;
     offr[j] = d < radix ? __ldg(off + (size_t)d * P.tiles_sort) : 0u;
   }
-  for (uint32_t k = tid; k < SORT_WARPS * radix / 2; k += SORT_BLOCK)
-    reinterpret_cast<uint32_t *>(s_whist)[k] = 0u;
+  // warp counters cleared with 16-byte stores (SORT_WARPS * radix * 2 bytes, a multiple of 16)
+  for (uint32_t k = tid; k < SORT_WARPS * radix / 8; k += SORT_BLOCK)
+    reinterpret_cast<uint4 *>(s_whist)[k] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
 
   // load: warp w covers positions [w*256, w*256+256) of the tile, item k at k*32 + lane
