@@ -385,7 +385,7 @@ def main() -> None:
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-filter latency run")
     ap.add_argument("--no-fusion", action="store_true", help="skip the lidar + radar workload")
     ap.add_argument("--no-evaluation", action="store_true", help="skip timing the evaluation calls")
-    ap.add_argument("--no-serving", action="store_true", help="skip the 3 s serving-loop run")
+    ap.add_argument("--no-serving", action="store_true", help="skip the two 3 s serving-loop runs")
     ap.add_argument("--no-ego", action="store_true", help="skip the ego-motion workload")
     ap.add_argument("--no-phdmib", action="store_true", help="skip the PHD/MIB filter workload")
     args = ap.parse_args()
@@ -544,6 +544,13 @@ def main() -> None:
         if world > 1:
             dist.destroy_process_group()
         return
+    # streams that come and go, admitted as others leave (rank 0 alone: a per-GPU figure)
+    sessions = None
+    if not args.no_serving:
+        from paper_1605_02406_b300 import serve
+        sessions = serve.run_sessions(seconds=3.0)
+        if world > 1:
+            sessions["workload"] += " (rank 0's GPU only)"
     evaluation = None if args.no_evaluation else evaluation_time()
     fusion = None
     if not args.no_fusion:
@@ -584,6 +591,7 @@ def main() -> None:
         "phdmib": phdmib,
         "evaluation": evaluation,
         "serving": serving,
+        "serving_sessions": sessions,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

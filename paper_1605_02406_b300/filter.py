@@ -34,8 +34,9 @@ class DogFilter:
 
     def close(self):
         if getattr(self, "h", None):
-            N.dog_destroy(self.h)
+            N.dog_destroy(self.h)  # waits for the filter's stream first
             self.h = None
+            self._ws = None  # the workspace goes back to torch's allocator
 
     def __del__(self):
         try:

@@ -10,12 +10,21 @@ overlap on the GPU, and stamps its completion with a CUDA event.  Latency = comp
 arrival on the GPU's clock (the arrivals are mapped onto it through an event recorded at
 the start).
 
+`run_sessions` is the same loop with streams that come and go: each connects at some time,
+waits in arrival order until a slot and its HBM need are free (`Admission`), is served for
+a session of random length, and on leaving returns its workspace, so streams that could
+not fit at first are admitted as others depart.
+
     python -m paper_1605_02406_b300.serve --seconds 3
+    python -m paper_1605_02406_b300.serve --sessions --seconds 3 --budget-gb 40
 """
 from __future__ import annotations
 
 import argparse
+import collections
 import json
+import queue
+import threading
 import time
 
 import numpy as np
@@ -26,12 +35,50 @@ from . import replicas, scene
 from .filter import DogFilter
 
 
+class Admission:
+    """Admission of streams by HBM need and free slots, in arrival order: a stream waits
+    until every stream that arrived before it is admitted and its own need fits the budget
+    left by the streams still active (no overtaking, so no stream waits forever behind a
+    flow of smaller ones).  Pure host bookkeeping in bytes."""
+
+    def __init__(self, budget_bytes: float, slots: int):
+        self.budget, self.slots = float(budget_bytes), int(slots)
+        self.used = 0.0
+        self.active = {}  # stream -> bytes
+        self.queue = collections.deque()
+
+    def request(self, k: int, need: float) -> None:
+        if need > self.budget:
+            raise ValueError(f"stream {k} needs {need:.0f} bytes, more than the whole budget")
+        self.queue.append((k, float(need)))
+
+    def admit(self) -> list:
+        """Streams admitted now, in arrival order."""
+        out = []
+        while (self.queue and len(self.active) < self.slots
+               and self.used + self.queue[0][1] <= self.budget):
+            k, need = self.queue.popleft()
+            self.active[k] = need
+            self.used += need
+            out.append(k)
+        return out
+
+    def release(self, k: int) -> None:
+        self.used -= self.active.pop(k)
+        if not self.active:
+            self.used = 0.0  # no rounding residue once nothing is active
+
+
+def stream_need(c: dict) -> int:
+    """Device bytes of one stream: its filter workspace and its measurement grid."""
+    return N.dog_workspace_bytes(N.make_params(scene.filter_params(c))) + 8 * c["width"] * c["height"]
+
+
 def admit(cfgs: list, budget_bytes: float, rank: int = 0, world: int = 1) -> tuple:
     """Streams placed on this rank by their workspaces against a budget per rank (one rank:
     admitted in order while they fit); also the number rejected on every rank and the bytes
     used on this one."""
-    need = [N.dog_workspace_bytes(N.make_params(scene.filter_params(c))) + 8 * c["width"] * c["height"]
-            for c in cfgs]  # + the grid
+    need = [stream_need(c) for c in cfgs]
     where = replicas.place_by_budget(need, world, budget_bytes)
     admitted = [dict(c, index=k) for k, (c, r) in enumerate(zip(cfgs, where)) if r == rank]
     used = sum(b for b, r in zip(need, where) if r == rank)
@@ -106,13 +153,152 @@ def run(n_streams: int = 256, seconds: float = 3.0, budget_gb: float = 120.0, se
     }
 
 
+def run_sessions(n_streams: int = 256, seconds: float = 3.0, budget_gb: float = 40.0, slots: int = 64,
+                 mean_session_s: float = 1.0, connect_s: float = 1.5, seed: int = 7, cfgs: list = None,
+                 keep: bool = False) -> dict:
+    """Streams that come and go.  Stream k connects at a uniform time in [0, connect_s) and
+    wants a session of Exp(mean_session_s) seconds; admitted (Admission: arrival order,
+    budget_gb and `slots` streams at once), it gets a filter and a device grid, and its
+    first request (which also captures the filter's CUDA graph) is issued at once; further
+    requests (one frame each) follow by a Poisson process at its rate until its session ends
+    (at `seconds` at the latest).  Once its session is over and its last frame has finished
+    on the GPU, its filter is destroyed and its workspace freed, and waiting streams are
+    admitted in its place.  Opening and closing filters run on a worker thread (the
+    library's graph capture is thread-local), so the request loop never waits for them.
+    With keep=True the result lists every served stream's frame count, grid and final
+    cells, to be checked against the same stream run alone."""
+    cfgs = scene.serving_stream_configs(n_streams) if cfgs is None else cfgs
+    n = len(cfgs)
+    rng = np.random.default_rng(seed)
+    connect = np.sort(rng.uniform(0.0, connect_s, n))
+    life = rng.exponential(mean_session_s, n)
+    need = [stream_need(c) for c in cfgs]
+    adm = Admission(budget_gb * 1e9, slots)
+    todo, opened, closed = queue.Queue(), queue.Queue(), queue.Queue()
+    # each stream's measurement grid, as its sensor would deliver it (made before the run)
+    grids = [scene.random_measurement_grid(c["width"], c["height"], rng) for c in cfgs]
+
+    def worker():
+        while True:
+            job = todo.get()
+            if job is None:
+                return
+            kind, k, obj = job
+            if kind == "close":
+                obj.close()
+                del obj
+                closed.put(k)
+                continue
+            ta = time.perf_counter()
+            c = cfgs[k]
+            f = DogFilter(scene.filter_params(c, seed=500 + k))
+            g = grids[k]
+            f.set_measurement_grid(**{kk: torch.tensor(v, device="cuda") for kk, v in g.items()})
+            f.step(0.1)
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(f.stream)
+            opened.put((k, f, g, ev, obj, time.perf_counter() - ta))
+
+    th = threading.Thread(target=worker, daemon=True)
+    live, served, waits, done, first = {}, {}, [], [], []
+    pending = 0  # admitted, not yet opened or not yet closed
+    open_s, n_open, max_live = 0.0, 0, 0
+    start = torch.cuda.Event(enable_timing=True)
+    start.record()
+    torch.cuda.synchronize()
+    th.start()
+    t0 = time.perf_counter()
+    ci = 0
+    while True:
+        now = time.perf_counter() - t0
+        while ci < n and connect[ci] <= now:
+            adm.request(ci, need[ci])
+            ci += 1
+        while not closed.empty():
+            adm.release(closed.get())
+            pending -= 1
+        if now < seconds:
+            for k in adm.admit():
+                waits.append(now - connect[k])
+                todo.put(("open", k, now))
+                pending += 1
+        while not opened.empty():  # first frame issued by the worker at admission time
+            k, f, g, ev, t_req, dt = opened.get()
+            pending -= 1
+            open_s += dt
+            n_open += 1
+            nu = int(cfgs[k]["nu"])
+            first.append((t_req, ev))
+            done.append((t_req, nu, ev))
+            live[k] = dict(f=f, grid_host=g if keep else None, t_end=min(t_req + life[k], seconds),
+                           next=time.perf_counter() - t0 + rng.exponential(1.0 / cfgs[k]["rate_hz"]),
+                           last=ev, frames=1, rate=cfgs[k]["rate_hz"], nu=nu)
+        max_live = max(max_live, len(live))
+        issued = False
+        for k in list(live):
+            s = live[k]
+            now = time.perf_counter() - t0
+            while s["next"] <= now and s["next"] < s["t_end"]:  # requests due
+                s["f"].step(0.1)
+                ev = torch.cuda.Event(enable_timing=True)
+                ev.record(s["f"].stream)
+                done.append((s["next"], s["nu"], ev))
+                s["last"] = ev
+                s["frames"] += 1
+                s["next"] += rng.exponential(1.0 / s["rate"])
+                issued = True
+            if now >= s["t_end"] and s["last"].query():  # session over, last frame finished
+                served[k] = dict(frames=s["frames"])
+                if keep:
+                    served[k].update(grid=s["grid_host"], cells=s["f"].cells(["m_occ", "m_free", "p_occ"]))
+                todo.put(("close", k, s["f"]))
+                pending += 1
+                del live[k]
+        if now >= seconds and not live and pending == 0:
+            break
+        if not issued:
+            time.sleep(0.0002)
+    todo.put(None)
+    th.join()
+    torch.cuda.synchronize()
+    t_first = {id(ev) for _, ev in first}
+    lat = np.array([start.elapsed_time(ev) * 1e-3 - a for a, _, ev in done if id(ev) not in t_first])
+    lat1 = np.array([start.elapsed_time(ev) * 1e-3 - a for a, ev in first])
+    updates = sum(nu for _, nu, _ in done)
+    last = max(start.elapsed_time(ev) for _, _, ev in done) * 1e-3
+    w = np.array(waits)
+    out = {
+        "workload": f"serving sessions: {n} streams connecting over {connect_s:g} s, sessions "
+                    f"Exp({mean_session_s:g} s), {budget_gb:.0f} GB and {slots} slots",
+        "streams_served": len(served), "streams_never_admitted": n - len(served),
+        "most_streams_at_once": max_live, "requests": len(done),
+        "admitted_after_waiting": int((w > 0.01).sum()),
+        "wait_s": {"p50": float(np.percentile(w, 50)), "max": float(w.max())},
+        "open_ms_mean": open_s / max(n_open, 1) * 1e3,
+        # admission to the end of the stream's first frame (filter set-up on the worker,
+        # queued behind the other streams admitted at the same time, and graph capture)
+        "first_frame_ms": {"p50": float(np.percentile(lat1, 50) * 1e3), "p99": float(np.percentile(lat1, 99) * 1e3)},
+        "served_particle_updates_per_s": updates / last, "updates": updates,
+        # the requests after each stream's first frame
+        "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
+                       "max": float(lat.max() * 1e3)},
+    }
+    if keep:
+        out["served"] = served
+    return out
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--streams", type=int, default=256)
     ap.add_argument("--seconds", type=float, default=3.0)
-    ap.add_argument("--budget-gb", type=float, default=120.0)
+    ap.add_argument("--budget-gb", type=float, default=None)
+    ap.add_argument("--sessions", action="store_true", help="streams that come and go")
     args = ap.parse_args()
-    print(json.dumps(run(args.streams, args.seconds, args.budget_gb)))
+    if args.sessions:
+        print(json.dumps(run_sessions(args.streams, args.seconds, args.budget_gb or 40.0)))
+    else:
+        print(json.dumps(run(args.streams, args.seconds, args.budget_gb or 120.0)))
 
 
 if __name__ == "__main__":

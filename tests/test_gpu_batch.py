@@ -200,3 +200,37 @@ def test_batch_with_phdmib_filter_equals_single_filters():
                     va, vb = va.astype(np.float32).view(np.uint32), vb.astype(np.float32).view(np.uint32)
                 assert np.array_equal(va, vb), f"frame {frame}, filter {i}: {k} differs"
     batch.close()
+
+
+def test_sessions_admit_waiting_streams_and_match_streams_alone():
+    """Streams that come and go (serve.run_sessions): with room for three at once, the later
+    streams wait and are admitted as earlier ones leave; every served stream's cells equal,
+    bit for bit, the same stream stepped alone for as many frames."""
+    from paper_1605_02406_b300 import serve
+    from paper_1605_02406_b300.filter import DogFilter
+
+    base = scene.serving_stream_configs(12)
+    cfgs = [dict(c, width=64 if k % 2 else 96, height=64, nu=16 * (64 if k % 2 else 96) * 64)
+            for k, c in enumerate(base)]
+    for c in cfgs:
+        c["nu_b"] = c["nu"] // 4
+    room = 3 * max(serve.stream_need(c) for c in cfgs)
+    r = serve.run_sessions(seconds=1.0, budget_gb=room / 1e9, slots=3, mean_session_s=0.2,
+                           connect_s=0.3, cfgs=cfgs, keep=True)
+    assert r["most_streams_at_once"] <= 3
+    assert r["streams_served"] + r["streams_never_admitted"] == len(cfgs)
+    assert r["admitted_after_waiting"] >= 1 and r["streams_served"] >= 4
+    checked = 0
+    for k, s in r["served"].items():
+        if s["frames"] == 0:
+            continue
+        g = DogFilter(scene.filter_params(cfgs[k], seed=500 + k))
+        g.set_measurement_grid(**s["grid"])
+        for _ in range(s["frames"]):
+            g.step(0.1)
+        alone = g.cells(["m_occ", "m_free", "p_occ"])
+        g.close()
+        for f in ("m_occ", "m_free", "p_occ"):
+            assert np.array_equal(alone[f], s["cells"][f]), (k, f)
+        checked += 1
+    assert checked >= 4
