@@ -37,6 +37,7 @@ class DogFilter:
             N.dog_destroy(self.h)  # waits for the filter's stream first
             self.h = None
             self._ws = None  # the workspace goes back to torch's allocator
+            self._keep = []  # and so do the grid buffers recorded on the filter's stream
 
     def __del__(self):
         try:

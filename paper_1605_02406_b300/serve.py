@@ -30,9 +30,16 @@ import time
 import numpy as np
 import torch
 
+from cuda.bindings import runtime as cudart
+
 from . import native as N
 from . import replicas, scene
 from .filter import DogFilter
+
+
+def _check(err) -> None:
+    if err != cudart.cudaError_t.cudaSuccess:
+        raise RuntimeError(f"CUDA runtime: {err}")
 
 
 class Admission:
@@ -164,7 +171,10 @@ def run_sessions(n_streams: int = 256, seconds: float = 3.0, budget_gb: float = 
     (at `seconds` at the latest).  Once its session is over and its last frame has finished
     on the GPU, its filter is destroyed and its workspace freed, and waiting streams are
     admitted in its place.  Opening and closing filters run on a worker thread (the
-    library's graph capture is thread-local), so the request loop never waits for them.
+    library's graph capture is thread-local), so the request loop never waits for them;
+    each filter gets a CUDA stream of its own for its lifetime (torch's pooled streams are
+    shared between filters, and no other filter's work may enter a stream while the
+    worker captures a new filter's graph on it).
     With keep=True the result lists every served stream's frame count, grid and final
     cells, to be checked against the same stream run alone."""
     cfgs = scene.serving_stream_configs(n_streams) if cfgs is None else cfgs
@@ -185,19 +195,23 @@ def run_sessions(n_streams: int = 256, seconds: float = 3.0, budget_gb: float = 
                 return
             kind, k, obj = job
             if kind == "close":
-                obj.close()
-                del obj
+                f, raw = obj
+                f.close()  # waits for the stream, frees workspace and grid buffers
+                _check(cudart.cudaStreamDestroy(raw)[0])
+                del f, obj, job
                 closed.put(k)
                 continue
             ta = time.perf_counter()
             c = cfgs[k]
-            f = DogFilter(scene.filter_params(c, seed=500 + k))
+            err, raw = cudart.cudaStreamCreateWithFlags(cudart.cudaStreamNonBlocking)
+            _check(err)
+            f = DogFilter(scene.filter_params(c, seed=500 + k), stream=torch.cuda.ExternalStream(int(raw)))
             g = grids[k]
             f.set_measurement_grid(**{kk: torch.tensor(v, device="cuda") for kk, v in g.items()})
             f.step(0.1)
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(f.stream)
-            opened.put((k, f, g, ev, obj, time.perf_counter() - ta))
+            opened.put((k, f, raw, g, ev, obj, time.perf_counter() - ta))
 
     th = threading.Thread(target=worker, daemon=True)
     live, served, waits, done, first = {}, {}, [], [], []
@@ -223,14 +237,14 @@ def run_sessions(n_streams: int = 256, seconds: float = 3.0, budget_gb: float = 
                 todo.put(("open", k, now))
                 pending += 1
         while not opened.empty():  # first frame issued by the worker at admission time
-            k, f, g, ev, t_req, dt = opened.get()
+            k, f, raw, g, ev, t_req, dt = opened.get()
             pending -= 1
             open_s += dt
             n_open += 1
             nu = int(cfgs[k]["nu"])
             first.append((t_req, ev))
             done.append((t_req, nu, ev))
-            live[k] = dict(f=f, grid_host=g if keep else None, t_end=min(t_req + life[k], seconds),
+            live[k] = dict(f=f, raw=raw, grid_host=g if keep else None, t_end=min(t_req + life[k], seconds),
                            next=time.perf_counter() - t0 + rng.exponential(1.0 / cfgs[k]["rate_hz"]),
                            last=ev, frames=1, rate=cfgs[k]["rate_hz"], nu=nu)
         max_live = max(max_live, len(live))
@@ -251,7 +265,7 @@ def run_sessions(n_streams: int = 256, seconds: float = 3.0, budget_gb: float = 
                 served[k] = dict(frames=s["frames"])
                 if keep:
                     served[k].update(grid=s["grid_host"], cells=s["f"].cells(["m_occ", "m_free", "p_occ"]))
-                todo.put(("close", k, s["f"]))
+                todo.put(("close", k, (s["f"], s["raw"])))
                 pending += 1
                 del live[k]
         if now >= seconds and not live and pending == 0:
