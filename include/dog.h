@@ -273,20 +273,23 @@ int dog_kernels_per_step(const dog_filter *f);
  * memory -- code running where cudaMalloc is forbidden or unavailable, such as a host
  * callback, a real-time thread that must not take the allocator's locks, or a process whose
  * device memory is owned by another framework's pool).
- *   d_keys       [n] cell index of each particle (device; each < num_cells, others are left
- *                out of the ranges and sort in an unspecified place)
+ *   d_keys       [n] cell index of each particle (device).  A key >= num_cells (any value,
+ *                including those with the top bit set) belongs to no cell: such particles
+ *                are placed after all particles with valid keys, in input order, and are
+ *                in no cell's range.
  *   d_perm       [n] out: stable sort permutation (sorted position -> particle index)
  *   d_cell_start, d_cell_end [num_cells] out: half-open range of each cell in sorted order,
  *                0/0 for an empty cell (the same values as DOG_DBG_PERM / CELL_START / END)
- * Limits: n <= DOG_NOALLOC_MAX_PARTICLES, num_cells <= DOG_NOALLOC_MAX_CELLS; larger sizes
- * return DOG_ERR_UNSUPPORTED and touch nothing.  Scratch: one fixed array of 8,405,248
- * bytes in the library's device image (held by every GPU that loads the library until the
- * process exits); no call allocates or frees memory.  Asynchronous on cuda_stream.
- * The first call on a device looks up that array's device address for the current device
- * (make it before any stream capture).  Every call on a device shares the array: calls
- * that overlap on the GPU (other streams or threads) race and must be serialised. */
+ * Limits: n <= DOG_NOALLOC_MAX_PARTICLES, 1 <= num_cells <= DOG_NOALLOC_MAX_CELLS; larger
+ * sizes return DOG_ERR_UNSUPPORTED and touch nothing.  Scratch: one fixed array of
+ * 10,502,400 bytes in the library's device image (held by every GPU that loads the library
+ * until the process exits); no call allocates or frees memory.  Asynchronous on cuda_stream.
+ * The first call in a CUDA context looks up that array's device address and sets the sort
+ * kernels' shared-memory limits for the current device (make it before any stream capture);
+ * later calls in the same context reuse them.  Every call on a device shares the array:
+ * calls that overlap on the GPU (other streams or threads) race and must be serialised. */
 #define DOG_NOALLOC_MAX_PARTICLES (1u << 19)
-#define DOG_NOALLOC_MAX_CELLS (1u << 22)
+#define DOG_NOALLOC_MAX_CELLS ((1u << 22) - 1u)
 int dog_assign_cells_noalloc(const uint32_t *d_keys, uint32_t n, uint32_t num_cells,
                              uint32_t *d_perm, uint32_t *d_cell_start, uint32_t *d_cell_end,
                              void *cuda_stream);

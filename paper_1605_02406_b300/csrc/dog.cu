@@ -948,21 +948,27 @@ int dog_profile_read(dog_filter *f, float *ms, const char **names, int max, int 
 // ====================================================================================
 namespace {
 
-constexpr uint32_t NA_MAX_N = 1u << 19;      // particles per call
-constexpr uint32_t NA_MAX_CELLS = 1u << 22;  // cells per call (keys of at most 22 bits)
+constexpr uint32_t NA_MAX_N = 1u << 19;             // particles per call
+constexpr uint32_t NA_MAX_CELLS = (1u << 22) - 1u;  // cells per call: with the sentinel
+                                                    // num_cells, keys of at most 22 bits
 constexpr uint32_t NA_TILES = NA_MAX_N / SORT_TILE;
 constexpr size_t NA_CTL = 256;
 static_assert(sizeof(DevCtl) <= NA_CTL, "the control block fits its slot");
 constexpr size_t NA_HIST = 2 * 2048 * 4;
 constexpr size_t NA_DCNT = (size_t)2 * NA_TILES * 2048 * 4;
 constexpr size_t NA_ARR = (size_t)NA_MAX_N * 4;
-constexpr size_t NA_BYTES = NA_CTL + NA_HIST + NA_DCNT + 3 * NA_ARR;  // 8,405,248 bytes
+constexpr size_t NA_BYTES = NA_CTL + NA_HIST + NA_DCNT + 4 * NA_ARR;  // 10,502,400 bytes
+static_assert(NA_MAX_CELLS == DOG_NOALLOC_MAX_CELLS && NA_MAX_N == DOG_NOALLOC_MAX_PARTICLES,
+              "the header states the limits");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
-// digit histograms of all passes for caller-provided keys; block t counts the keys of sort
-// tile t and writes that tile's first-pass digit counts
-__global__ void k_na_hist(const uint32_t *__restrict__ keys, KParams K, DevBufs B) {
+// The caller's keys with every key >= num_cells replaced by the sentinel num_cells (so that
+// those particles sort after all others, in input order, and fall in no cell's range), and
+// the digit histograms of all passes over them; block t handles sort tile t and writes that
+// tile's first-pass digit counts.
+__global__ void k_na_hist(const uint32_t *__restrict__ keys, uint32_t num_cells, uint32_t *__restrict__ kc,
+                          KParams K, DevBufs B) {
   extern __shared__ uint32_t sh[];
   const uint32_t nh = (uint32_t)K.passes * K.radix;
   for (uint32_t k = threadIdx.x; k < nh; k += blockDim.x) sh[k] = 0u;
@@ -971,7 +977,11 @@ __global__ void k_na_hist(const uint32_t *__restrict__ keys, KParams K, DevBufs 
   for (uint32_t i = blockIdx.x * SORT_TILE + threadIdx.x; i < (blockIdx.x + 1u) * SORT_TILE;
        i += blockDim.x) {
     const bool ok = i < K.nu;
-    const uint32_t key = ok ? keys[i] : 0u;
+    uint32_t key = 0u;
+    if (ok) {
+      key = min(keys[i], num_cells);
+      if (kc) kc[i] = key;
+    }
     for (int p = 0; p < K.passes; ++p) {
       const uint32_t d = ok ? ((key >> (p * K.dbits)) & mask) : 0xffffffffu;
       const uint32_t peers = __match_any_sync(FULL, d);
@@ -985,7 +995,7 @@ __global__ void k_na_hist(const uint32_t *__restrict__ keys, KParams K, DevBufs 
     B.dcnt[(size_t)d * K.tiles_sort + blockIdx.x] = sh[d];
 }
 
-// half-open range of each cell in the sorted order (keys outside [0, num_cells) are skipped)
+// half-open range of each cell in the sorted order (the sentinel key num_cells is skipped)
 __global__ void k_na_ranges(const uint32_t *__restrict__ ks, uint32_t n, uint32_t num_cells,
                             uint32_t *start, uint32_t *end) {
   for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
@@ -996,31 +1006,57 @@ __global__ void k_na_ranges(const uint32_t *__restrict__ ks, uint32_t n, uint32_
   }
 }
 
+// The scratch array's device address and the sort kernels' shared-memory limits belong to a
+// CUDA context: they are set up once per context (with its device current) and looked up
+// again whenever the calling thread's current context differs from the one they were set up
+// in (a context destroyed by cudaDeviceReset and created anew gets a fresh set-up).  The
+// context handle comes from the driver's cuCtxGetCurrent, reached through the runtime.
 struct NaDevice {
   bool ready = false;
+  void *ctx = nullptr;
   char *base = nullptr;
 };
 NaDevice g_na_dev[64];
 std::mutex g_na_mutex;
+typedef int (*CtxGetCurrentFn)(void **);
 
-// once per device, with that device current: the scratch array's device address (in host
-// code the array's name is only a stand-in; a kernel must be given this address)
+void *current_context() {
+  static CtxGetCurrentFn fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      (void)cudaGetLastError();
+      p = nullptr;
+    }
+    return (CtxGetCurrentFn)p;
+  }();
+  void *ctx = nullptr;
+  if (fn && fn(&ctx) != 0) ctx = nullptr;
+  return ctx;
+}
+
 int na_setup(char **base) {
   int dev = 0;
   DOG_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return DOG_ERR_UNSUPPORTED;
+  void *ctx = current_context();  // null if no context is current in this thread yet
   std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (!g_na_dev[dev].ready) {
+  NaDevice &d = g_na_dev[dev];
+  if (!d.ready || ctx != d.ctx) {
     void *p = nullptr;
+    d.ready = false;
+    // (the first runtime call on the device binds its primary context to the thread)
     DOG_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
     DOG_CUDA(cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sort_smem_bytes(2048)));
     DOG_CUDA(cudaFuncSetAttribute(k_sort_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)count_smem_bytes(2048, COUNT_TILES)));
-    g_na_dev[dev].base = (char *)p;
-    g_na_dev[dev].ready = true;
+    d.base = (char *)p;
+    d.ctx = current_context();
+    d.ready = d.ctx != nullptr;  // without a context handle: set up again on every call
   }
-  *base = g_na_dev[dev].base;
+  *base = d.base;
   return DOG_OK;
 }
 
@@ -1039,8 +1075,9 @@ extern "C" int dog_assign_cells_noalloc(const uint32_t *d_keys, uint32_t n, uint
   DOG_CUDA(cudaMemsetAsync(d_cell_start, 0, 4 * (size_t)num_cells, st));
   DOG_CUDA(cudaMemsetAsync(d_cell_end, 0, 4 * (size_t)num_cells, st));
   if (n == 0) return DOG_OK;
+  // key bits cover the sentinel num_cells
   int bits = 1;
-  while ((1ull << bits) < num_cells) ++bits;
+  while ((1ull << bits) <= num_cells) ++bits;
   KParams K{};
   K.nu = n;
   K.passes = (bits + 10) / 11;
@@ -1051,13 +1088,15 @@ extern "C" int dog_assign_cells_noalloc(const uint32_t *d_keys, uint32_t n, uint
   B.ctl = (DevCtl *)base;
   B.hist = (uint32_t *)(base + NA_CTL);
   B.dcnt = (uint32_t *)(base + NA_CTL + NA_HIST);
-  uint32_t *key_t0 = (uint32_t *)(base + NA_CTL + NA_HIST + NA_DCNT);
+  uint32_t *key_c = (uint32_t *)(base + NA_CTL + NA_HIST + NA_DCNT);
+  uint32_t *key_t0 = key_c + NA_MAX_N;
   uint32_t *val_t0 = key_t0 + NA_MAX_N;
   uint32_t *key_sorted = val_t0 + NA_MAX_N;
   // every array of the scratch is rewritten before it is read: the histogram by k_tick, the
-  // per-tile digit counts by k_na_hist (first pass) and k_sort_count (later passes)
+  // clamped keys and the per-tile digit counts by k_na_hist (first pass) and k_sort_count
+  // (later passes)
   k_tick<<<1, 256, 0, st>>>(B, 2048 * K.passes);
-  k_na_hist<<<K.tiles_sort, 256, 4u * K.passes * K.radix, st>>>(d_keys, K, B);
+  k_na_hist<<<K.tiles_sort, 256, 4u * K.passes * K.radix, st>>>(d_keys, num_cells, key_c, K, B);
   const size_t ssm = sort_smem_bytes(K.radix);
   int sms = 148;
   {
@@ -1066,7 +1105,7 @@ extern "C" int dog_assign_cells_noalloc(const uint32_t *d_keys, uint32_t n, uint
     DOG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   }
   const uint32_t ct = count_tiles_per_block(K.tiles_sort, sms);
-  const uint32_t *kin = d_keys, *vin = nullptr;
+  const uint32_t *kin = key_c, *vin = nullptr;
   for (int p = 0; p < K.passes; ++p) {
     uint32_t *kout = (p == K.passes - 1) ? key_sorted : key_t0;
     uint32_t *vout = (p == K.passes - 1) ? d_perm : val_t0;
@@ -1143,7 +1182,7 @@ int enqueue_sort(dog_filter *f, int passes, uint32_t ct, cudaEvent_t e0, cudaEve
   const DevBufs &B = f->B;
   cudaStream_t st = f->st;
   DOG_CUDA(cudaMemsetAsync(B.hist, 0, 4 * 2048 * (size_t)passes, st));
-  k_na_hist<<<K.tiles_sort, 256, 4u * K.passes * K.radix, st>>>(B.key_pred, K, B);
+  k_na_hist<<<K.tiles_sort, 256, 4u * K.passes * K.radix, st>>>(B.key_pred, 0xffffffffu, nullptr, K, B);
   DOG_CUDA(cudaEventRecord(e0, st));
   const size_t ssm = sort_smem_bytes(K.radix);
   const uint32_t *kin = B.key_pred, *vin = nullptr;

@@ -33,7 +33,7 @@ SYMBOLS = ["dog_workspace_bytes", "dog_create", "dog_set_measurement_grid", "dog
            "dog_last_cuda_error", "dog_eval_clusters", "dog_eval_mahalanobis",
            "dog_get_cells_async", "dog_wait_cells", "dog_set_ego_motion", "dog_set_bernoulli_grid",
            "dog_autotune", "dog_set_sort_config", "dog_sort_config"]
-DOG_NOALLOC_MAX_PARTICLES, DOG_NOALLOC_MAX_CELLS = 1 << 19, 1 << 22
+DOG_NOALLOC_MAX_PARTICLES, DOG_NOALLOC_MAX_CELLS = 1 << 19, (1 << 22) - 1
 
 
 class dog_params(C.Structure):

@@ -7,6 +7,9 @@ framework's pool).  Its scratch lives in one fixed array inside the library, sha
 calls.  The test feeds it the cell indices that dog_step computed for a frame and checks
 that it returns the same sort permutation and cell ranges that dog_step itself produced,
 on two calls in a row of different sizes (the second must not see the first's leftovers).
+Keys outside [0, num_cells) -- which the filter never produces but a caller may pass -- must
+sort after every valid key, in input order, and belong to no cell's range; that case and the
+largest accepted sizes are checked against numpy's stable argsort and a brute-force scan.
 This file is collected last so that a failure here stops a `-x` run only after every other
 test has run; it also passes alone in a fresh process.
 """
@@ -39,7 +42,7 @@ def _noalloc(keys_np, num_cells):
 
     from paper_1605_02406_b300 import native as N
     stream = torch.cuda.current_stream()
-    keys = torch.from_numpy(keys_np.astype(np.int32).view(np.int32)).cuda()
+    keys = torch.from_numpy(np.ascontiguousarray(keys_np, dtype=np.uint32).view(np.int32)).cuda()
     n = keys_np.size
     perm = torch.full((max(n, 1),), -1, dtype=torch.int32, device="cuda")
     start = torch.full((num_cells,), -1, dtype=torch.int32, device="cuda")
@@ -64,6 +67,62 @@ def test_noalloc_assignment_matches_dog_step_twice():
         assert np.array_equal(perm, ref["PERM"]), f"call {seed}: permutation differs"
         assert np.array_equal(start, ref["CELL_START"]), f"call {seed}: cell starts differ"
         assert np.array_equal(end, ref["CELL_END"]), f"call {seed}: cell ends differ"
+
+
+def _reference(keys, num_cells):
+    """Stable order with every key >= num_cells treated as the sentinel num_cells, and the
+    half-open range of each cell found by scanning the sorted keys."""
+    sk = np.minimum(keys.astype(np.int64), num_cells)
+    perm = np.argsort(sk, kind="stable").astype(np.uint32)
+    ks = sk[perm]
+    start = np.zeros(num_cells, np.uint32)
+    end = np.zeros(num_cells, np.uint32)
+    heads = np.flatnonzero(np.r_[True, ks[1:] != ks[:-1]])
+    tails = np.r_[heads[1:], ks.size]
+    for h, t in zip(heads, tails):
+        if ks[h] < num_cells:
+            start[ks[h]], end[ks[h]] = h, t
+    return perm, start, end
+
+
+def _check_against_reference(keys, num_cells, what):
+    perm, start, end = _noalloc(keys, num_cells)
+    rp, rs, re_ = _reference(keys, num_cells)
+    assert np.array_equal(perm, rp), f"{what}: permutation differs"
+    assert np.array_equal(start, rs), f"{what}: cell starts differ"
+    assert np.array_equal(end, re_), f"{what}: cell ends differ"
+    # every particle with a valid key lies in its cell's range
+    k = keys.astype(np.int64)
+    pos = np.empty(keys.size, np.int64)
+    pos[perm] = np.arange(keys.size)
+    ok = k < num_cells
+    assert np.all((rs[k[ok]] <= pos[ok]) & (pos[ok] < re_[k[ok]])), what
+
+
+def test_noalloc_keys_beyond_the_grid_sort_last_in_no_range():
+    rng = np.random.default_rng(11)
+    num_cells, n = 1000, 3 * 4096 + 123
+    keys = rng.integers(0, num_cells, n).astype(np.uint32)
+    bad = rng.random(n) < 0.1
+    keys[bad] = rng.choice(np.array([num_cells, num_cells + 33, 1 << 20, (1 << 31) | 5, 0xFFFFFFFF],
+                                    dtype=np.uint32), int(bad.sum()))
+    _check_against_reference(keys, num_cells, "1000 cells, 10 % of keys out of range")
+    # a cell index just below the limit next to keys just above it (133 = 100 + 33 shares its
+    # low bits with cell 5, which must keep its own range)
+    keys2 = np.array([5, 133, 5, 99, 100, 0, 133, 5], np.uint32)
+    _check_against_reference(keys2, 100, "100 cells, keys sharing low bits with cell 5")
+
+
+def test_noalloc_at_its_largest_sizes():
+    import torch
+
+    from paper_1605_02406_b300 import native as N
+    rng = np.random.default_rng(12)
+    n, C = N.DOG_NOALLOC_MAX_PARTICLES, N.DOG_NOALLOC_MAX_CELLS
+    keys = rng.integers(0, C + 64, n).astype(np.uint32)  # a few beyond the grid
+    keys[: n // 8] = np.sort(keys[: n // 8])             # a nearly sorted stretch
+    _check_against_reference(keys, C, "largest sizes")
+    torch.cuda.synchronize()
 
 
 def test_noalloc_rejects_sizes_beyond_its_limit():
