@@ -31,7 +31,6 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 from paper_1605_02406_b300 import scene  # noqa: E402
-from paper_1605_02406_b300.ncu_summary import csrc_hash  # noqa: E402
 
 METRIC = "particle-updates/s at 1024² grid, 4M particles; p50/p99 latency batched vs plain"
 CFG_ID = "automotive_1024"
@@ -54,6 +53,18 @@ ALG_BYTES = {
     "k_resample": (8, 4, 0),      # read w' 4; write the source index 4; newborn w 4
     "k_tick": (0, 0, 0),
 }
+
+
+def csrc_hash() -> str:
+    """Hash of the CUDA sources: DRAM traffic recorded in profiles/ncu_traffic.json is
+    reported only while the kernels it was measured on are unchanged."""
+    import hashlib
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_1605_02406_b300", "csrc")
+    for n in sorted(os.listdir(d)):
+        with open(os.path.join(d, n), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
 
 
 def peaks() -> tuple:

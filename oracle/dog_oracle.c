@@ -358,9 +358,9 @@ static int cmp_keyidx(const void *a, const void *b) {
 
 /* Radar spatial likelihood g (reading: Gaussian in the particle's radial velocity as seen
  * from the sensor; the constant factor cancels in the normalisation Eq. DSnormalizationfactor). */
-static real likelihood(const oracle *o, real x, real y, real vx, real vy, int64_t c) {
-  real dx = x - (real)o->p.sensor_x;
-  real dy = y - (real)o->p.sensor_y;
+static real radar_g(real sx, real sy, real x, real y, real vx, real vy, real zv, real sg) {
+  real dx = x - sx;
+  real dy = y - sy;
   real a = dx * dx;
   real b = dy * dy;
   real r2 = a + b;
@@ -372,11 +372,14 @@ static real likelihood(const oracle *o, real x, real y, real vx, real vy, int64_
     real num = e + f;
     vr = num / r;
   }
-  real dd = vr - o->zv[c];
-  real d = dd / o->sgv[c];
+  real dd = vr - zv;
+  real d = dd / sg;
   real d2 = d * d;
   real ex = R(-0.5) * d2;
   return R_EXP(ex);
+}
+static real likelihood(const oracle *o, real x, real y, real vx, real vy, int64_t c) {
+  return radar_g((real)o->p.sensor_x, (real)o->p.sensor_y, x, y, vx, vy, o->zv[c], o->sgv[c]);
 }
 
 /* smallest q in [0, a] with (q+1) * d > a * b, i.e. floor(a*b/d), d > 0 */
@@ -955,6 +958,13 @@ void oracle_cell_update(double m_pred, double m_free_prev, double zO, double zF,
               &mO, &mF, &rb, &rp, &mFp);
   out[0] = mO; out[1] = mF; out[2] = rb; out[3] = rp;
   out[4] = mFp;
+}
+
+/* exposed for the pins of the radar likelihood (the mode's arithmetic, inputs rounded to it) */
+double oracle_radar_likelihood(double sensor_x, double sensor_y, double x, double y, double vx,
+                               double vy, double z_vr, double sigma_vr) {
+  return (double)radar_g((real)(float)sensor_x, (real)(float)sensor_y, (real)x, (real)y, (real)vx,
+                         (real)vy, (real)z_vr, (real)sigma_vr);
 }
 
 /* exposed for the statistical pins of the noise generator */

@@ -47,6 +47,8 @@ def _lib(mode: str):
         lib.oracle_cell_update.argtypes = [C.c_double] * 6 + [C.POINTER(C.c_double)]
         lib.oracle_box_muller.argtypes = [C.c_uint32, C.c_uint32, fp]
         lib.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        lib.oracle_radar_likelihood.restype = C.c_double
+        lib.oracle_radar_likelihood.argtypes = [C.c_double] * 8
         if mode == "f32":
             lib.oracle_ln_f32.restype = C.c_float
             lib.oracle_ln_f32.argtypes = [C.c_float]
@@ -213,6 +215,12 @@ def sincos2pi_f32(u: float):
     s, c = C.c_float(), C.c_float()
     _lib("f32").oracle_sincos2pi_f32(float(u), C.byref(s), C.byref(c))
     return s.value, c.value
+
+
+def radar_likelihood(sensor, x, y, vx, vy, z_vr, sigma_vr, mode: str = "f32") -> float:
+    """The radar spatial likelihood g of one particle (constant factor dropped)."""
+    return _lib(mode).oracle_radar_likelihood(float(sensor[0]), float(sensor[1]), float(x), float(y),
+                                              float(vx), float(vy), float(z_vr), float(sigma_vr))
 
 
 def cell_update(m_pred, m_free_prev, zO, zF, alpha, p_B, mode: str = "f32") -> dict:

@@ -188,7 +188,15 @@ def run_sessions(n_streams: int = 256, seconds: float = 3.0, budget_gb: float = 
     # each stream's measurement grid, as its sensor would deliver it (made before the run)
     grids = [scene.random_measurement_grid(c["width"], c["height"], rng) for c in cfgs]
 
+    failed = queue.Queue()  # an exception of the worker, re-raised by the request loop
+
     def worker():
+        try:
+            serve_jobs()
+        except BaseException as e:  # noqa: BLE001 -- handed to the request loop
+            failed.put(e)
+
+    def serve_jobs():
         while True:
             job = todo.get()
             if job is None:
@@ -224,6 +232,10 @@ def run_sessions(n_streams: int = 256, seconds: float = 3.0, budget_gb: float = 
     t0 = time.perf_counter()
     ci = 0
     while True:
+        if not failed.empty():
+            raise RuntimeError("serving worker failed while opening or closing a filter") from failed.get()
+        if not th.is_alive():
+            raise RuntimeError("serving worker exited unexpectedly")
         now = time.perf_counter() - t0
         while ci < n and connect[ci] <= now:
             adm.request(ci, need[ci])
