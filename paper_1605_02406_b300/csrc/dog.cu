@@ -97,12 +97,13 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
   B->bassoc = record ? (uint32_t *)take(4 * (nb ? nb : 1)) : nullptr;
   float **pc[] = {&B->mF, &B->zO, &B->zF, &B->pA, &B->zv, &B->sgv, &B->mO, &B->rho_p, &B->rho_b,
                   &B->pO, &B->mean_x, &B->mean_y, &B->var_x, &B->var_y, &B->cov, &B->mpred,
-                  &B->muA, &B->muU, &B->paeff, &B->rinv};
+                  &B->muA, &B->muU, &B->paeff};
   for (auto q : pc) *q = (float *)take(4 * C);
   B->mF_warp = (p.flags & DOG_EGO) ? (float *)take(4 * C) : nullptr;
   B->mF_in = (p.flags & DOG_EGO) ? B->mF_warp : B->mF;
   B->rb_pred = (p.flags & DOG_FULL) ? (float *)take(4 * C) : nullptr;
   B->csum = (CellSum *)take(sizeof(CellSum) * C);
+  B->cmom = (CellMom *)take(sizeof(CellMom) * C);
   B->g_stage = (float *)take(4 * 5 * C);
   B->c_stage = (float *)take(4 * (10 * C + 64));
   B->A = (unsigned long long *)take(8 * C);
@@ -122,8 +123,7 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
   B->S_piece = (unsigned long long *)take(8 * C);
   B->A_piece = (unsigned long long *)take(8 * C);
   B->Mx = (unsigned long long *)take(8 * 5 * C);
-  B->Mcnt = (uint32_t *)take(4 * C);
-  B->Pf = (float *)take(4 * 10 * (size_t)d.tiles_seg);
+  B->Pf = (float *)take(4 * 20 * (size_t)d.tiles_seg);
   B->tile_whole = (uint32_t *)take(4 * (size_t)d.tiles_seg);
   B->cross_t1 = (uint32_t *)take(4 * C);
   B->tile_q = (unsigned long long *)take(8 * (size_t)d.tiles_cell);
@@ -248,8 +248,12 @@ int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
   if (radar) k_birth<true><<<f->birth_grid, BIRTH_BLOCK, 0, st>>>(K, B);
   else k_birth<false><<<f->birth_grid, BIRTH_BLOCK, 0, st>>>(K, B);
   ++k; mark();
-  if (radar) k_normalise<true><<<K.tiles_norm, NORM_BLOCK, 0, st>>>(K, B);
-  else k_normalise_lidar<<<K.tiles_norm, NORM_BLOCK, 0, st>>>(K, B);
+  if (radar) {
+    k_normalise<true><<<K.tiles_norm, NORM_BLOCK, 0, st>>>(K, B);
+    k_moments<<<(K.C + 255) / 256 < 2368u ? (K.C + 255) / 256 : 2368u, 256, 0, st>>>(K, B);  // timed with it
+  } else {
+    k_normalise_lidar<<<K.tiles_norm, NORM_BLOCK, 0, st>>>(K, B);
+  }
   ++k; mark();
   k_scan_tiles<true><<<1, SCAN_BLOCK, 0, st>>>(B.cdf_tile, nullptr, K.tiles_norm, B.cdf_incl, nullptr,
                                                 &B.ctl->W_total, nullptr, K, B.ctl);
@@ -282,7 +286,6 @@ int reset_epochs(dog_filter *f) {
   DOG_CUDA(cudaMemsetAsync(B.S_piece, 0, 8 * (size_t)d.C, f->st));
   DOG_CUDA(cudaMemsetAsync(B.A_piece, 0, 8 * (size_t)d.C, f->st));
   DOG_CUDA(cudaMemsetAsync(B.Mx, 0, 8 * 5 * (size_t)d.C, f->st));
-  DOG_CUDA(cudaMemsetAsync(B.Mcnt, 0, 4 * (size_t)d.C, f->st));
   return DOG_OK;
 }
 
@@ -362,7 +365,8 @@ int dog_workspace_bytes(const dog_params *params, size_t *out_bytes) {
 
 int dog_kernels_per_step(const dog_filter *f) {
   if (!f) return 0;
-  return f->nk + ((f->p.flags & DOG_EGO) ? 2 : 0);  // + the ego-motion setting and warp
+  // + the radar filter's moment kernel, + the ego-motion setting and warp
+  return f->nk + (f->radar ? 1 : 0) + ((f->p.flags & DOG_EGO) ? 2 : 0);
 }
 
 static_assert(FLAG_EGO == DOG_EGO, "the kernels' ego flag is the ABI's");

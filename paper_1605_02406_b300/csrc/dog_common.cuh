@@ -41,16 +41,24 @@ struct DevCtl {
 //                   checkpoint, or a frame without resampling).
 enum : uint32_t { POST_RESAMPLED = 0, POST_DIRECT = 1 };
 
-// Per-cell result of the segment pass, one 32-byte record so that a finished cell costs two
-// 16-byte stores: S = 2^-40 fixed-point sum of the predicted weights, tag = 2 frame (cell
-// finished in one tile) or 2 frame + 1 (pieces in the accumulators), m = the lidar
-// filter's velocity moments (mean x, mean y, var x, var y, cov) of a cell finished in one tile.
-struct __align__(32) CellSum {
+// Per-cell result of the segment pass, a 16-byte head read by the cell update for every
+// cell: S = 2^-40 fixed-point sum of the predicted weights, tag = 2 frame (cell finished in
+// one tile) or 2 frame + 1 (pieces in the accumulators).
+struct __align__(16) CellSum {
   unsigned long long S;
   uint32_t tag;
-  float m[5];
+  uint32_t pad;
 };
-static_assert(sizeof(CellSum) == 32, "cell record is 32 bytes");
+static_assert(sizeof(CellSum) == 16, "cell head is 16 bytes");
+// The lidar filter's compensated (double-float hi + lo) sums of w vx, w vy, w vx^2, w vy^2,
+// w vx vy over a cell finished in one tile, 48 bytes (three 16-byte stores), read by the
+// cell update only for such cells.
+struct __align__(16) CellMom {
+  float hi[5];
+  float lo[5];
+  uint32_t pad[2];
+};
+static_assert(sizeof(CellMom) == 48, "moment record is 48 bytes");
 
 struct KParams {
   int W, H;
@@ -87,8 +95,9 @@ struct DevBufs {
   // pA = p_A, zv = p_FP, sgv = p_c (clutter density; the single-object likelihood is 1)
   float *zO, *zF, *pA, *zv, *sgv;
   float *mO, *rho_p, *rho_b, *pO, *mean_x, *mean_y, *var_x, *var_y, *cov;
-  float *mpred, *muA, *muU, *paeff, *rinv;
+  float *mpred, *muA, *muU, *paeff;
   CellSum *csum;                   // [C] segment-pass result per cell
+  CellMom *cmom;                   // [C] lidar moment sums of cells finished in one tile
   float *g_stage;                  // [5][C] measurement grid uploaded from the host
   float *c_stage;                  // [10][C] + error word: cells read back to the host
   unsigned long long *A;           // [C] fixed-point sum of g w (radar)
@@ -105,13 +114,13 @@ struct DevBufs {
   uint32_t *dcnt;                  // [passes][tiles_sort][radix] digit counts of each sort
                                    // tile, turned into global output offsets in place
   unsigned long long *S_piece, *A_piece;  // [C] pieces of cells spread over several tiles
-  unsigned long long *Mx;          // [5][C] moment pieces (radar normalisation)
-  float *Pf;                       // [tiles_seg][2][5] lidar moment sums of a segment tile's
-                                   // first segment begun earlier (or the whole tile) and of
-                                   // its last segment continued later
+  unsigned long long *Mx;          // [5][C] moment pieces of cells spread over several
+                                   // normalisation tiles (radar filter)
+  float *Pf;                       // [tiles_seg][2][10] lidar moment sums (hi[5], lo[5]) of
+                                   // a segment tile's first segment begun earlier (or the
+                                   // whole tile) and of its last segment continued later
   uint32_t *tile_whole;            // [tiles_seg] 1: the tile lies inside one cell
   uint32_t *cross_t1;              // [C] first segment tile of a cell spread over tiles
-  uint32_t *Mcnt;                  // [C] pieces counted in so far
   unsigned long long *tile_q, *tile_qin;  // [tiles_cell] newborn mass per tile, inclusive
   uint32_t *tile_n, *tile_nin;             // [tiles_cell] birth cells per tile, inclusive
   unsigned long long *cdf_tile, *cdf_incl; // [tiles_norm] joint weight per tile, inclusive

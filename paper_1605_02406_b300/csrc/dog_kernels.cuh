@@ -12,8 +12,9 @@
 //   k_scan_tiles          prefix of the tiles' newborn masses
 //   k_birth_prep  Alg. 5  slot range, associated share and weights of each birth cell
 //   k_birth       Alg. 5  newborn particles, slots proportional to the newborn mass
-//   k_normalise   Alg. 4/6 normalised persistent weights, velocity moments, tile sums of
-//                          the joint weights
+//   k_normalise   Alg. 4/6 normalised persistent weights, velocity moment sums, tile sums
+//                          of the joint weights
+//   k_moments     Alg. 6  (radar filter) the cells' velocity moments from those sums
 //   k_scan_tiles          CDF of the joint weights over tiles
 //   k_resample    Alg. 7  systematic resampling A + newborns -> B
 // No block waits for another block of the same launch: every cross-block dependency is a
@@ -260,10 +261,10 @@ constexpr int PRED_BLOCK = 256, PRED_ROUNDS = 4, PRED_TILE = PRED_BLOCK * 4 * PR
 // moves that bit from the cell index to the particle index (see k_sort_pass)
 constexpr uint32_t OUT_OF_GRID = 0x80000000u;
 
-__device__ __forceinline__ void predict_one(const KParams &P, uint32_t i, uint32_t frame, float T,
-                                            float4 &st, float &w, uint32_t &key) {
+__device__ __forceinline__ void predict_one(const KParams &P, const PhiloxKeys &PK, uint32_t i, uint32_t frame,
+                                            float T, float4 &st, float &w, uint32_t &key) {
   float &x = st.x, &y = st.y, &vx = st.z, &vy = st.w;
-  const U4 r = philox(i, frame, TAG_PREDICT, P.seed_lo, P.seed_hi);
+  const U4 r = philox(i, frame, TAG_PREDICT, PK);
   float n0, n1, n2, n3;
   gauss2(r.a, r.b, n0, n1);
   gauss2(r.c, r.d, n2, n3);
@@ -294,6 +295,7 @@ __global__ void __launch_bounds__(PRED_BLOCK) k_predict(KParams P, DevBufs B) {
   const uint32_t mask = P.radix - 1u;
   const bool ego = (P.flags & FLAG_EGO) != 0u && B.ctl->ego_on != 0u;
   const Ego E{B.ctl->ego_c, B.ctl->ego_s, B.ctl->ego_dx, B.ctl->ego_dy};
+  const PhiloxKeys PK = philox_keys(P.seed_lo, P.seed_hi);
   for (int rnd = 0; rnd < PRED_ROUNDS; ++rnd) {
     const uint32_t i0 = blockIdx.x * PRED_TILE + (uint32_t)rnd * (PRED_BLOCK * 4) + threadIdx.x * 4;
     uint32_t key[4];
@@ -317,10 +319,10 @@ __global__ void __launch_bounds__(PRED_BLOCK) k_predict(KParams P, DevBufs B) {
         ego_transform(P, E, s2);
         ego_transform(P, E, s3);
       }
-      predict_one(P, i0 + 0, frame, T, s0, w.x, key[0]);
-      predict_one(P, i0 + 1, frame, T, s1, w.y, key[1]);
-      predict_one(P, i0 + 2, frame, T, s2, w.z, key[2]);
-      predict_one(P, i0 + 3, frame, T, s3, w.w, key[3]);
+      predict_one(P, PK, i0 + 0, frame, T, s0, w.x, key[0]);
+      predict_one(P, PK, i0 + 1, frame, T, s1, w.y, key[1]);
+      predict_one(P, PK, i0 + 2, frame, T, s2, w.z, key[2]);
+      predict_one(P, PK, i0 + 3, frame, T, s3, w.w, key[3]);
       B.As[i0] = s0;
       B.As[i0 + 1] = s1;
       B.As[i0 + 2] = s2;
@@ -338,7 +340,7 @@ __global__ void __launch_bounds__(PRED_BLOCK) k_predict(KParams P, DevBufs B) {
           float4 s = posterior_record(P, B, mode, i);
           if (ego) ego_transform(P, E, s);
           float w = mode == POST_DIRECT ? B.Bw[i] : w_res;
-          predict_one(P, i, frame, T, s, w, key[k]);
+          predict_one(P, PK, i, frame, T, s, w, key[k]);
           B.As[i] = s;
           B.Aw[i] = w;
           B.key_pred[i] = key[k];
@@ -783,26 +785,58 @@ __device__ __forceinline__ Seg<N, V> seg_zero(const Seg<N, V> &) {
   return r;
 }
 
-// a fixed-point weight sum and five binary32 moment sums under one head flag
+// five compensated (double-float) moment sums under one head flag, and the same with the
+// fixed-point weight sum of the segment pass
+struct SegMom {
+  uint32_t f;
+  DF m[5];
+};
 struct SegQM {
   uint32_t f;
   unsigned long long q;
-  float m[5];
+  DF m[5];
 };
+__device__ __forceinline__ SegMom seg_combine(const SegMom &a, const SegMom &b) {
+  SegMom r;
+  r.f = a.f | b.f;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) r.m[k] = b.f ? b.m[k] : df_add(a.m[k], b.m[k]);
+  return r;
+}
 __device__ __forceinline__ SegQM seg_combine(const SegQM &a, const SegQM &b) {
   SegQM r;
   r.f = a.f | b.f;
   r.q = b.f ? b.q : a.q + b.q;
 #pragma unroll
-  for (int k = 0; k < 5; ++k) r.m[k] = b.f ? b.m[k] : __fadd_rn(a.m[k], b.m[k]);
+  for (int k = 0; k < 5; ++k) r.m[k] = b.f ? b.m[k] : df_add(a.m[k], b.m[k]);
+  return r;
+}
+template <typename S>
+__device__ __forceinline__ void shfl_moments(S &r, const S &a, int o) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    r.m[k].hi = __shfl_up_sync(FULL, a.m[k].hi, o);
+    r.m[k].lo = __shfl_up_sync(FULL, a.m[k].lo, o);
+  }
+}
+__device__ __forceinline__ SegMom seg_shfl_up(const SegMom &a, int o) {
+  SegMom r;
+  r.f = __shfl_up_sync(FULL, a.f, o);
+  shfl_moments(r, a, o);
   return r;
 }
 __device__ __forceinline__ SegQM seg_shfl_up(const SegQM &a, int o) {
   SegQM r;
   r.f = __shfl_up_sync(FULL, a.f, o);
   r.q = __shfl_up_sync(FULL, a.q, o);
+  shfl_moments(r, a, o);
+  return r;
+}
+__device__ __forceinline__ SegMom seg_zero(const SegMom &) {
+  SegMom r;
+  r.f = 0;
 #pragma unroll
-  for (int k = 0; k < 5; ++k) r.m[k] = __shfl_up_sync(FULL, a.m[k], o);
+  for (int k = 0; k < 5; ++k) r.m[k] = DF{0.0f, 0.0f};
   return r;
 }
 __device__ __forceinline__ SegQM seg_zero(const SegQM &) {
@@ -810,7 +844,7 @@ __device__ __forceinline__ SegQM seg_zero(const SegQM &) {
   r.f = 0;
   r.q = 0ull;
 #pragma unroll
-  for (int k = 0; k < 5; ++k) r.m[k] = 0.0f;
+  for (int k = 0; k < 5; ++k) r.m[k] = DF{0.0f, 0.0f};
   return r;
 }
 
@@ -894,56 +928,64 @@ __device__ __forceinline__ void store_run(float *p, uint32_t j0, uint32_t n, con
   }
 }
 
-// moment terms of one particle: u v_x, u v_y, u v_x^2, u v_y^2, u v_x v_y (u = w'/rho_p)
-__device__ __forceinline__ void moment_terms(float u, float vx, float vy, float (&m)[5]) {
-  const float mx = __fmul_rn(u, vx), my = __fmul_rn(u, vy);
+// moment terms of one particle as exact double-float products: w v_x, w v_y, w v_x^2,
+// w v_y^2, w v_x v_y (w v_x and w v_y exact; the second products carry the first's low part)
+__device__ __forceinline__ void moment_terms(float w, float vx, float vy, DF (&m)[5]) {
+  const DF mx = two_prod(w, vx), my = two_prod(w, vy);
   m[0] = mx;
   m[1] = my;
-  m[2] = __fmul_rn(mx, vx);
-  m[3] = __fmul_rn(my, vy);
-  m[4] = __fmul_rn(mx, vy);
+  const DF xx = two_prod(mx.hi, vx), yy = two_prod(my.hi, vy), xy = two_prod(mx.hi, vy);
+  m[2] = DF{xx.hi, __fmaf_rn(mx.lo, vx, xx.lo)};
+  m[3] = DF{yy.hi, __fmaf_rn(my.lo, vy, yy.lo)};
+  m[4] = DF{xy.hi, __fmaf_rn(mx.lo, vy, xy.lo)};
 }
 
-// Eq. mean_x, var_x, covar_xy from the cell's sums of u v, u v^2, u vx vy
-__device__ __forceinline__ void moments_store(const DevBufs &B, uint32_t c, const float (&m)[5]) {
-  const float mx = m[0], my = m[1];
-  B.mean_x[c] = mx;
-  B.mean_y[c] = my;
-  B.var_x[c] = fmaxf(__fsub_rn(m[2], __fmul_rn(mx, mx)), 0.0f);
-  B.var_y[c] = fmaxf(__fsub_rn(m[3], __fmul_rn(my, my)), 0.0f);
-  B.cov[c] = __fsub_rn(m[4], __fmul_rn(mx, my));
+// Eq. mean_x, var_x, covar_xy from the expectations E[vx], E[vy], E[vx^2], E[vy^2], E[vx vy]
+// under the cell-normalised weights (double-float), each result rounded once to binary32;
+// variances clamped at 0
+__device__ __forceinline__ void moments_of_expectations(const DF (&E)[5], float (&o)[5]) {
+  o[0] = df_to_f(E[0]);
+  o[1] = df_to_f(E[1]);
+  o[2] = fmaxf(df_to_f(df_sub(E[2], df_mul(E[0], E[0]))), 0.0f);
+  o[3] = fmaxf(df_to_f(df_sub(E[3], df_mul(E[1], E[1]))), 0.0f);
+  o[4] = df_to_f(df_sub(E[4], df_mul(E[0], E[1])));
 }
-
-// the first 16 bytes of a cell record: S, tag and the first moment
-__device__ __forceinline__ void csum_store_head(CellSum *r, unsigned long long S, uint32_t tag, float m0) {
-  *reinterpret_cast<uint4 *>(r) = make_uint4((uint32_t)S, (uint32_t)(S >> 32), tag, __float_as_uint(m0));
-}
-
-// moments from the sums of w v, w v^2, w vx vy over a cell and its weight sum S (2^-40
-// fixed point): the cell-normalised weight is w / S
-__device__ __forceinline__ void moments_of_sums(const float (&m)[5], unsigned long long S, float (&o)[5]) {
-  float u[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  if (S != 0ull) {
-    const float inv = __fdiv_rn(1.0f, fx40_to_f(S));
+// the moments from the sums of w v, ... over a cell, times the factor f / d (f >= 0, d > 0):
+// E = sum (f / d), the factor once in double-float
+__device__ __forceinline__ void moments_scaled(const DF (&m)[5], float f, float d, float (&o)[5]) {
+  const DF k = df_div_f(DF{f, 0.0f}, d);
+  DF E[5];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) u[k] = __fmul_rn(m[k], inv);
-  }
-  const float mx = u[0], my = u[1];
-  o[0] = mx;
-  o[1] = my;
-  o[2] = fmaxf(__fsub_rn(u[2], __fmul_rn(mx, mx)), 0.0f);
-  o[3] = fmaxf(__fsub_rn(u[3], __fmul_rn(my, my)), 0.0f);
-  o[4] = __fsub_rn(u[4], __fmul_rn(mx, my));
+  for (int i = 0; i < 5; ++i) E[i] = df_mul(m[i], k);
+  moments_of_expectations(E, o);
 }
-__device__ __forceinline__ void moments_from_sums(const DevBufs &B, uint32_t c, const float (&m)[5],
-                                                  unsigned long long S) {
-  float o[5];
-  moments_of_sums(m, S, o);
+__device__ __forceinline__ void moments_store(const DevBufs &B, uint32_t c, const float (&o)[5]) {
   B.mean_x[c] = o[0];
   B.mean_y[c] = o[1];
   B.var_x[c] = o[2];
   B.var_y[c] = o[3];
   B.cov[c] = o[4];
+}
+
+// a cell's head: S and the tag
+__device__ __forceinline__ void csum_store_head(CellSum *r, unsigned long long S, uint32_t tag) {
+  *reinterpret_cast<uint4 *>(r) = make_uint4((uint32_t)S, (uint32_t)(S >> 32), tag, 0u);
+}
+// the compensated moment sums of a cell finished in one tile
+__device__ __forceinline__ void cmom_store(CellMom *r, const DF (&m)[5]) {
+  float4 *q = reinterpret_cast<float4 *>(r);
+  q[0] = make_float4(m[0].hi, m[1].hi, m[2].hi, m[3].hi);
+  q[1] = make_float4(m[4].hi, m[0].lo, m[1].lo, m[2].lo);
+  q[2] = make_float4(m[3].lo, m[4].lo, 0.0f, 0.0f);
+}
+__device__ __forceinline__ void cmom_load(const CellMom *r, DF (&m)[5]) {
+  const float4 *q = reinterpret_cast<const float4 *>(r);
+  const float4 a = q[0], b = q[1], c = q[2];
+  m[0] = DF{a.x, b.y};
+  m[1] = DF{a.y, b.z};
+  m[2] = DF{a.z, b.w};
+  m[3] = DF{a.w, c.x};
+  m[4] = DF{b.x, c.y};
 }
 
 // k_segsum: cell ranges (Alg. 2) and S_c = sum of q40(w) (Eq. DS_particle_sum_pred as an
@@ -1061,7 +1103,7 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
     if (t) {
       B.cend[c] = j + 1;
       if (seen) {
-        csum_store_head(B.csum + c, run[0], frame << 1, 0.0f);
+        csum_store_head(B.csum + c, run[0], frame << 1);
         if constexpr (RADAR) B.A[c] = run[N - 1];
       } else {
         atomicAdd(B.S_piece + c, run[0]);
@@ -1076,14 +1118,16 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
 }
 
 // k_segsum_lidar: k_segsum for a filter without radar likelihood (g == 1), which also sums
-// the velocity moments of Eq. mean_x, var_x, covar_xy.  With g == 1 the normalised weight
-// is w' = (rho_p / S_c) w, so the weight each moment uses, w' / rho_p, equals w / S_c: the
-// moments follow from the predicted weights here, one pass earlier than the normalisation.
-// w v, w v^2, w vx vy are summed per cell in binary32 by the same block-wide segmented
-// scan; a cell inside the tile is finished here; a cell spread over tiles adds the pieces
-// of S in exact 2^-40 fixed point and leaves its binary32 moment pieces in per-tile slots,
-// which k_cell adds in tile order.
-__global__ void __launch_bounds__(SEG_BLOCK, 6) k_segsum_lidar(KParams P, DevBufs B) {
+// the velocity moment terms of Eq. mean_x, var_x, covar_xy.  With g == 1 the normalised
+// weight is w' = mu_UA w with one factor mu_UA = rho_p / S_c per cell, so the moments
+// E[v] = sum w' v / rho_p = (mu_UA / rho_p) sum w v follow from sums of the predicted weights,
+// one pass earlier than the normalisation.  w v, w v^2, w vx vy are summed per cell as
+// compensated double-float sums (exact products, two_sum additions) by the block-wide
+// segmented scan; a cell inside the tile leaves its sums in its moment record; a cell spread
+// over tiles adds the pieces of S in exact 2^-40 fixed point and leaves its double-float
+// moment pieces in per-tile slots, which k_cell adds in tile order.  k_cell applies the
+// factor mu_UA / rho_p.
+__global__ void __launch_bounds__(SEG_BLOCK, 5) k_segsum_lidar(KParams P, DevBufs B) {
   __shared__ SegQM s_wqm[SEG_BLOCK / 32 + 1];
   __shared__ float s_x[3][SEG_PADDED];  // w, vx, vy in tile order (padded)
   const uint32_t tile = blockIdx.x, frame = B.ctl->frame;
@@ -1156,7 +1200,7 @@ __global__ void __launch_bounds__(SEG_BLOCK, 6) k_segsum_lidar(KParams P, DevBuf
   }
   const SegQM ex = block_seg_excl(agg, s_wqm);
   unsigned long long rq = ex.q;
-  float rm[5];
+  DF rm[5];
 #pragma unroll
   for (int k = 0; k < 5; ++k) rm[k] = ex.m[k];
   bool seen = ex.f != 0;  // the current segment's head lies in this tile
@@ -1170,13 +1214,13 @@ __global__ void __launch_bounds__(SEG_BLOCK, 6) k_segsum_lidar(KParams P, DevBuf
     const uint32_t j = j0 + it;
     if (j >= P.nu) break;
     const bool h = (head >> it) & 1u, t = (tail >> it) & 1u;
-    const uint32_t m = seg_pad(threadIdx.x * SEG_ITEMS + it);
+    const uint32_t m = seg_pad(threadIdx.x * SEG_ITEMS + it);  // the item's terms again
     const unsigned long long q = qw(s_x[0][m]);
-    float mt[5];
+    DF mt[5];
     moment_terms(s_x[0][m], s_x[1][m], s_x[2][m], mt);
     rq = h ? q : rq + q;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) rm[k] = h ? mt[k] : __fadd_rn(rm[k], mt[k]);
+    for (int k = 0; k < 5; ++k) rm[k] = h ? mt[k] : df_add(rm[k], mt[k]);
     seen |= h;
     const uint32_t c = key[it];
     if (record) {  // explicit cell ranges only for the diagnostic interface
@@ -1184,19 +1228,19 @@ __global__ void __launch_bounds__(SEG_BLOCK, 6) k_segsum_lidar(KParams P, DevBuf
       if (t) B.cend[c] = j + 1;
     }
     if (j == last_valid) B.tile_whole[tile] = (!t && !seen) ? 1u : 0u;
-    if (t && seen) {  // the whole cell lies in this tile: one 32-byte record
-      float o[5];
-      moments_of_sums(rm, rq, o);
-      csum_store_head(B.csum + c, rq, frame << 1, o[0]);
-      *reinterpret_cast<float4 *>(&B.csum[c].m[1]) = make_float4(o[1], o[2], o[3], o[4]);
+    if (t && seen) {  // the whole cell lies in this tile: its head and moment sums
+      csum_store_head(B.csum + c, rq, frame << 1);
+      cmom_store(B.cmom + c, rm);
     } else if (t || j == last_valid) {  // a piece of a cell spread over several tiles
-      // S exactly in fixed point; the moment sums in binary32 in this tile's slot (0: the
-      // cell began in an earlier tile, 1: it continues in a later one), which k_cell adds in
-      // tile order (full relative precision however small the weights are)
+      // S exactly in fixed point; the moment sums in this tile's slot (0: the cell began in
+      // an earlier tile, 1: it continues in a later one), which k_cell adds in tile order
       atomicAdd(B.S_piece + c, rq);
-      float *slot = B.Pf + ((size_t)tile * 2u + (seen ? 1u : 0u)) * 5u;
+      float *slot = B.Pf + ((size_t)tile * 2u + (seen ? 1u : 0u)) * 10u;
 #pragma unroll
-      for (int k = 0; k < 5; ++k) slot[k] = rm[k];
+      for (int k = 0; k < 5; ++k) {
+        slot[k] = rm[k].hi;
+        slot[5 + k] = rm[k].lo;
+      }
       if (seen) B.cross_t1[c] = tile;
       if (t) B.csum[c].tag = (frame << 1) | 1u;
     }
@@ -1405,7 +1449,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
   uint32_t wn = 0u;
   // all loads of the thread's cells first (independent, in flight together)
   uint32_t tgs[CELL_ITEMS];
-  float mFs[CELL_ITEMS], zOs[CELL_ITEMS], zFs[CELL_ITEMS], m0s[CELL_ITEMS];
+  float mFs[CELL_ITEMS], zOs[CELL_ITEMS], zFs[CELL_ITEMS];
   unsigned long long Ss[CELL_ITEMS];
   const bool full = !RADAR && (P.flags & FLAG_FULL) != 0u;  // the PHD/MIB filter of Sect. VI
 #pragma unroll
@@ -1415,7 +1459,6 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
     const uint4 h = in ? *reinterpret_cast<const uint4 *>(B.csum + c) : make_uint4(0u, 0u, 0u, 0u);
     Ss[it] = ((unsigned long long)h.y << 32) | h.x;
     tgs[it] = h.z;
-    m0s[it] = __uint_as_float(h.w);
     mFs[it] = in ? B.mF_in[c] : 0.0f;
     zOs[it] = in ? B.zO[c] : 0.0f;
     zFs[it] = in ? B.zF[c] : 0.0f;
@@ -1441,7 +1484,7 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
       const unsigned long long S = Ss[it];
       const float Sf = fx40_to_f(S);
       const float mp = fminf(Sf, 1.0f);
-      float mO, mF, rb, rp, alloc;
+      float mO, mF, rb, rp, alloc, muU;
       float muA = 0.0f, pa = 0.0f;
       if (full) {
         // predicted Bernoulli RFS: persistent existence r_p = min(S, 1) (the weights of a cell
@@ -1474,20 +1517,20 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
         muA = f;                      // newborn weights f r_b / n (k_birth_prep)
         B.rb_pred[c] = rbp;
         B.pO[c] = mO;
-        B.muU[c] = (S > 0ull) ? (Sf > 1.0f ? __fdiv_rn(f, Sf) : f) : 0.0f;
+        muU = (S > 0ull) ? (Sf > 1.0f ? __fdiv_rn(f, Sf) : f) : 0.0f;
       } else {
         cell_update(P, mp, mFs[it], zOs[it], zFs[it], mO, mF, rb);
         rp = __fsub_rn(mO, rb);
         alloc = rb;
         B.pO[c] = __fadd_rn(mO, __fmul_rn(0.5f, __fsub_rn(__fsub_rn(1.0f, mO), mF)));
-        B.muU[c] = (S > 0ull) ? __fdiv_rn(rp, Sf) : 0.0f;
+        muU = (S > 0ull) ? __fdiv_rn(rp, Sf) : 0.0f;
       }
+      B.muU[c] = muU;
       // (m_pred itself is not stored: the diagnostic read recomputes it from S, k_mpred)
       B.mO[c] = mO;
       B.mF[c] = mF;
       B.rho_b[c] = rb;
       B.rho_p[c] = rp;
-      if constexpr (RADAR) B.rinv[c] = rp > 0.0f ? __fdiv_rn(1.0f, rp) : 0.0f;  // radar moments
       if constexpr (RADAR) {
         unsigned long long A = 0ull;
         if (cross) {
@@ -1506,35 +1549,31 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
       // filter's stays 0 from the workspace's initialisation
       if (RADAR || full) B.muA[c] = muA;
       if constexpr (!RADAR) {  // moments of the lidar filter (see k_segsum_lidar)
+        // E[v] = sum w' v / rho_p with w' = mu_UA w: the compensated sums of w v, ... times
+        // mu_UA / rho_p in double-float (Eq. mean_x, var_x, covar_xy)
         float o[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        if (cross) {  // the cell's pieces in tile order: first, whole tiles, last
-          uint32_t t = B.cross_t1[c];
-          float mm[5];
-          const float *first = B.Pf + ((size_t)t * 2u + 1u) * 5u;
+        if (occ && rp > 0.0f && muU > 0.0f) {
+          DF mm[5];
+          if (cross) {  // the cell's pieces in tile order: first, whole tiles, last
+            uint32_t t = B.cross_t1[c];
+            const float *first = B.Pf + ((size_t)t * 2u + 1u) * 10u;
 #pragma unroll
-          for (int k = 0; k < 5; ++k) mm[k] = first[k];
-          for (++t; t < P.tiles_seg; ++t) {
-            const float *pc = B.Pf + (size_t)t * 10u;
+            for (int k = 0; k < 5; ++k) mm[k] = DF{first[k], first[5 + k]};
+            for (++t; t < P.tiles_seg; ++t) {
+              const float *pc = B.Pf + (size_t)t * 20u;
 #pragma unroll
-            for (int k = 0; k < 5; ++k) mm[k] = __fadd_rn(mm[k], pc[k]);
-            if (!B.tile_whole[t]) break;
+              for (int k = 0; k < 5; ++k) mm[k] = df_add(mm[k], DF{pc[k], pc[5 + k]});
+              if (!B.tile_whole[t]) break;
+            }
+          } else {  // finished by the segment pass
+            cmom_load(B.cmom + c, mm);
           }
-          moments_of_sums(mm, rp > 0.0f ? S : 0ull, o);
-        } else if (occ && rp > 0.0f) {  // finished by the segment pass
-          const float4 r = *reinterpret_cast<const float4 *>(&B.csum[c].m[1]);
-          o[0] = m0s[it];
-          o[1] = r.x;
-          o[2] = r.y;
-          o[3] = r.z;
-          o[4] = r.w;
+          moments_scaled(mm, muU, rp, o);
         }
-        B.mean_x[c] = o[0];
-        B.mean_y[c] = o[1];
-        B.var_x[c] = o[2];
-        B.var_y[c] = o[3];
-        B.cov[c] = o[4];
+        moments_store(B, c, o);
       } else if (!occ) {
-        B.mean_x[c] = 0.0f; B.mean_y[c] = 0.0f; B.var_x[c] = 0.0f; B.var_y[c] = 0.0f; B.cov[c] = 0.0f;
+        float z[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        moments_store(B, c, z);
       }
       qb = q40(alloc);
     }
@@ -1764,18 +1803,25 @@ __global__ void __launch_bounds__(BIRTH_BLOCK) k_birth(KParams P, DevBufs B) {
 // in sorted order, read contiguously from the sorted copy, then newborn slots):
 //   w' = p_A mu_A g w + (1 - p_A) mu_UA w   (Eq. DSnormalization; lidar cells: mu_UA w),
 //   velocity moments of the persistent particles per cell (Eq. mean_x, var_x, covar_xy):
-//   the terms u v, u v^2, u vx vy of the cell-normalised weight u = w'/rho_p are summed by
-//   the block's segmented scan in binary32 (fixed tree order, so runs repeat bit for bit);
-//   a cell spread over several tiles collects its pieces in exact fixed point with integer
-//   atomics and the tile adding the last piece (counted against the cell's tile span)
-//   finishes it; and the tile sum of q40 of the joint weights for the resampling CDF.
+//   the terms w' v, w' v^2, w' vx vy are formed as exact double-float products and summed
+//   by the block's segmented scan with compensated additions; a cell inside the tile leaves
+//   its sums in its moment record; a cell spread over several tiles adds its pieces,
+//   divided by rho_p, in exact 2^-40 fixed point with integer atomics; k_moments finishes
+//   both;
+//   and the tile sum of q40 of the joint weights for the resampling CDF.
 // ====================================================================================
 constexpr int NORM_BLOCK = 256, NORM_ITEMS = 8, NORM_TILE = NORM_BLOCK * NORM_ITEMS;
 
+// shared-memory index of a thread's item, padded by one element per NORM_ITEMS so that a
+// warp reading its threads' item k hits distinct banks
+__device__ __forceinline__ uint32_t norm_pad(uint32_t m) { return m + m / NORM_ITEMS; }
+constexpr int NORM_PADDED = NORM_TILE + NORM_TILE / NORM_ITEMS;
+
 template <bool RADAR>
 __global__ void __launch_bounds__(NORM_BLOCK, 4) k_normalise(KParams P, DevBufs B) {
-  __shared__ Seg<5, float> s_w[NORM_BLOCK / 32 + 1];
+  __shared__ SegMom s_w[NORM_BLOCK / 32 + 1];
   __shared__ unsigned long long s_red[NORM_BLOCK / 32];
+  __shared__ float s_t[3][NORM_PADDED];  // w', vx, vy of the tile's items, for the tail pass
   const uint32_t tile = blockIdx.x;
   const uint32_t ntot = P.nu + P.nu_b;
   const uint32_t j0 = tile * NORM_TILE + threadIdx.x * NORM_ITEMS;
@@ -1783,12 +1829,9 @@ __global__ void __launch_bounds__(NORM_BLOCK, 4) k_normalise(KParams P, DevBufs 
   unsigned long long qsum = 0ull;
   const bool has_pers = tile * NORM_TILE < P.nu;  // block-uniform
   uint32_t key[NORM_ITEMS];
-  float mu[NORM_ITEMS], mvx[NORM_ITEMS], mvy[NORM_ITEMS];  // u = w'/rho_p and velocities
   uint32_t head = 0, tail = 0;
-  Seg<5, float> agg;
-  agg.f = 0;
-#pragma unroll
-  for (int k = 0; k < 5; ++k) agg.v[k] = 0.0f;
+  SegMom agg;
+  agg = seg_zero(agg);
   if (has_pers) {
     float ws[NORM_ITEMS], gs[NORM_ITEMS];
     load_run<NORM_ITEMS>(B.key_sorted, j0, P.nu, key, 0xffffffffu);
@@ -1796,24 +1839,19 @@ __global__ void __launch_bounds__(NORM_BLOCK, 4) k_normalise(KParams P, DevBufs 
     // the radar likelihood g of each particle, left in wn by k_segsum (for every particle of
     // a cell with p_A > 0, which includes every cell with an effective p_A > 0)
     if (RADAR) load_runf<NORM_ITEMS>(B.wn, j0, P.nu, gs);
-    float4 st[NORM_ITEMS];
+    float mvx[NORM_ITEMS], mvy[NORM_ITEMS], wnv[NORM_ITEMS];
 #pragma unroll
     for (int it = 0; it < NORM_ITEMS; ++it) {
-      st[it] = j0 + it < P.nu ? __ldg(B.Os + j0 + it) : make_float4(0.f, 0.f, 0.f, 0.f);
-      mvx[it] = st[it].z;
-      mvy[it] = st[it].w;
+      const float4 st = j0 + it < P.nu ? __ldg(B.Os + j0 + it) : make_float4(0.f, 0.f, 0.f, 0.f);
+      mvx[it] = st.z;
+      mvy[it] = st.w;
     }
     const uint32_t kprev = (j0 > 0 && j0 <= P.nu) ? __ldg(B.key_sorted + j0 - 1) : 0xfffffffeu;
     const uint32_t knext = (j0 + NORM_ITEMS < P.nu) ? __ldg(B.key_sorted + j0 + NORM_ITEMS) : 0xfffffffeu;
     // per-cell factors of all items before any arithmetic (independent loads in flight)
-    float cmu[NORM_ITEMS], crinv[NORM_ITEMS];
+    float cmu[NORM_ITEMS];
 #pragma unroll
-    for (int it = 0; it < NORM_ITEMS; ++it) {
-      const bool ok = j0 + it < P.nu;
-      cmu[it] = ok ? __ldg(B.muU + key[it]) : 0.0f;
-      crinv[it] = ok ? __ldg(B.rinv + key[it]) : 0.0f;
-    }
-    float wn_out[NORM_ITEMS];
+    for (int it = 0; it < NORM_ITEMS; ++it) cmu[it] = j0 + it < P.nu ? __ldg(B.muU + key[it]) : 0.0f;
 #pragma unroll
     for (int it = 0; it < NORM_ITEMS; ++it) {
       const uint32_t j = j0 + it;
@@ -1824,8 +1862,7 @@ __global__ void __launch_bounds__(NORM_BLOCK, 4) k_normalise(KParams P, DevBufs 
       const bool t = ok && (j == P.nu - 1 || key[it] != kn);
       head |= (uint32_t)h << it;
       tail |= (uint32_t)t << it;
-      mu[it] = 0.0f;
-      wn_out[it] = 0.0f;
+      wnv[it] = 0.0f;
       if (ok) {
         const uint32_t c = key[it];
         const float w = ws[it];
@@ -1840,16 +1877,19 @@ __global__ void __launch_bounds__(NORM_BLOCK, 4) k_normalise(KParams P, DevBufs 
         } else {
           wn = __fmul_rn(muU, w);
         }
-        wn_out[it] = wn;
+        wnv[it] = wn;
         qsum += q40(wn);
-        mu[it] = __fmul_rn(wn, crinv[it]);
       }
-      Seg<5, float> e;
+      SegMom e;
       e.f = h;
-      moment_terms(mu[it], mvx[it], mvy[it], e.v);
+      moment_terms(wnv[it], mvx[it], mvy[it], e.m);
       agg = seg_combine(agg, e);
+      const uint32_t m = norm_pad(threadIdx.x * NORM_ITEMS + it);
+      s_t[0][m] = wnv[it];
+      s_t[1][m] = mvx[it];
+      s_t[2][m] = mvy[it];
     }
-    store_run<NORM_ITEMS>(B.wn, j0, P.nu, wn_out);
+    store_run<NORM_ITEMS>(B.wn, j0, P.nu, wnv);
   }
   // newborn sources of this tile
 #pragma unroll
@@ -1868,12 +1908,12 @@ __global__ void __launch_bounds__(NORM_BLOCK, 4) k_normalise(KParams P, DevBufs 
     B.cdf_tile[tile] = tsum;
   }
   if (!has_pers) return;  // block-uniform
-  // segmented moment sums within the tile (binary32, combined in a fixed tree order)
-  const Seg<5, float> ex = block_seg_excl(agg, s_w);
+  // segmented compensated moment sums within the tile
+  const SegMom ex = block_seg_excl(agg, s_w);
   const uint32_t last_valid = min(tile * NORM_TILE + NORM_TILE, P.nu) - 1u;
-  float run[5];
+  DF run[5];
 #pragma unroll
-  for (int k = 0; k < 5; ++k) run[k] = ex.v[k];
+  for (int k = 0; k < 5; ++k) run[k] = ex.m[k];
   bool seen = ex.f != 0;
   // the running sums are only read at a segment's end or the tile's last particle
   if (tail == 0u && !(j0 <= last_valid && last_valid < j0 + NORM_ITEMS)) return;
@@ -1882,33 +1922,58 @@ __global__ void __launch_bounds__(NORM_BLOCK, 4) k_normalise(KParams P, DevBufs 
     const uint32_t j = j0 + it;
     if (j >= P.nu) break;
     const bool h = (head >> it) & 1u, t = (tail >> it) & 1u;
-    float m[5];
-    moment_terms(mu[it], mvx[it], mvy[it], m);
+    const uint32_t mi = norm_pad(threadIdx.x * NORM_ITEMS + it);
+    DF m[5];
+    moment_terms(s_t[0][mi], s_t[1][mi], s_t[2][mi], m);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) run[k] = h ? m[k] : __fadd_rn(run[k], m[k]);
+    for (int k = 0; k < 5; ++k) run[k] = h ? m[k] : df_add(run[k], m[k]);
     seen |= h;
     if (!t && j != last_valid) continue;
     const uint32_t c = key[it];
-    if (t && seen) {
-      if (__ldg(B.rho_p + c) > 0.0f) moments_store(B, c, run);  // the cell lies in this tile
-      else { float z[5] = {0.f, 0.f, 0.f, 0.f, 0.f}; moments_store(B, c, z); }
+    if (t && seen) {  // the cell lies in this tile: its raw sums, finished by k_moments
+      cmom_store(B.cmom + c, run);
       continue;
     }
-    // a piece of a cell spread over several tiles: exact fixed-point accumulation
+    // a piece of a cell spread over several tiles: its sums divided by rho_p, accumulated
+    // exactly in fixed point (|E[v]| <= max |v|, so the 2^-40 quanta are absolute errors)
+    const float rp = __ldg(B.rho_p + c);
+    if (!(rp > 0.0f)) continue;
     const size_t Cs = P.C;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) atomicAdd(B.Mx + k * Cs + c, q40s(run[k]));
-    __threadfence();
-    const uint32_t span = (__ldg(B.cend + c) - 1u) / NORM_TILE - __ldg(B.cstart + c) / NORM_TILE + 1u;
-    if (atomicAdd(B.Mcnt + c, 1u) + 1u == span) {
-      __threadfence();
-      float tot[5];
-#pragma unroll
-      for (int k = 0; k < 5; ++k) tot[k] = fx40s_to_f(atomicExch(B.Mx + k * Cs + c, 0ull));
-      atomicExch(B.Mcnt + c, 0u);
-      if (__ldg(B.rho_p + c) > 0.0f) moments_store(B, c, tot);
-      else { float z[5] = {0.f, 0.f, 0.f, 0.f, 0.f}; moments_store(B, c, z); }
+    for (int k = 0; k < 5; ++k) {
+      const DF e = df_div_f(run[k], rp);
+      atomicAdd(B.Mx + k * Cs + c, q40s(e.hi) + q40s(e.lo));
     }
+  }
+}
+
+// k_moments (radar filter, after k_normalise): the velocity moments of every cell with
+// particles this frame from its compensated sums of w' v, ... divided by rho_p (a cell
+// inside one normalisation tile) or from its exact fixed-point pieces (a cell spread over
+// several; read and cleared for the next frame); 0 where rho_p = 0.
+__global__ void __launch_bounds__(256) k_moments(KParams P, DevBufs B) {
+  const uint32_t frame = B.ctl->frame;
+  const size_t Cs = P.C;
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < P.C; c += gridDim.x * blockDim.x) {
+    const uint32_t tag = B.csum[c].tag;
+    if ((tag >> 1) != frame || frame == 0u) continue;  // no particles: zeros from k_cell
+    const uint32_t a = B.cstart[c], e = B.cend[c];
+    const bool whole = a / NORM_TILE == (e - 1u) / NORM_TILE;
+    const float rp = B.rho_p[c];
+    float o[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (whole) {
+      if (rp > 0.0f) {
+        DF m[5];
+        cmom_load(B.cmom + c, m);
+        moments_scaled(m, 1.0f, rp, o);
+      }
+    } else {
+      DF E[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) E[k] = fx40s_to_df(atomicExch(B.Mx + k * Cs + c, 0ull));
+      if (rp > 0.0f) moments_of_expectations(E, o);
+    }
+    moments_store(B, c, o);
   }
 }
 

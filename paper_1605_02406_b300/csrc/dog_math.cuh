@@ -34,6 +34,32 @@ __device__ __forceinline__ U4 philox(uint32_t e, uint32_t frame, uint32_t tag, u
   return U4{x0, x1, x2, x3};
 }
 
+// The same generator with its key schedule (the ten round keys, which depend on the seed
+// only) computed once: kernels that draw for several elements keep them in registers.
+struct PhiloxKeys {
+  uint32_t k0[10], k1[10];
+};
+__device__ __forceinline__ PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
+  PhiloxKeys K;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    K.k0[r] = k0 + (uint32_t)r * 0x9E3779B9u;
+    K.k1[r] = k1 + (uint32_t)r * 0xBB67AE85u;
+  }
+  return K;
+}
+__device__ __forceinline__ U4 philox(uint32_t e, uint32_t frame, uint32_t tag, const PhiloxKeys &K) {
+  uint32_t x0 = e, x1 = frame, x2 = tag, x3 = 0u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * x0, hi0 = __umulhi(0xD2511F53u, x0);
+    const uint32_t lo1 = 0xCD9E8D57u * x2, hi1 = __umulhi(0xCD9E8D57u, x2);
+    const uint32_t y0 = hi1 ^ x1 ^ K.k0[r], y2 = hi0 ^ x3 ^ K.k1[r];
+    x0 = y0; x1 = lo1; x2 = y2; x3 = lo0;
+  }
+  return U4{x0, x1, x2, x3};
+}
+
 enum : uint32_t { TAG_INIT = 0, TAG_PREDICT = 1, TAG_BIRTH = 2, TAG_RESAMPLE = 3 };
 
 // uniform draws from the top 24 bits: [0,1) and (0,1]
@@ -178,6 +204,59 @@ __device__ __forceinline__ float fx40s_to_f(unsigned long long s) {
   const int hi = (int)(uint32_t)(s >> 32);
   const uint32_t lo = (uint32_t)s;
   return __fmul_rn(__fadd_rn(__fmul_rn((float)hi, 0x1p32f), (float)lo), 0x1p-40f);
+}
+
+// ------------------------------------------------------------------------------------
+// Compensated (double-float) arithmetic for the per-cell velocity moments: a value is an
+// unevaluated sum hi + lo of two binary32 numbers.  two_sum (Knuth) and two_prod (with one
+// fused multiply-add) return the exact rounding error of a sum / product, so sums of
+// double-float terms carry about 48 significant bits whatever their number and order.
+// ------------------------------------------------------------------------------------
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return DF{s, e};
+}
+__device__ __forceinline__ DF two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return DF{p, __fmaf_rn(a, b, -p)};
+}
+// a + b; the low parts are added without compensation (their error is second order)
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const DF s = two_sum(a.hi, b.hi);
+  return DF{s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo))};
+}
+__device__ __forceinline__ DF df_norm(DF a) {  // hi = RN(hi + lo)
+  const float s = __fadd_rn(a.hi, a.lo);
+  return DF{s, __fsub_rn(a.lo, __fsub_rn(s, a.hi))};
+}
+__device__ __forceinline__ DF df_mul_f(DF a, float b) {
+  const DF p = two_prod(a.hi, b);
+  return df_norm(DF{p.hi, __fmaf_rn(a.lo, b, p.lo)});
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const DF p = two_prod(a.hi, b.hi);
+  const float c = __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.hi));
+  return df_norm(DF{p.hi, __fadd_rn(p.lo, c)});
+}
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, DF{-b.hi, -b.lo}); }
+// a / b for b > 0: quotient, exact remainder by one fused multiply-add, one correction
+__device__ __forceinline__ DF df_div_f(DF a, float b) {
+  const float q1 = __fdiv_rn(a.hi, b);
+  const float r = __fadd_rn(__fmaf_rn(-q1, b, a.hi), a.lo);
+  return df_norm(DF{q1, __fdiv_rn(r, b)});
+}
+__device__ __forceinline__ float df_to_f(DF a) { return __fadd_rn(a.hi, a.lo); }
+
+// signed 2^-40 fixed point -> double-float: the binary32 value and the exact integer
+// remainder below it
+__device__ __forceinline__ DF fx40s_to_df(unsigned long long s) {
+  const float hi = fx40s_to_f(s);
+  return DF{hi, fx40s_to_f(s - q40s(hi))};
 }
 
 // ------------------------------------------------------------------------------------

@@ -1,22 +1,27 @@
 """GPU parity: the CUDA path (through the C ABI) against the oracle's FP32 mirror on the
 same seeded inputs.  Integer and index results (cell keys, sort order, cell ranges,
 fixed-point sums, newborn slots, resample sources) and every FP32 mass, weight and particle
-state are compared bit for bit; velocity moments within a tolerance derived from the
-kernel's arithmetic:
+state are compared bit for bit; velocity means within 1e-5 absolute, variances and
+covariance within a bound derived from the arithmetic:
 
-The kernel sums the terms w v, w v^2, w vx vy (Eq. mean_x, var_x, covar_xy; for the lidar
-filter w'/rho_p = w/S_c exactly, so it uses the predicted weights w and divides by the
-fixed-point S_c; with a radar likelihood it sums u v, ... with u = w' (1/rho_p)) in binary32
-over a binary tree of depth <= 10 inside a 1024-particle tile and scales by one rounded
-reciprocal; the oracle sums w' v, ... in binary64 from its binary32 w' (one more rounding
-per term).  A lidar cell spread over p tiles adds its p binary32 pieces in tile order (p - 1
-more roundings); a radar cell adds its pieces of the normalised terms (whose |sum| is
-E|v|) in 2^-40 fixed point, one unit per piece.  Each normalised sum is therefore off by at
-most (10 + p + 4) 2^-24 of the sum of |terms| (+ p 2^-40 for radar), i.e. for p <= 100,
-|err(mean)| <= 114 * 2^-24 * E|v| + 1e-10 <= 7e-6 sqrt(E[v^2]).  The tolerances below are
-that bound with headroom (the cells of these cases span far fewer tiles):
-mean: 1e-5 (1 + sqrt(E[v^2])); variance and covariance: 1e-5 (1 + E[v^2]).
+The oracle forms E[v] = sum_i w'_i v_i / rho_p (Eq. mean_x) and E[v^2], E[vx vy] in binary64
+from its binary32 normalised weights w'_i = RN(mu_UA w_i) (radar cells: Eq. DSnormalization
+with g) and rounds each moment once to binary32.  The kernels form the products w v, w v^2,
+w vx vy exactly as double-float (hi + lo) values, add them with two_sum (compensated, about
+48 bits whatever the number of particles and tiles), and finish in double-float:
+lidar cells as (mu_UA / rho_p) sum w v, radar cells as sum w' v / rho_p with the oracle's own
+w'.  The two differ by (i) the rounding of each w'_i in the oracle, which the lidar kernel
+does not apply: |sum_i w'_i eps_i v_i / rho_p| <= 2^-24 E|v| (and usually far less, the
+eps_i being independent); (ii) the final binary32 rounding on each side, at most one unit
+in the last place of the moment between them; (iii) the double-float residue, < 2^-44
+relative.  Means: 2^-24 E|v| + ulp(mean) stays below 1e-5 for |v| <= 40 m/s, the tolerance
+the benchmark spec states.  Variances and covariance: the same terms on E[v^2] plus the
+cancellation in E[v^2] - E[v]^2: <= 2^-23 E[v^2] + 2 |mean| 1e-5 + ulp(var) + 1e-7; the
+tolerance is that bound.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -51,20 +56,43 @@ def assert_bits(name, got, ref):
     assert bad.size == 0, f"{name}: {bad.size} mismatches, first at {bad[:5]}: got {got[bad[:5]]} ref {ref[bad[:5]]}"
 
 
+MEAN_TOL = 1e-5  # absolute, on mean_vx and mean_vy
+
+
 def moment_tolerance(ref):
-    ev2x = ref["var_vx"].astype(np.float64) + ref["mean_vx"].astype(np.float64) ** 2
-    ev2y = ref["var_vy"].astype(np.float64) + ref["mean_vy"].astype(np.float64) ** 2
-    return {"mean_vx": 1e-5 * (1 + np.sqrt(ev2x)), "mean_vy": 1e-5 * (1 + np.sqrt(ev2y)),
-            "var_vx": 1e-5 * (1 + ev2x), "var_vy": 1e-5 * (1 + ev2y),
-            "cov_vxy": 1e-5 * (1 + np.sqrt(ev2x * ev2y))}
+    mx, my = (np.abs(ref[k].astype(np.float64)) for k in ("mean_vx", "mean_vy"))
+    ev2x = ref["var_vx"].astype(np.float64) + mx ** 2
+    ev2y = ref["var_vy"].astype(np.float64) + my ** 2
+    ulp = lambda a: np.spacing(np.abs(a).astype(np.float32)).astype(np.float64)
+
+    def var_tol(ev2, m, v):
+        return 2.0 ** -23 * ev2 + 2 * m * MEAN_TOL + ulp(v) + 1e-7
+    return {"mean_vx": np.full(mx.shape, MEAN_TOL), "mean_vy": np.full(my.shape, MEAN_TOL),
+            "var_vx": var_tol(ev2x, mx, ref["var_vx"]), "var_vy": var_tol(ev2y, my, ref["var_vy"]),
+            "cov_vxy": 2.0 ** -23 * np.sqrt(ev2x * ev2y) + (mx + my) * MEAN_TOL + ulp(ref["cov_vxy"]) + 1e-7}
+
+
+WORST = {}  # realised largest differences per moment over every frame compared
+
+
+def _record_worst(what, d):
+    for k, v in d.items():
+        WORST[k] = max(WORST.get(k, 0.0), float(v))
+    path = os.environ.get("DOG_PARITY_REPORT")
+    if path:
+        with open(path, "w") as f:
+            json.dump(WORST, f, indent=1, sort_keys=True)
 
 
 def assert_moments(got, ref):
     tol = moment_tolerance(ref)
+    worst = {}
     for k in MOMENT_FIELDS:
         d = np.abs(got[k].astype(np.float64) - ref[k].astype(np.float64))
+        worst[k] = d.max() if d.size else 0.0
         bad = np.flatnonzero(d > tol[k])
         assert bad.size == 0, f"{k}: {bad.size} cells off, worst {d.max()} at {bad[:5]}"
+    _record_worst("", worst)
 
 
 PARTICLE_DBG = [("PRED_X", "pred_x"), ("PRED_Y", "pred_y"), ("PRED_VX", "pred_vx"),
