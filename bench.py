@@ -127,23 +127,82 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_oracle_rate(params: dict, grids: list, budget_s: float = 12.0) -> dict:
-    """The oracle (FP32 mirror) on frames of the same workload until about budget_s."""
+def host_cpu() -> dict:
+    """The host's core count and CPU model (the oracle runs on one of its cores)."""
+    model = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+def oracle_frames(params: dict, grids: list, mode: str, frames: int, budget_s: float = 1e9) -> tuple:
+    """Frames of the oracle from the initial state (grid set + step, wall clock); returns
+    (frames done, seconds)."""
     from oracle import OracleFilter
-    o = OracleFilter(params, "f32")
-    n, t0 = 0, time.perf_counter()
-    while True:
+    o = OracleFilter(params, mode)
+    n, el = 0, 0.0
+    while n < frames and el < budget_s:
         g = grids[n % len(grids)]
-        o.set_measurement_grid(g["m_occ"], g["m_free"])
+        args = [g["m_occ"], g["m_free"]] + ([g["p_A"], g["z_vr"], g["sigma_vr"]] if "p_A" in g else [])
+        o.set_measurement_grid(*args)
+        t0 = time.perf_counter()
         o.step(0.1)
+        el += time.perf_counter() - t0
         n += 1
-        el = time.perf_counter() - t0
-        if el > budget_s or n >= len(grids):
-            break
+    return n, el
+
+
+def cpu_oracle_rate(params: dict, grids: list, budget_s: float = 12.0) -> dict:
+    """The oracle (FP32 mirror) on frames of the same workload until about budget_s, and
+    its binary64 mode on a few frames."""
+    n, el = oracle_frames(params, grids, "f32", len(grids), budget_s)
+    n64, el64 = oracle_frames(params, grids, "f64", 3, budget_s / 2)
     return {"value": params["nu"] * n / el, "unit": "particle-updates/s", "cores": 1,
             "kind": "oracle",
             "sample": f"{n} consecutive frames of the full 1024x1024 / 4,194,304 + 1,048,576 "
-                      f"particle workload from the initial state, single thread"}
+                      f"particle workload from the initial state, single thread (step time only)",
+            "f64": {"value": params["nu"] * n64 / el64, "frames": n64},
+            "host": host_cpu()}
+
+
+def cpu_plan() -> dict:
+    """The CPU baseline plan: both oracle modes, single thread, median of 3 runs, on the plain
+    128x128 workload (20 frames), the automotive 1024x1024 workload (100 frames), the first 10
+    frames of the 2048x2048 lidar + radar workload and 3 sampled filters of the 64-filter batch
+    (50 frames each).  Step time only (scene generation excluded).  Tens of minutes."""
+    cases = [("plain_128", scene.CONFIGS["plain_128"], 20, 1001),
+             ("automotive_1024", scene.CONFIGS["automotive_1024"], 100, 1002),
+             ("fusion_2048 (first 10 frames)", scene.CONFIGS["fusion_2048"], 10, 1005)]
+    bcfgs = scene.batched_configs(64)
+    for k in (0, 21, 42):
+        cases.append((f"batched filter {k} ({bcfgs[k]['width']}x{bcfgs[k]['height']}, {bcfgs[k]['nu']:,} particles)",
+                      bcfgs[k], 50, 2000 + k))
+    out = {"host": host_cpu(), "runs": 3, "cases": []}
+    for name, cfg, frames, seed in cases:
+        params = scene.filter_params(cfg, seed=42)
+        grids = scene.frame_sequence(cfg, min(frames, 16), seed)
+        row = {"workload": name, "frames": frames, "num_particles": params["nu"]}
+        for mode in ("f32", "f64"):
+            ts = [oracle_frames(params, grids, mode, frames)[1] for _ in range(3)]
+            t = statistics.median(ts)
+            row[mode] = {"seconds": t, "particle_updates_per_s": params["nu"] * frames / t}
+        out["cases"].append(row)
+        print(json.dumps(row), flush=True)
+    return out
+
+
+def bench_config(cfg: dict, params: dict, world: int) -> dict:
+    """The workload description, the same in both arms."""
+    return {"workload": cfg["name"], "grid": "1024x1024", "cell_size_m": 0.1,
+            "num_particles": params["nu"], "num_birth": params["nu_b"],
+            "scene": "30 moving rectangles, 200 static boxes, 2160 beams",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "l2": "inputs larger than L2 (particle state 168 MB); no flush"}
 
 
 def run_reference(args) -> None:
@@ -156,7 +215,7 @@ def run_reference(args) -> None:
     params = scene.filter_params(cfg)
     grids = scene.frame_sequence(cfg, min(args.steps + args.warmup, 16), 1002)
     o = OracleFilter(params, "f32")
-    warm = min(args.warmup, 3)
+    warm = args.warmup
     for k in range(warm):
         g = grids[k % len(grids)]
         o.set_measurement_grid(g["m_occ"], g["m_free"])
@@ -178,8 +237,7 @@ def run_reference(args) -> None:
         "n_gpus": args.gpus, "steps": done, "warmup": warm,
         "ms_per_step": el / done * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": cfg["name"], "grid": "1024x1024", "cell_size_m": 0.1,
-                   "num_particles": params["nu"], "num_birth": params["nu_b"]},
+        "config": bench_config(cfg, params, 1),
         "cpu_baseline": {"value": v, "unit": "particle-updates/s", "cores": 1, "kind": "oracle",
                          "sample": f"{done} full frames (of {args.steps} requested, bounded to "
                                    f"~120 s) after {warm} warm-up frames, single thread"},
@@ -233,8 +291,10 @@ def batched_latency(frames: int, warmup: int, dt: float = 0.1, rank: int = 0, wo
             f.step(dt)
 
     t_plain = t_batch = [0.0]  # a rank without filters still joins the reductions
+    grouping = None
     if filters:
         batch = DogBatch(filters)
+        grouping = batch.autotune(dts, frames=2)  # real frames, before the timed region
         t_plain = run(plain)
         t_batch = run(lambda: batch.step(dts))
         batch.close()
@@ -247,8 +307,51 @@ def batched_latency(frames: int, warmup: int, dt: float = 0.1, rank: int = 0, wo
     med = replicas.slowest(float(np.median(t_batch)), "cuda")
     return dict({"workload": "batched: 64 filters, sides 256-1024 at 0.1 m, 2^18-2^22 particles each "
                              f"({nu_total:,} in total)" + (f", placed on {world} GPUs by HBM need" if world > 1 else ""),
-                 "frames": frames}, **pct,
+                 "frames": frames, "grouping": grouping}, **pct,
                 batched_particle_updates_per_s=nu_total / (med * 1e-3))
+
+
+def small_batch_latency(frames: int, warmup: int, n: int = 128, side: int = 64, nu: int = 8192) -> dict:
+    """Many small filters (128 grids of 64x64 at 0.25 m, 8,192 + 2,048 particles each), where
+    launches rather than bytes dominate: a loop of dog_step calls vs one batched frame."""
+    import torch
+
+    from paper_1605_02406_b300.filter import DogBatch, DogFilter
+    shared = torch.cuda.Stream()
+    rng = np.random.default_rng(3)
+    filters = []
+    for k in range(n):
+        p = dict(width=side, height=side, cell_size=0.25, nu=nu, nu_b=nu // 4, p_S=0.99, p_B=0.02,
+                 alpha=0.9, sigma_pos=0.05, sigma_vel=1.0, sigma_birth_vel=4.0, sensor_x=side * 0.125,
+                 sensor_y=side * 0.125, seed=700 + k, flags=0)
+        f = DogFilter(p, stream=shared)
+        g = scene.random_measurement_grid(side, side, rng)
+        f.set_measurement_grid(**{kk: torch.tensor(v, device="cuda") for kk, v in g.items()})
+        filters.append(f)
+    batch = DogBatch(filters)
+    grouping = batch.autotune(0.1, frames=2)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * frames)]
+
+    def run(step):
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        for k in range(frames):
+            ev[2 * k].record(shared)
+            step()
+            ev[2 * k + 1].record(shared)
+        torch.cuda.synchronize()
+        return [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(frames)]
+
+    t_plain = run(lambda: [f.step(0.1) for f in filters])
+    t_batch = run(lambda: batch.step(0.1))
+    batch.close()
+    for f in filters:
+        f.close()
+    return {"workload": f"{n} filters of {side}x{side} at 0.25 m, {nu:,} + {nu // 4:,} particles each",
+            "grouping": grouping,
+            "plain_p50": float(np.percentile(t_plain, 50)), "plain_p99": float(np.percentile(t_plain, 99)),
+            "batched_p50": float(np.percentile(t_batch, 50)), "batched_p99": float(np.percentile(t_batch, 99))}
 
 
 def evaluation_time(reps: int = 50) -> dict:
@@ -396,10 +499,16 @@ def main() -> None:
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-filter latency run")
     ap.add_argument("--no-fusion", action="store_true", help="skip the lidar + radar workload")
     ap.add_argument("--no-evaluation", action="store_true", help="skip timing the evaluation calls")
-    ap.add_argument("--no-serving", action="store_true", help="skip the two 3 s serving-loop runs")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop runs")
+    ap.add_argument("--serving-seconds", type=float, default=10.0,
+                    help="simulated seconds of arrivals per serving arm (the workload states 60)")
     ap.add_argument("--no-ego", action="store_true", help="skip the ego-motion workload")
     ap.add_argument("--no-phdmib", action="store_true", help="skip the PHD/MIB filter workload")
+    ap.add_argument("--cpu-plan", action="store_true", help="only the full CPU baseline plan (slow)")
     args = ap.parse_args()
+    if args.cpu_plan:
+        print(json.dumps(cpu_plan()), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -536,10 +645,11 @@ def main() -> None:
     batched = {"workload": None}
     if not args.no_batched:
         batched = batched_latency(frames=min(args.steps, 50), warmup=args.warmup, rank=rank, world=world)
-    serving = None
+    serving = serving_plain = None
     if not args.no_serving:
         from paper_1605_02406_b300 import serve
-        serving = serve.run(seconds=3.0, rank=rank, world=world)
+        serving_plain = serve.run(seconds=args.serving_seconds, rank=rank, world=world, plain=True)
+        serving = serve.run(seconds=args.serving_seconds, rank=rank, world=world)
         if world > 1:
             last = replicas.slowest(serving["last_completion_s"], "cuda")
             updates = replicas.total(serving["updates"], "cuda")
@@ -559,9 +669,12 @@ def main() -> None:
     sessions = None
     if not args.no_serving:
         from paper_1605_02406_b300 import serve
-        sessions = serve.run_sessions(seconds=3.0)
+        sessions = serve.run_sessions(seconds=min(args.serving_seconds, 5.0))
         if world > 1:
             sessions["workload"] += " (rank 0's GPU only)"
+    small = None
+    if not args.no_batched:
+        small = small_batch_latency(frames=min(args.steps, 50), warmup=args.warmup)
     evaluation = None if args.no_evaluation else evaluation_time()
     fusion = None
     if not args.no_fusion:
@@ -576,14 +689,9 @@ def main() -> None:
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": cfg["name"], "grid": "1024x1024", "cell_size_m": 0.1,
-                   "num_particles": nu, "num_birth": nb, "scene": "30 moving rectangles, 200 static boxes, 2160 beams",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": "inputs larger than L2 (particle state 168 MB); no flush",
-                   "launch": "CUDA graph per step",
-                   "sort": dict(sort_cfg, chosen_by="dog_autotune")},
-        "latency_ms": dict(batched, step_p50=float(np.percentile(per_step, 50)),
-                           step_p99=float(np.percentile(per_step, 99))),
+        "config": bench_config(cfg, params, world),
+        "launch": "CUDA graph per step",
+        "sort": dict(sort_cfg, chosen_by="dog_autotune"),
         "e2e": {"value": e2e_value, "unit": "particle-updates/s",
                 "h2d_bytes_per_step": 2 * 4 * C, "d2h_bytes_per_step": 3 * 4 * C},
         "gpu_launches": launches,
@@ -601,8 +709,14 @@ def main() -> None:
         "ego": ego,
         "phdmib": phdmib,
         "evaluation": evaluation,
-        "serving": serving,
         "serving_sessions": sessions,
+        "serving_plain": serving_plain,
+        "serving": serving,
+        # last, so that the tail of the line the driver keeps holds it: per-frame latency of
+        # the 64-filter batched workload (a loop of dog_step vs one batched frame), of the
+        # many-small-filters batch, and of the single filter's step
+        "latency_ms": dict(batched, step_p50=float(np.percentile(per_step, 50)),
+                           step_p99=float(np.percentile(per_step, 99)), small_filters=small),
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -300,25 +300,51 @@ void dog_destroy(dog_filter *f);
 
 /* ---- Batched stepping (no counterpart in the paper: a way to run many independent
  * filters per frame).  A batch advances n filters by one frame each with a single CUDA-graph
- * launch whose n parallel branches are the filters' own frame sequences, so small filters
- * overlap on the GPU and the host issues one launch instead of n.  Every filter of a batch
- * must have been created on the same non-NULL stream; the batch launches on that stream, so
- * each filter's other calls (grids, cells, state) stay ordered with the batched frames.
- * Filters created with DOG_PROFILE cannot be batched.  A filter may belong to several
- * batches and may still be stepped alone with dog_step; the caller must not destroy a
- * filter before the batches that hold it. */
+ * launch in which every phase of the frame (prediction, each sort pass, cell sums, cell
+ * update, newborns, normalisation, resampling) is ONE kernel launch over the tiles of all n
+ * filters: a block finds its filter and tile from a prefix table of the filters' block
+ * counts, so small and large filters fill the GPU together.  Each filter's parameters and
+ * buffer table are written into a 1 KB slot of its own workspace when the batch captures its
+ * graph (the library still allocates no device memory).  Every filter of a batch must have
+ * been created on the same non-NULL stream; the batch launches on that stream, so each
+ * filter's other calls (grids, cells, state) stay ordered with the batched frames.  Filters
+ * created with DOG_PROFILE cannot be batched.  A filter may belong to several batches and
+ * may still be stepped alone with dog_step; the caller must not destroy a filter before the
+ * batches that hold it. */
 typedef struct dog_batch dog_batch;
 
-/* Create a batch over filters[0..n) (n >= 1, pointers kept, not owned).
- * Errors: INVALID_ARG (NULL, n < 1, different or NULL streams, a profiling filter), CUDA. */
+/* Create a batch over filters[0..n) (1 <= n <= 128, distinct, pointers kept, not owned).
+ * Errors: INVALID_ARG (NULL, n < 1, a filter listed twice, different or NULL streams, a
+ * profiling filter), UNSUPPORTED (n > 128), CUDA. */
 int dog_batch_create(dog_filter *const *filters, int n, dog_batch **out);
 
 /* One frame of every filter of the batch, with time steps dt[0..n) (host array, s).  Each
  * filter needs a measurement grid, as for dog_step.  Asynchronous; results equal n calls of
  * dog_step bit for bit.  The graph is captured on the first call and again whenever a
- * filter's grid switched between lidar and lidar + radar.
+ * filter's grid switched between lidar and lidar + radar, its sort configuration changed
+ * (dog_autotune, dog_set_sort_config), or another batch captured it since.
  * Errors: INVALID_ARG (dt out of domain), BAD_STATE (a filter without grid), CUDA. */
 int dog_batch_step(dog_batch *b, const float *dt);
+
+/* Grouping of the batch's filters: consecutive filters (in the order given to
+ * dog_batch_create) whose workspaces add up to at most group_bytes form one group; a filter
+ * larger than that is a group of its own.  Each group is one branch of the batch graph, the
+ * branches run concurrently, and within a group of several filters every phase of the frame
+ * is one launch over all of them; a group of one filter runs its own kernels.  0 (the
+ * default) makes every filter its own branch; SIZE_MAX fuses the whole batch into one group.
+ * Results do not depend on the grouping.  The graph is captured again at the next step.
+ * dog_batch_groups returns the current number of groups.  Errors: INVALID_ARG. */
+int dog_batch_set_group_bytes(dog_batch *b, size_t group_bytes);
+int dog_batch_groups(const dog_batch *b, int *n_groups);
+
+/* Pick the grouping by measurement: steps the batch with each candidate grouping (one
+ * filter per branch, groups of up to 64 MB, 256 MB, 1 GB, 4 GB of workspace, the whole batch
+ * fused), `frames` timed frames each after one that captures the graph, with time steps
+ * dt[0..n), and keeps the fastest (written to *chosen if not NULL).  These are real frames of
+ * every filter (each needs its measurement grid, as for dog_batch_step): the filters advance
+ * by one frame per step taken, results being the same under every grouping.  Synchronises
+ * the batch's stream.  Errors: as dog_batch_step; INVALID_ARG (frames < 1). */
+int dog_batch_autotune(dog_batch *b, const float *dt, int frames, size_t *chosen);
 
 /* Release the batch (waits for its stream); the filters stay. */
 void dog_batch_destroy(dog_batch *b);

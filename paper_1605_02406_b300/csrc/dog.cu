@@ -3,6 +3,7 @@
 // graph and replayed), checkpoint, intermediates and kernel profiling.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -13,6 +14,7 @@
 
 #include "../../include/dog.h"
 #include "dog_kernels.cuh"
+#include "dog_batch.cuh"
 #include "dog_eval.cuh"
 
 using namespace dog;
@@ -20,6 +22,7 @@ using namespace dog;
 namespace {
 
 constexpr int MAX_KERNELS = 18;
+constexpr size_t DOG_BATCH_GROUP_BYTES_DEFAULT = 0;  // one filter per branch
 constexpr int PROFILE_RING = 1024;
 
 struct Derived {
@@ -132,6 +135,7 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
   B->tile_nin = (uint32_t *)take(4 * (size_t)d.tiles_cell);
   B->cdf_tile = (unsigned long long *)take(8 * (size_t)d.tiles_norm);
   B->cdf_incl = (unsigned long long *)take(8 * (size_t)d.tiles_norm);
+  B->batch_slot = (unsigned char *)take(1024);
   return (off + 255) & ~(size_t)255;
 }
 
@@ -172,6 +176,10 @@ struct dog_filter {
   cudaEvent_t ev_h2d = nullptr, ev_stage_free = nullptr, ev_snap = nullptr, ev_d2h = nullptr;
   bool d2h_pending = false;
   uint32_t *d2h_err = nullptr;  // pinned host word: error bits of the frame being read back
+  // batched launches: the batch whose view of this filter its workspace slot holds, and a
+  // counter of changes of the launch configuration (sort passes, digit width, count tiles)
+  const void *slot_owner = nullptr;
+  uint32_t cfg_version = 0;
 };
 
 namespace {
@@ -485,21 +493,38 @@ int dog_create(const dog_params *params, void *d_workspace, size_t workspace_byt
 struct dog_batch {
   std::vector<dog_filter *> f;
   cudaStream_t st = nullptr;
-  std::vector<cudaStream_t> side;     // capture-time branch streams, one per filter
-  std::vector<cudaEvent_t> join;      // branch ends
-  cudaEvent_t fork = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  std::vector<BatchFilter> desc;      // each filter's description as captured (host copy)
   std::vector<unsigned char> radar;   // each filter's grid kind when the graph was captured
+  std::vector<uint32_t> cfg_version;  // each filter's configuration version then
+  // grouping: consecutive filters whose workspaces add up to at most group_bytes form one
+  // group (a filter larger than that is a group of its own); each group is one branch of the
+  // graph, its phases fused over its filters
+  size_t group_bytes = 0;
+  std::vector<cudaStream_t> side;     // capture-time branch streams, one per group
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
 };
 
 int dog_batch_create(dog_filter *const *filters, int n, dog_batch **out) {
   if (!filters || !out || n < 1) return DOG_ERR_INVALID_ARG;
+  if (n > BATCH_MAX) return DOG_ERR_UNSUPPORTED;
   for (int i = 0; i < n; ++i)
     if (!filters[i] || !filters[i]->st || filters[i]->profile || filters[i]->st != filters[0]->st)
       return DOG_ERR_INVALID_ARG;
-  dog_batch *b = new dog_batch();
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j)
+      if (filters[i] == filters[j]) return DOG_ERR_INVALID_ARG;
+  // the batched kernels' shared-memory limits (per kernel, as for the single-filter ones)
+  DOG_CUDA(cudaFuncSetAttribute(kb_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sort_smem_bytes(2048)));
+  DOG_CUDA(cudaFuncSetAttribute(kb_sort_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)count_smem_bytes(2048, COUNT_TILES)));
+  dog_batch *b = new (std::nothrow) dog_batch();
+  if (!b) return DOG_ERR_INVALID_ARG;
   b->f.assign(filters, filters + n);
   b->st = filters[0]->st;
+  b->group_bytes = DOG_BATCH_GROUP_BYTES_DEFAULT;
   b->side.assign(n, nullptr);
   b->join.assign(n, nullptr);
   cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
@@ -515,27 +540,161 @@ int dog_batch_create(dog_filter *const *filters, int n, dog_batch **out) {
   return DOG_OK;
 }
 
-// capture one graph whose branch i is filter i's frame (enqueued on a side stream forked
-// from and joined back into the batch stream)
+int dog_batch_set_group_bytes(dog_batch *b, size_t group_bytes) {
+  if (!b) return DOG_ERR_INVALID_ARG;
+  if (group_bytes != b->group_bytes && b->gexec) {
+    cudaGraphExecDestroy(b->gexec);  // captured again at the next step
+    b->gexec = nullptr;
+  }
+  b->group_bytes = group_bytes;
+  return DOG_OK;
+}
+
+int dog_batch_groups(const dog_batch *b, int *n_groups) {
+  if (!b || !n_groups) return DOG_ERR_INVALID_ARG;
+  int g = 0;
+  size_t acc = 0;
+  for (size_t i = 0; i < b->f.size(); ++i) {
+    const size_t w = b->f[i]->ws_bytes;
+    if (i == 0 || acc + w > b->group_bytes) {
+      ++g;
+      acc = 0;
+    }
+    acc += w;
+  }
+  *n_groups = g;
+  return DOG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// the launch arguments of one phase: the filters `take` selects, `blocks` blocks each
+template <typename Take, typename Blocks>
+bool batch_args(const std::vector<dog_filter *> &fs, BatchArgs &A, Take take, Blocks blocks) {
+  A.n = 0;
+  uint32_t tot = 0;
+  for (const dog_filter *f : fs) {
+    if (!take(f)) continue;
+    const uint32_t c = blocks(f);
+    if (c == 0) continue;
+    A.first[A.n] = tot;
+    A.f[A.n] = reinterpret_cast<const BatchFilter *>(f->B.batch_slot);
+    tot += c;
+    ++A.n;
+  }
+  A.first[A.n] = tot;
+  return A.n > 0;
+}
+template <typename Take, typename Bytes>
+size_t batch_smem(const std::vector<dog_filter *> &fs, Take take, Bytes bytes) {
+  size_t m = 0;
+  for (const dog_filter *f : fs)
+    if (take(f) && bytes(f) > m) m = bytes(f);
+  return m;
+}
+
+// one frame of the filters fs on stream st: each phase of the frame once over all of them
+int enqueue_group_frame(const std::vector<dog_filter *> &fs, cudaStream_t st) {
+  const std::vector<dog_filter *> &bf = fs;
+  BatchArgs A;
+  auto all = [](const dog_filter *) { return true; };
+  auto lidar = [](const dog_filter *f) { return !f->radar; };
+  auto radar = [](const dog_filter *f) { return f->radar; };
+  auto one = [](const dog_filter *) { return 1u; };
+  if (batch_args(bf, A, all, one)) kb_tick<<<A.first[A.n], 256, 0, st>>>(A);
+  auto ego = [](const dog_filter *f) { return (f->K.flags & DOG_EGO) != 0; };
+  if (batch_args(bf, A, ego, [](const dog_filter *f) { return std::min((f->K.C + 255) / 256, 592u); }))
+    kb_ego_warp<<<A.first[A.n], 256, 0, st>>>(A);
+  if (batch_args(bf, A, all, [](const dog_filter *f) { return (f->K.nu + PRED_TILE - 1) / PRED_TILE; }))
+    kb_predict<<<A.first[A.n], PRED_BLOCK,
+                 batch_smem(bf, all, [](const dog_filter *f) { return (size_t)4 * f->K.passes * f->K.radix; }),
+                 st>>>(A);
+  int max_passes = 0;
+  for (const dog_filter *f : bf) max_passes = std::max(max_passes, f->K.passes);
+  for (int p = 0; p < max_passes; ++p) {
+    auto has = [p](const dog_filter *f) { return f->K.passes > p; };
+    if (p > 0 && batch_args(bf, A, has, [](const dog_filter *f) {
+          return (f->K.tiles_sort + f->count_ct - 1) / f->count_ct;
+        }))
+      kb_sort_count<<<A.first[A.n], COUNT_BLOCK,
+                      batch_smem(bf, has, [](const dog_filter *f) { return count_smem_bytes(f->K.radix, f->count_ct); }),
+                      st>>>(A, p);
+    if (batch_args(bf, A, has, [](const dog_filter *f) { return f->K.radix; }))
+      kb_sort_offsets<<<A.first[A.n], OFF_BLOCK, 0, st>>>(A, p);
+    if (batch_args(bf, A, has, [](const dog_filter *f) { return f->K.tiles_sort; }))
+      kb_sort_pass<<<A.first[A.n], SORT_BLOCK,
+                     batch_smem(bf, has, [](const dog_filter *f) { return sort_smem_bytes(f->K.radix); }), st>>>(A, p);
+  }
+  auto seg = [](const dog_filter *f) { return f->K.tiles_seg; };
+  auto cell = [](const dog_filter *f) { return f->K.tiles_cell; };
+  auto norm = [](const dog_filter *f) { return f->K.tiles_norm; };
+  auto births = [](const dog_filter *f) { return (uint32_t)f->birth_grid; };
+  if (batch_args(bf, A, lidar, seg)) kb_segsum_lidar<<<A.first[A.n], SEG_BLOCK, 0, st>>>(A);
+  if (batch_args(bf, A, radar, seg)) kb_segsum<true><<<A.first[A.n], SEG_BLOCK, 0, st>>>(A);
+  if (batch_args(bf, A, lidar, cell)) kb_cell<false><<<A.first[A.n], CELL_BLOCK, 0, st>>>(A);
+  if (batch_args(bf, A, radar, cell)) kb_cell<true><<<A.first[A.n], CELL_BLOCK, 0, st>>>(A);
+  if (batch_args(bf, A, all, one)) kb_scan_tiles<false><<<A.first[A.n], SCAN_BLOCK, 0, st>>>(A);
+  if (batch_args(bf, A, lidar, cell)) kb_birth_prep<false><<<A.first[A.n], CELL_BLOCK, 0, st>>>(A);
+  if (batch_args(bf, A, radar, cell)) kb_birth_prep<true><<<A.first[A.n], CELL_BLOCK, 0, st>>>(A);
+  if (batch_args(bf, A, lidar, births)) kb_birth<false><<<A.first[A.n], BIRTH_BLOCK, 0, st>>>(A);
+  if (batch_args(bf, A, radar, births)) kb_birth<true><<<A.first[A.n], BIRTH_BLOCK, 0, st>>>(A);
+  if (batch_args(bf, A, lidar, norm)) kb_normalise_lidar<<<A.first[A.n], NORM_BLOCK, 0, st>>>(A);
+  if (batch_args(bf, A, radar, norm)) kb_normalise_radar<<<A.first[A.n], NORM_BLOCK, 0, st>>>(A);
+  if (batch_args(bf, A, radar, [](const dog_filter *f) { return std::min((f->K.C + 255) / 256, 2368u); }))
+    kb_moments<<<A.first[A.n], 256, 0, st>>>(A);
+  if (batch_args(bf, A, all, one)) kb_scan_tiles<true><<<A.first[A.n], SCAN_BLOCK, 0, st>>>(A);
+  if (batch_args(bf, A, all, norm)) kb_resample<<<A.first[A.n], RES_BLOCK, 0, st>>>(A);
+  return cuda_fail(cudaGetLastError());
+}
+}  // namespace
+
+extern "C" {
+
+// write every filter's description into its slot (in stream order) and capture the frame
 static int batch_capture(dog_batch *b) {
   if (b->gexec) {
     cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
   }
   const int n = (int)b->f.size();
+  b->desc.resize(n);
+  b->radar.resize(n);
+  b->cfg_version.resize(n);
+  for (int i = 0; i < n; ++i) {
+    dog_filter *f = b->f[i];
+    BatchFilter &d = b->desc[i];
+    std::memset(&d, 0, sizeof(d));
+    d.P = f->K;
+    d.B = f->B;
+    d.count_ct = f->count_ct;
+    d.birth_grid = (uint32_t)f->birth_grid;
+    DOG_CUDA(cudaMemcpyAsync(f->B.batch_slot, &d, sizeof(BatchFilter), cudaMemcpyHostToDevice, b->st));
+    f->slot_owner = b;
+    b->radar[i] = f->radar ? 1 : 0;
+    b->cfg_version[i] = f->cfg_version;
+  }
   DOG_CUDA(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
   int rc = cuda_fail(cudaEventRecord(b->fork, b->st));
-  for (int i = 0; i < n && rc == DOG_OK; ++i) {
-    dog_filter *f = b->f[i];
-    rc = cuda_fail(cudaStreamWaitEvent(b->side[i], b->fork, 0));
+  size_t i0 = 0;
+  for (int g = 0; rc == DOG_OK && i0 < b->f.size(); ++g) {
+    size_t i1 = i0 + 1, acc = b->f[i0]->ws_bytes;
+    while (i1 < b->f.size() && acc + b->f[i1]->ws_bytes <= b->group_bytes) acc += b->f[i1++]->ws_bytes;
+    rc = cuda_fail(cudaStreamWaitEvent(b->side[g], b->fork, 0));
     if (rc) break;
-    cudaStream_t own = f->st;
-    f->st = b->side[i];
-    rc = enqueue_frame(f, f->radar, nullptr);
-    f->st = own;
-    if (rc) break;
-    rc = cuda_fail(cudaEventRecord(b->join[i], b->side[i]));
-    if (rc == DOG_OK) rc = cuda_fail(cudaStreamWaitEvent(b->st, b->join[i], 0));
+    if (i1 == i0 + 1) {  // a group of one filter: its own kernels
+      dog_filter *f = b->f[i0];
+      cudaStream_t own = f->st;
+      f->st = b->side[g];
+      rc = enqueue_frame(f, f->radar, nullptr);
+      f->st = own;
+    } else {
+      const std::vector<dog_filter *> grp(b->f.begin() + i0, b->f.begin() + i1);
+      rc = enqueue_group_frame(grp, b->side[g]);
+    }
+    if (rc == DOG_OK) rc = cuda_fail(cudaEventRecord(b->join[g], b->side[g]));
+    if (rc == DOG_OK) rc = cuda_fail(cudaStreamWaitEvent(b->st, b->join[g], 0));
+    i0 = i1;
   }
   cudaGraph_t graph = nullptr;
   const cudaError_t e = cudaStreamEndCapture(b->st, &graph);
@@ -547,8 +706,6 @@ static int batch_capture(dog_batch *b) {
   const cudaError_t e2 = cudaGraphInstantiate(&b->gexec, graph, 0);
   cudaGraphDestroy(graph);
   DOG_CUDA(e2);
-  b->radar.resize(n);
-  for (int i = 0; i < n; ++i) b->radar[i] = b->f[i]->radar ? 1 : 0;
   return DOG_OK;
 }
 
@@ -559,8 +716,13 @@ int dog_batch_step(dog_batch *b, const float *dt) {
     if (!(dt[i] >= 0.0f) || !std::isfinite(dt[i])) return DOG_ERR_INVALID_ARG;
     if (!b->f[i]->has_grid) return DOG_ERR_BAD_STATE;
   }
+  // captured again when a filter's grid kind or launch configuration changed, or another
+  // batch wrote its slot since
   bool recapture = !b->gexec;
-  for (int i = 0; i < n && !recapture; ++i) recapture = b->radar[i] != (b->f[i]->radar ? 1 : 0);
+  for (int i = 0; i < n && !recapture; ++i) {
+    const dog_filter *f = b->f[i];
+    recapture = b->radar[i] != (f->radar ? 1 : 0) || b->cfg_version[i] != f->cfg_version || f->slot_owner != b;
+  }
   for (int i = 0; i < n; ++i) {  // time steps that changed, in stream order before the frame
     dog_filter *f = b->f[i];
     if (!f->dt_valid || dt[i] != f->dt) {
@@ -583,6 +745,54 @@ int dog_batch_step(dog_batch *b, const float *dt) {
   return DOG_OK;
 }
 
+int dog_batch_autotune(dog_batch *b, const float *dt, int frames, size_t *chosen) {
+  if (!b || !dt || frames < 1) return DOG_ERR_INVALID_ARG;
+  // candidate groupings, from one filter per branch to the whole batch in one group
+  const size_t cand[] = {0, (size_t)64 << 20, (size_t)256 << 20, (size_t)1 << 30, (size_t)4 << 30,
+                         ~(size_t)0};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  DOG_CUDA(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(ce);
+  }
+  size_t best = b->group_bytes;
+  float best_ms = 3.0e38f;
+  int rc = DOG_OK;
+  int last_groups = -1;
+  for (size_t c : cand) {
+    rc = dog_batch_set_group_bytes(b, c);
+    int ng = 0;
+    if (rc == DOG_OK) rc = dog_batch_groups(b, &ng);
+    if (rc) break;
+    if (ng == last_groups) continue;  // the same grouping as the candidate before
+    last_groups = ng;
+    rc = dog_batch_step(b, dt);  // captures the graph of this grouping
+    float ms = 3.0e38f;
+    for (int k = 0; k < frames && rc == DOG_OK; ++k) {
+      ce = cudaEventRecord(e0, b->st);
+      if (ce == cudaSuccess) rc = dog_batch_step(b, dt);
+      if (rc == DOG_OK && ce == cudaSuccess) ce = cudaEventRecord(e1, b->st);
+      if (rc == DOG_OK && ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+      float t = 0.0f;
+      if (rc == DOG_OK && ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+      if (ce != cudaSuccess) rc = cuda_fail(ce);
+      if (t < ms) ms = t;
+    }
+    if (rc) break;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (chosen) *chosen = best;
+  return dog_batch_set_group_bytes(b, best);
+}
+
 void dog_batch_destroy(dog_batch *b) {
   if (!b) return;
   if (b->st) cudaStreamSynchronize(b->st);
@@ -592,6 +802,8 @@ void dog_batch_destroy(dog_batch *b) {
   for (auto x : b->join)
     if (x) cudaEventDestroy(x);
   if (b->fork) cudaEventDestroy(b->fork);
+  for (dog_filter *f : b->f)
+    if (f->slot_owner == b) f->slot_owner = nullptr;
   delete b;
 }
 
@@ -1169,6 +1381,7 @@ void set_sort_cfg(dog_filter *f, int passes, uint32_t ct) {
   f->K.radix = 1u << dbits;
   f->count_ct = ct;
   f->nk = 9 + 3 * passes;
+  f->cfg_version += 1;  // batches holding the filter capture again
   for (auto &g : f->gexec)  // the next step captures the frame again
     if (g) {
       cudaGraphExecDestroy(g);

@@ -124,6 +124,7 @@ struct DevBufs {
   unsigned long long *tile_q, *tile_qin;  // [tiles_cell] newborn mass per tile, inclusive
   uint32_t *tile_n, *tile_nin;             // [tiles_cell] birth cells per tile, inclusive
   unsigned long long *cdf_tile, *cdf_incl; // [tiles_norm] joint weight per tile, inclusive
+  unsigned char *batch_slot;       // [1024] the filter's description for batched launches
 };
 
 __device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) {

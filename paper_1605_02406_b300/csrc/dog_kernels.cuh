@@ -28,10 +28,11 @@ namespace dog {
 // ====================================================================================
 // k_tick: begin a frame
 // ====================================================================================
-__global__ void k_tick(DevBufs B, int n_hist) {
+__device__ __forceinline__ void tick_body(const DevBufs &B, int n_hist) {
   for (int i = threadIdx.x; i < n_hist; i += blockDim.x) B.hist[i] = 0u;
   if (threadIdx.x == 0) B.ctl->frame += 1u;
 }
+__global__ void k_tick(DevBufs B, int n_hist) { tick_body(B, n_hist); }
 
 // ====================================================================================
 // k_init: initial state -- particles uniform over the grid, birth-distribution
@@ -225,13 +226,13 @@ __device__ __forceinline__ void ego_transform(const KParams &P, const Ego &E, fl
   st.w = __fsub_rn(__fmul_rn(E.c, vy), __fmul_rn(E.s, vx));
 }
 
-__global__ void k_ego_warp(KParams P, DevBufs B) {
+__device__ __forceinline__ void ego_warp_body(const KParams &P, const DevBufs &B, uint32_t blk, uint32_t nblk) {
   const DevCtl *ctl = B.ctl;
   const bool on = ctl->ego_on != 0u;
   const Ego E{ctl->ego_c, ctl->ego_s, ctl->ego_dx, ctl->ego_dy};
-  const uint32_t stride = gridDim.x * blockDim.x;
+  const uint32_t stride = nblk * blockDim.x;
   const float Wf = (float)P.W, Hf = (float)P.H;
-  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < P.C; c += stride) {
+  for (uint32_t c = blk * blockDim.x + threadIdx.x; c < P.C; c += stride) {
     float v;
     if (!on) {
       v = B.mF[c];
@@ -248,6 +249,7 @@ __global__ void k_ego_warp(KParams P, DevBufs B) {
     B.mF_warp[c] = v;
   }
 }
+__global__ void k_ego_warp(KParams P, DevBufs B) { ego_warp_body(P, B, blockIdx.x, gridDim.x); }
 
 // ====================================================================================
 // k_predict (Alg. 1): Eq. process with per-frame Gaussian noise, Eq. particle_persistence,
@@ -283,7 +285,7 @@ __device__ __forceinline__ void predict_one(const KParams &P, const PhiloxKeys &
   if (!in) key |= OUT_OF_GRID;
 }
 
-__global__ void __launch_bounds__(PRED_BLOCK) k_predict(KParams P, DevBufs B) {
+__device__ __forceinline__ void predict_body(const KParams &P, const DevBufs &B, uint32_t blk) {
   extern __shared__ uint32_t sh_hist[];  // [passes][radix]
   const uint32_t nh = (uint32_t)P.passes * P.radix;
   for (uint32_t k = threadIdx.x; k < nh; k += PRED_BLOCK) sh_hist[k] = 0u;
@@ -297,7 +299,7 @@ __global__ void __launch_bounds__(PRED_BLOCK) k_predict(KParams P, DevBufs B) {
   const Ego E{B.ctl->ego_c, B.ctl->ego_s, B.ctl->ego_dx, B.ctl->ego_dy};
   const PhiloxKeys PK = philox_keys(P.seed_lo, P.seed_hi);
   for (int rnd = 0; rnd < PRED_ROUNDS; ++rnd) {
-    const uint32_t i0 = blockIdx.x * PRED_TILE + (uint32_t)rnd * (PRED_BLOCK * 4) + threadIdx.x * 4;
+    const uint32_t i0 = blk * PRED_TILE + (uint32_t)rnd * (PRED_BLOCK * 4) + threadIdx.x * 4;
     uint32_t key[4];
     bool valid[4];
     if (i0 + 4 <= P.nu) {
@@ -370,10 +372,11 @@ __global__ void __launch_bounds__(PRED_BLOCK) k_predict(KParams P, DevBufs B) {
     const uint32_t v = sh_hist[k];
     if (v) atomicAdd(&B.hist[(k / P.radix) * 2048u + (k % P.radix)], v);
   }
-  // this block's keys are tile blockIdx.x of the first sort pass: its first-pass digit counts
+  // this block's keys are tile blk of the first sort pass: its first-pass digit counts
   for (uint32_t d = threadIdx.x; d < P.radix; d += PRED_BLOCK)
-    B.dcnt[(size_t)d * P.tiles_sort + blockIdx.x] = sh_hist[d];
+    B.dcnt[(size_t)d * P.tiles_sort + blk] = sh_hist[d];
 }
+__global__ void __launch_bounds__(PRED_BLOCK) k_predict(KParams P, DevBufs B) { predict_body(P, B, blockIdx.x); }
 
 // ====================================================================================
 // Sort (Alg. 2): LSD radix sort of (cell index, particle index) pairs on digits of up to 11
@@ -453,15 +456,14 @@ inline uint32_t count_tiles_per_block(uint32_t tiles, int sms) {
   return ct;
 }
 
-__global__ void __launch_bounds__(COUNT_BLOCK) k_sort_count(KParams P, DevBufs B,
-                                                            const uint32_t *__restrict__ keys, int pass,
-                                                            uint32_t ct) {
+__device__ __forceinline__ void sort_count_body(const KParams &P, const DevBufs &B, const uint32_t *__restrict__ keys,
+                                                int pass, uint32_t ct, uint32_t blk) {
   extern __shared__ uint32_t sh_cnt[];  // [ct][radix]
   const uint32_t radix = P.radix, mask = radix - 1u;
   const int shift = pass * P.dbits;
   for (uint32_t k = threadIdx.x; k < ct * radix; k += COUNT_BLOCK) sh_cnt[k] = 0u;
   __syncthreads();
-  const uint32_t t0 = blockIdx.x * ct;
+  const uint32_t t0 = blk * ct;
   const uint32_t base = t0 * SORT_TILE;
   const uint32_t end = min(base + ct * SORT_TILE, P.nu);
   // four consecutive keys per thread and access (the same tile: SORT_TILE % 4 == 0), four
@@ -504,7 +506,7 @@ __global__ void __launch_bounds__(COUNT_BLOCK) k_sort_count(KParams P, DevBufs B
   uint32_t *col = B.dcnt + (size_t)pass * radix * P.tiles_sort;
   const uint32_t nt = min(ct, P.tiles_sort - t0);
   // rows start on 16-byte (8-byte) boundaries when tiles_sort is a multiple of 4 (2), and so
-  // does this block's run t0 = blockIdx.x * ct
+  // does this block's run t0 = blk * ct
   const bool v4 = nt == ct && ct % 4u == 0u && P.tiles_sort % 4u == 0u;
   const bool v2 = nt == ct && ct == 2u && P.tiles_sort % 2u == 0u;
   for (uint32_t d = threadIdx.x; d < radix; d += COUNT_BLOCK) {
@@ -520,6 +522,11 @@ __global__ void __launch_bounds__(COUNT_BLOCK) k_sort_count(KParams P, DevBufs B
     }
   }
 }
+__global__ void __launch_bounds__(COUNT_BLOCK) k_sort_count(KParams P, DevBufs B,
+                                                            const uint32_t *__restrict__ keys, int pass,
+                                                            uint32_t ct) {
+  sort_count_body(P, B, keys, pass, ct, blockIdx.x);
+}
 
 // k_sort_offsets: for one pass, counts[d][t] -> (sum of the histogram below digit d) +
 // sum_{t' < t} counts[d][t'], in place.  One block per digit; thread k owns a contiguous run
@@ -527,10 +534,10 @@ __global__ void __launch_bounds__(COUNT_BLOCK) k_sort_count(KParams P, DevBufs B
 // block scans the runs' totals.
 constexpr int OFF_BLOCK = 256, OFF_WARPS = OFF_BLOCK / 32, OFF_PER = 16;
 
-__global__ void __launch_bounds__(OFF_BLOCK) k_sort_offsets(KParams P, DevBufs B, int pass) {
+__device__ __forceinline__ void sort_offsets_body(const KParams &P, const DevBufs &B, int pass, uint32_t blk) {
   __shared__ uint32_t s_h[OFF_WARPS], s_t[OFF_WARPS];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t d = blockIdx.x;
+  const uint32_t d = blk;
   const uint32_t T = P.tiles_sort;
   const uint32_t *hist = B.hist + pass * 2048u;
   uint32_t *M = B.dcnt + ((size_t)pass * P.radix + d) * T;
@@ -615,11 +622,13 @@ __global__ void __launch_bounds__(OFF_BLOCK) k_sort_offsets(KParams P, DevBufs B
     }
   }
 }
+__global__ void __launch_bounds__(OFF_BLOCK) k_sort_offsets(KParams P, DevBufs B, int pass) {
+  sort_offsets_body(P, B, pass, blockIdx.x);
+}
 
-__global__ void __launch_bounds__(SORT_BLOCK, 2)
-    k_sort_pass(KParams P, DevBufs B, const uint32_t *__restrict__ keys_in,
-                const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
-                uint32_t *__restrict__ vals_out, int pass) {
+__device__ __forceinline__ void sort_pass_body(const KParams &P, const DevBufs &B, const uint32_t *__restrict__ keys_in,
+                                               const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
+                                               uint32_t *__restrict__ vals_out, int pass, uint32_t blk) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t radix = P.radix;
   const size_t big = sort_smem_bytes(radix) - (size_t)3 * radix * 4 - 128;
@@ -631,7 +640,7 @@ __global__ void __launch_bounds__(SORT_BLOCK, 2)
   uint32_t *s_misc = s_base + radix;  // [32]: warp sums
 
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t tile = blockIdx.x;
+  const uint32_t tile = blk;
   const int shift = pass * P.dbits;
   const uint32_t mask = radix - 1u;
   // global output offset of this tile's digits (radix <= 2048)
@@ -730,6 +739,12 @@ __global__ void __launch_bounds__(SORT_BLOCK, 2)
       vals_out[gp] = kv.y;
     }
   }
+}
+__global__ void __launch_bounds__(SORT_BLOCK, 2)
+    k_sort_pass(KParams P, DevBufs B, const uint32_t *__restrict__ keys_in,
+                const uint32_t *__restrict__ vals_in, uint32_t *__restrict__ keys_out,
+                uint32_t *__restrict__ vals_out, int pass) {
+  sort_pass_body(P, B, keys_in, vals_in, keys_out, vals_out, pass, blockIdx.x);
 }
 
 // ====================================================================================
@@ -997,11 +1012,11 @@ __device__ __forceinline__ void cmom_load(const CellMom *r, DF (&m)[5]) {
 // through shared memory.  The radar filter also leaves each particle's likelihood g in wn
 // (sorted order), where k_normalise reads it before it writes the normalised weight.
 template <bool RADAR>
-__global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
+__device__ __forceinline__ void segsum_body(const KParams &P, const DevBufs &B, uint32_t blk) {
   constexpr int N = RADAR ? 2 : 1;
   __shared__ Seg<N> s_w[SEG_BLOCK / 32 + 1];
   __shared__ unsigned long long s_q[N][SEG_PADDED];
-  const uint32_t tile = blockIdx.x, frame = B.ctl->frame;
+  const uint32_t tile = blk, frame = B.ctl->frame;
   const uint32_t base = tile * SEG_TILE;
   const uint32_t last_valid = min(base + SEG_TILE, P.nu) - 1u;
   // gather phase, warp-striped: position base + it*256 + threadIdx.x.  All permutation
@@ -1116,6 +1131,10 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
     }
   }
 }
+template <bool RADAR>
+__global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
+  segsum_body<RADAR>(P, B, blockIdx.x);
+}
 
 // k_segsum_lidar: k_segsum for a filter without radar likelihood (g == 1), which also sums
 // the velocity moment terms of Eq. mean_x, var_x, covar_xy.  With g == 1 the normalised
@@ -1127,10 +1146,10 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
 // over tiles adds the pieces of S in exact 2^-40 fixed point and leaves its double-float
 // moment pieces in per-tile slots, which k_cell adds in tile order.  k_cell applies the
 // factor mu_UA / rho_p.
-__global__ void __launch_bounds__(SEG_BLOCK, 5) k_segsum_lidar(KParams P, DevBufs B) {
+__device__ __forceinline__ void segsum_lidar_body(const KParams &P, const DevBufs &B, uint32_t blk) {
   __shared__ SegQM s_wqm[SEG_BLOCK / 32 + 1];
   __shared__ float s_x[3][SEG_PADDED];  // w, vx, vy in tile order (padded)
-  const uint32_t tile = blockIdx.x, frame = B.ctl->frame;
+  const uint32_t tile = blk, frame = B.ctl->frame;
   const uint32_t base = tile * SEG_TILE;
   const uint32_t last_valid = min(base + SEG_TILE, P.nu) - 1u;
   // gather phase, warp-striped, all loads in flight before the stores.  After a resampled
@@ -1246,6 +1265,9 @@ __global__ void __launch_bounds__(SEG_BLOCK, 5) k_segsum_lidar(KParams P, DevBuf
     }
   }
 }
+__global__ void __launch_bounds__(SEG_BLOCK, 5) k_segsum_lidar(KParams P, DevBufs B) {
+  segsum_lidar_body(P, B, blockIdx.x);
+}
 
 // ====================================================================================
 // k_scan_tiles: inclusive prefix sums of per-tile totals (one block); the grand totals go
@@ -1341,10 +1363,10 @@ __device__ __forceinline__ uint32_t count_theta_below(const Theta &T, unsigned l
 }
 
 template <bool SETUP>
-__global__ void __launch_bounds__(SCAN_BLOCK)
-    k_scan_tiles(const unsigned long long *__restrict__ q, const uint32_t *__restrict__ n, uint32_t count,
-                 unsigned long long *q_incl, uint32_t *n_incl, unsigned long long *q_total,
-                 uint32_t *n_total, KParams P, DevCtl *ctl) {
+__device__ __forceinline__ void scan_tiles_body(const unsigned long long *__restrict__ q, const uint32_t *__restrict__ n,
+                                                uint32_t count, unsigned long long *q_incl, uint32_t *n_incl,
+                                                unsigned long long *q_total, uint32_t *n_total, const KParams &P,
+                                                DevCtl *ctl) {
   __shared__ unsigned long long s_q[SCAN_BLOCK / 32];
   __shared__ uint32_t s_n[SCAN_BLOCK / 32];
   const uint32_t per = (count + SCAN_BLOCK - 1) / SCAN_BLOCK;
@@ -1401,6 +1423,13 @@ __global__ void __launch_bounds__(SCAN_BLOCK)
       }
     }
 }
+template <bool SETUP>
+__global__ void __launch_bounds__(SCAN_BLOCK)
+    k_scan_tiles(const unsigned long long *__restrict__ q, const uint32_t *__restrict__ n, uint32_t count,
+                 unsigned long long *q_incl, uint32_t *n_incl, unsigned long long *q_total,
+                 uint32_t *n_total, KParams P, DevCtl *ctl) {
+  scan_tiles_body<SETUP>(q, n, count, q_incl, n_incl, q_total, n_total, P, ctl);
+}
 
 // ====================================================================================
 // k_cell (Alg. 3 + the cell half of Alg. 4): per cell the predicted occupied mass
@@ -1437,10 +1466,10 @@ __device__ __forceinline__ void cell_update(const KParams &P, float mp, float mF
 }
 
 template <bool RADAR>
-__global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
+__device__ __forceinline__ void cell_body(const KParams &P, const DevBufs &B, uint32_t blk) {
   __shared__ unsigned long long s_wq[CELL_BLOCK / 32 + 1];
   __shared__ uint32_t s_wn[CELL_BLOCK / 32 + 1];
-  const uint32_t tile = blockIdx.x, frame = B.ctl->frame;
+  const uint32_t tile = blk, frame = B.ctl->frame;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned long long qin[CELL_ITEMS];
   uint32_t nex[CELL_ITEMS];
@@ -1625,6 +1654,10 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
     }
   }
 }
+template <bool RADAR>
+__global__ void __launch_bounds__(CELL_BLOCK) k_cell(KParams P, DevBufs B) {
+  cell_body<RADAR>(P, B, blockIdx.x);
+}
 
 // ====================================================================================
 // k_birth (Alg. 5): cell c owns the newborn slots [floor(nu_b R_{c-1}/R), floor(nu_b R_c/R))
@@ -1677,10 +1710,10 @@ __device__ __forceinline__ void birth_init(const KParams &P, const DevBufs &B, u
 constexpr int BIRTH_SLOTS = 512, BIRTH_CACHE = 2048;
 
 template <bool RADAR>
-__global__ void __launch_bounds__(CELL_BLOCK) k_birth_prep(KParams P, DevBufs B) {
+__device__ __forceinline__ void birth_prep_body(const KParams &P, const DevBufs &B, uint32_t blk) {
   const unsigned long long R = B.ctl->R_total;
   if (R == 0ull) return;
-  const uint32_t T = blockIdx.x;
+  const uint32_t T = blk;
   const unsigned long long Tex = T > 0u ? B.tile_qin[T - 1u] : 0ull;
   const uint32_t G0 = T > 0u ? B.tile_nin[T - 1u] : 0u;
   if (T == P.tiles_cell - 1u && threadIdx.x == 0) B.bl_first[B.tile_nin[T]] = P.nu_b;  // sentinel
@@ -1718,6 +1751,10 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_birth_prep(KParams P, DevBufs B)
       B.birth_block_entry[blk] = G;
   }
 }
+template <bool RADAR>
+__global__ void __launch_bounds__(CELL_BLOCK) k_birth_prep(KParams P, DevBufs B) {
+  birth_prep_body<RADAR>(P, B, blockIdx.x);
+}
 
 // k_birth: a block makes the newborns of BIRTH_SLOTS consecutive slots.  Its slots belong to
 // the entries from the one owning its first slot to the one owning the next block's first
@@ -1725,12 +1762,12 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_birth_prep(KParams P, DevBufs B)
 // and each slot finds its entry (the last one whose first slot is <= the slot) by bisection
 // there.
 template <bool RADAR>
-__global__ void __launch_bounds__(BIRTH_BLOCK) k_birth(KParams P, DevBufs B) {
+__device__ __forceinline__ void birth_body(const KParams &P, const DevBufs &B, uint32_t blk) {
   __shared__ uint32_t s_first[BIRTH_CACHE + 1];
   const uint32_t frame = B.ctl->frame;
   const unsigned long long R = B.ctl->R_total;
   const bool record = (P.flags & 0x4u) != 0u;
-  const uint32_t s0 = blockIdx.x * BIRTH_SLOTS;
+  const uint32_t s0 = blk * BIRTH_SLOTS;
   const uint32_t s1 = min(s0 + BIRTH_SLOTS, P.nu_b);
   if (s0 >= s1) return;  // block-uniform (no newborn slots at all)
   if (R == 0ull) {
@@ -1740,8 +1777,8 @@ __global__ void __launch_bounds__(BIRTH_BLOCK) k_birth(KParams P, DevBufs B) {
     return;
   }
   const uint32_t nE = B.ctl->n_birth_cells;
-  const uint32_t G0 = B.birth_block_entry[blockIdx.x];
-  const uint32_t Glast = s1 < P.nu_b ? B.birth_block_entry[blockIdx.x + 1] : nE - 1u;
+  const uint32_t G0 = B.birth_block_entry[blk];
+  const uint32_t Glast = s1 < P.nu_b ? B.birth_block_entry[blk + 1] : nE - 1u;
   // entries G0 .. G0 + ncache - 1, and bl_first[G0 + ncache] (<= the sentinel at nE) after them
   const uint32_t ncache = min((uint32_t)BIRTH_CACHE, Glast - G0 + 1u);
   for (uint32_t k = threadIdx.x; k <= ncache; k += BIRTH_BLOCK) s_first[k] = __ldg(B.bl_first + G0 + k);
@@ -1797,6 +1834,10 @@ __global__ void __launch_bounds__(BIRTH_BLOCK) k_birth(KParams P, DevBufs B) {
     if (s < s1) birth_init(P, B, s, cell[r], assoc[r], wb[r], zv[r], sg[r], frame, record);
   }
 }
+template <bool RADAR>
+__global__ void __launch_bounds__(BIRTH_BLOCK) k_birth(KParams P, DevBufs B) {
+  birth_body<RADAR>(P, B, blockIdx.x);
+}
 
 // ====================================================================================
 // k_normalise (Alg. 4 / Alg. 6): over the joint source index space (persistent particles
@@ -1818,11 +1859,11 @@ __device__ __forceinline__ uint32_t norm_pad(uint32_t m) { return m + m / NORM_I
 constexpr int NORM_PADDED = NORM_TILE + NORM_TILE / NORM_ITEMS;
 
 template <bool RADAR>
-__global__ void __launch_bounds__(NORM_BLOCK, 4) k_normalise(KParams P, DevBufs B) {
+__device__ __forceinline__ void normalise_body(const KParams &P, const DevBufs &B, uint32_t blk) {
   __shared__ SegMom s_w[NORM_BLOCK / 32 + 1];
   __shared__ unsigned long long s_red[NORM_BLOCK / 32];
   __shared__ float s_t[3][NORM_PADDED];  // w', vx, vy of the tile's items, for the tail pass
-  const uint32_t tile = blockIdx.x;
+  const uint32_t tile = blk;
   const uint32_t ntot = P.nu + P.nu_b;
   const uint32_t j0 = tile * NORM_TILE + threadIdx.x * NORM_ITEMS;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1946,15 +1987,19 @@ __global__ void __launch_bounds__(NORM_BLOCK, 4) k_normalise(KParams P, DevBufs 
     }
   }
 }
+template <bool RADAR>
+__global__ void __launch_bounds__(NORM_BLOCK, 4) k_normalise(KParams P, DevBufs B) {
+  normalise_body<RADAR>(P, B, blockIdx.x);
+}
 
 // k_moments (radar filter, after k_normalise): the velocity moments of every cell with
 // particles this frame from its compensated sums of w' v, ... divided by rho_p (a cell
 // inside one normalisation tile) or from its exact fixed-point pieces (a cell spread over
 // several; read and cleared for the next frame); 0 where rho_p = 0.
-__global__ void __launch_bounds__(256) k_moments(KParams P, DevBufs B) {
+__device__ __forceinline__ void moments_body(const KParams &P, const DevBufs &B, uint32_t blk, uint32_t nblk) {
   const uint32_t frame = B.ctl->frame;
   const size_t Cs = P.C;
-  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < P.C; c += gridDim.x * blockDim.x) {
+  for (uint32_t c = blk * blockDim.x + threadIdx.x; c < P.C; c += nblk * blockDim.x) {
     const uint32_t tag = B.csum[c].tag;
     if ((tag >> 1) != frame || frame == 0u) continue;  // no particles: zeros from k_cell
     const uint32_t a = B.cstart[c], e = B.cend[c];
@@ -1976,13 +2021,14 @@ __global__ void __launch_bounds__(256) k_moments(KParams P, DevBufs B) {
     moments_store(B, c, o);
   }
 }
+__global__ void __launch_bounds__(256) k_moments(KParams P, DevBufs B) { moments_body(P, B, blockIdx.x, gridDim.x); }
 
 // k_normalise_lidar: the lidar filter's normalisation (Eq. DSnormalization with g == 1:
 // w' = mu_UA w, Alg. 4) and the tile sums of the joint quantised weights; its moments
 // were summed in k_segsum_lidar.
-__global__ void __launch_bounds__(NORM_BLOCK) k_normalise_lidar(KParams P, DevBufs B) {
+__device__ __forceinline__ void normalise_lidar_body(const KParams &P, const DevBufs &B, uint32_t blk) {
   __shared__ unsigned long long s_red[NORM_BLOCK / 32];
-  const uint32_t tile = blockIdx.x;
+  const uint32_t tile = blk;
   const uint32_t ntot = P.nu + P.nu_b;
   const uint32_t j0 = tile * NORM_TILE + threadIdx.x * NORM_ITEMS;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -2017,6 +2063,9 @@ __global__ void __launch_bounds__(NORM_BLOCK) k_normalise_lidar(KParams P, DevBu
     for (int w = 0; w < NORM_BLOCK / 32; ++w) tsum += s_red[w];
     B.cdf_tile[tile] = tsum;
   }
+}
+__global__ void __launch_bounds__(NORM_BLOCK) k_normalise_lidar(KParams P, DevBufs B) {
+  normalise_lidar_body(P, B, blockIdx.x);
 }
 
 // ====================================================================================
@@ -2075,11 +2124,11 @@ __device__ __forceinline__ uint32_t first_above_tile(const unsigned long long *Q
   return y;
 }
 
-__global__ void __launch_bounds__(RES_BLOCK, 2) k_resample(KParams P, DevBufs B) {
+__device__ __forceinline__ void resample_body(const KParams &P, const DevBufs &B, uint32_t blk) {
   __shared__ unsigned long long s_Q[NORM_TILE];  // inclusive CDF at each source of the tile
   __shared__ unsigned long long s_wsum[RES_BLOCK / 32];
   __shared__ uint32_t s_o[2];
-  const uint32_t tile = blockIdx.x;
+  const uint32_t tile = blk;
   const uint32_t base = tile * NORM_TILE, ntot = P.nu + P.nu_b;
   const unsigned long long Wt = B.ctl->W_total;
   if ((P.flags & 0x2u) != 0u || Wt == 0ull) {
@@ -2163,6 +2212,9 @@ __global__ void __launch_bounds__(RES_BLOCK, 2) k_resample(KParams P, DevBufs B)
       B.Bsrc[x] = base + y;
     }
   }
+}
+__global__ void __launch_bounds__(RES_BLOCK, 3) k_resample(KParams P, DevBufs B) {
+  resample_body(P, B, blockIdx.x);
 }
 
 }  // namespace dog

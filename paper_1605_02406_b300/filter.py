@@ -162,6 +162,19 @@ class DogBatch:
             dts = [dts] * len(self.filters)
         N.dog_batch_step(self.h, dts)
 
+    def autotune(self, dts, frames: int = 2) -> dict:
+        """Time the candidate groupings on real frames (each advances every filter) and keep
+        the fastest; returns the choice."""
+        if not hasattr(dts, "__len__"):
+            dts = [dts] * len(self.filters)
+        gb = N.dog_batch_autotune(self.h, dts, frames)
+        return {"group_bytes": gb, "groups": N.dog_batch_groups(self.h)}
+
+    def set_group_bytes(self, group_bytes: int) -> int:
+        """Group consecutive filters up to group_bytes of workspace; returns the groups."""
+        N.dog_batch_set_group_bytes(self.h, group_bytes)
+        return N.dog_batch_groups(self.h)
+
     def close(self):
         if getattr(self, "h", None):
             N.dog_batch_destroy(self.h)

@@ -32,7 +32,8 @@ SYMBOLS = ["dog_workspace_bytes", "dog_create", "dog_set_measurement_grid", "dog
            "dog_assign_cells_noalloc", "dog_batch_create", "dog_batch_step", "dog_batch_destroy",
            "dog_last_cuda_error", "dog_eval_clusters", "dog_eval_mahalanobis",
            "dog_get_cells_async", "dog_wait_cells", "dog_set_ego_motion", "dog_set_bernoulli_grid",
-           "dog_autotune", "dog_set_sort_config", "dog_sort_config"]
+           "dog_autotune", "dog_set_sort_config", "dog_sort_config", "dog_batch_set_group_bytes",
+           "dog_batch_groups", "dog_batch_autotune"]
 DOG_NOALLOC_MAX_PARTICLES, DOG_NOALLOC_MAX_CELLS = 1 << 19, (1 << 22) - 1
 
 
@@ -115,6 +116,9 @@ def lib() -> C.CDLL:
         L.dog_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp)]
         L.dog_batch_step.argtypes = [vp, C.POINTER(C.c_float)]
         L.dog_batch_destroy.argtypes = [vp]
+        L.dog_batch_set_group_bytes.argtypes = [vp, C.c_size_t]
+        L.dog_batch_groups.argtypes = [vp, C.POINTER(C.c_int)]
+        L.dog_batch_autotune.argtypes = [vp, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_size_t)]
         L.dog_batch_destroy.restype = None
         L.dog_last_cuda_error.argtypes = []
         L.dog_eval_clusters.argtypes = [vp, vp, C.c_uint32, vp, vp]
@@ -258,6 +262,23 @@ def dog_batch_create(handles: list) -> int:
 def dog_batch_step(b: int, dts) -> None:
     arr = (C.c_float * len(dts))(*[float(x) for x in dts])
     check("dog_batch_step", lib().dog_batch_step(b, arr))
+
+
+def dog_batch_set_group_bytes(b: int, group_bytes: int) -> None:
+    check("dog_batch_set_group_bytes", lib().dog_batch_set_group_bytes(b, int(group_bytes)))
+
+
+def dog_batch_groups(b: int) -> int:
+    n = C.c_int()
+    check("dog_batch_groups", lib().dog_batch_groups(b, C.byref(n)))
+    return n.value
+
+
+def dog_batch_autotune(b: int, dts, frames: int) -> int:
+    arr = (C.c_float * len(dts))(*[float(x) for x in dts])
+    chosen = C.c_size_t()
+    check("dog_batch_autotune", lib().dog_batch_autotune(b, arr, int(frames), C.byref(chosen)))
+    return chosen.value
 
 
 def dog_batch_destroy(b: int) -> None:

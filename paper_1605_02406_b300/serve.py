@@ -93,16 +93,19 @@ def admit(cfgs: list, budget_bytes: float, rank: int = 0, world: int = 1) -> tup
 
 
 def run(n_streams: int = 256, seconds: float = 3.0, budget_gb: float = 120.0, seed: int = 7,
-        warm_frames: int = 2, rank: int = 0, world: int = 1) -> dict:
+        warm_frames: int = 2, rank: int = 0, world: int = 1, plain: bool = False) -> dict:
     """One rank's share of the serving workload (all of it on one rank); budget_gb is per
     rank.  Besides the rates and latency percentiles, returns the raw counts (updates, the
-    last completion) from which several ranks' results combine."""
+    last completion) from which several ranks' results combine.  plain=True is the plain
+    per-grid loop on the same streams and arrivals: every filter on one CUDA stream, so the
+    requests run one at a time in arrival order (the queue's wait counts in the latency)."""
     cfgs = scene.serving_stream_configs(n_streams)
     admitted, rejected, used = admit(cfgs, budget_gb * 1e9, rank, world)
     rng = np.random.default_rng(seed + rank)
     filters, grids = [], []
+    one = torch.cuda.Stream() if plain else None
     for c in admitted:
-        f = DogFilter(scene.filter_params(c, seed=500 + c["index"]))
+        f = DogFilter(scene.filter_params(c, seed=500 + c["index"]), stream=one)
         g = scene.random_measurement_grid(c["width"], c["height"], rng)
         dg = {kk: torch.tensor(v, device="cuda") for kk, v in g.items()}
         f.set_measurement_grid(**dg)
@@ -149,6 +152,8 @@ def run(n_streams: int = 256, seconds: float = 3.0, budget_gb: float = 120.0, se
     return {
         "workload": f"serving: {n_streams} streams (sides 256/512/1024, 16 particles per cell), "
                     f"Poisson 10 Hz each, {budget_gb:.0f} GB admission",
+        "arm": "plain: one stream, requests in arrival order" if plain else
+               "concurrent: a CUDA stream per filter, requests of different streams overlap",
         "streams_admitted": len(admitted), "streams_rejected": rejected,
         "workspace_gb": used / 1e9, "seconds": seconds, "requests": len(done),
         "offered_particle_updates_per_s": sum(float(c["nu"]) * c["rate_hz"] for c in admitted),
@@ -320,11 +325,12 @@ def main() -> None:
     ap.add_argument("--seconds", type=float, default=3.0)
     ap.add_argument("--budget-gb", type=float, default=None)
     ap.add_argument("--sessions", action="store_true", help="streams that come and go")
+    ap.add_argument("--plain", action="store_true", help="one stream, requests in arrival order")
     args = ap.parse_args()
     if args.sessions:
         print(json.dumps(run_sessions(args.streams, args.seconds, args.budget_gb or 40.0)))
     else:
-        print(json.dumps(run(args.streams, args.seconds, args.budget_gb or 120.0)))
+        print(json.dumps(run(args.streams, args.seconds, args.budget_gb or 120.0, plain=args.plain)))
 
 
 if __name__ == "__main__":

@@ -40,7 +40,10 @@ def _snapshot(f):
     return out
 
 
-def test_batch_equals_single_filters():
+@pytest.mark.parametrize("group_bytes", [0, 1 << 62, "pairs"])
+def test_batch_equals_single_filters(group_bytes):
+    """Every grouping: each filter its own branch, all four fused into one launch per phase,
+    and two groups of two (fused phases in two concurrent branches)."""
     import torch
 
     from paper_1605_02406_b300.filter import DogBatch, DogFilter
@@ -50,6 +53,12 @@ def test_batch_equals_single_filters():
     g_b = _setup(batched, 7)
     g_s = _setup(single, 7)
     batch = DogBatch(batched)
+    if group_bytes == "pairs":
+        w = [f.nbytes for f in batched]
+        group_bytes = max(w[0] + w[1], w[2] + w[3])
+        assert batch.set_group_bytes(group_bytes) == 2
+    else:
+        assert batch.set_group_bytes(group_bytes) == (4 if group_bytes == 0 else 1)
     dts = [0.1, 0.05, 0.1, 0.2]
     for frame in range(5):
         for i in range(len(CASES)):
@@ -234,3 +243,101 @@ def test_sessions_admit_waiting_streams_and_match_streams_alone():
             assert np.array_equal(alone[f], s["cells"][f]), (k, f)
         checked += 1
     assert checked >= 4
+
+
+def test_batch_captures_again_after_configuration_changes_and_across_batches():
+    """Each filter's description lives in a slot of its workspace, written when a batch
+    captures: a filter shared by two batches stepped in turn, and a filter whose sort
+    configuration changes between batched frames, must still equal the same filters stepped
+    alone, bit for bit."""
+    import torch
+
+    from paper_1605_02406_b300.filter import DogBatch, DogFilter
+    cases = CASES[:2] + [dict(CASES[3], flags=0x80)]  # the last one may take a third pass
+    shared = torch.cuda.Stream()
+    batched = [DogFilter(p, stream=shared) for p in cases]
+    single = [DogFilter(p) for p in cases]
+    rng = np.random.default_rng(3)
+    grids = []
+    for fb, fs, p in zip(batched, single, cases):
+        st = scene.random_state(p, rng, occupied_frac=0.1)
+        fb.set_state(st)
+        fs.set_state(st)
+        grids.append([scene.random_measurement_grid(p["width"], p["height"], rng) for _ in range(3)])
+    one = DogBatch(batched)                   # all three
+    two = DogBatch([batched[1], batched[2]])  # two of them again
+    plan = [(one, [0, 1, 2]), (two, [1, 2]), (one, [0, 1, 2]), ("config", None), (one, [0, 1, 2]),
+            (two, [1, 2]), ("config", None), (two, [1, 2]), (one, [0, 1, 2])]
+    configs = iter([(3, 2), (2, 8)])
+    for step, (batch, members) in enumerate(plan):
+        if batch == "config":  # a new sort configuration for the shared filter with room for it
+            passes, ct = next(configs)
+            batched[2].set_sort_config(passes, ct)
+            single[2].set_sort_config(passes, ct)
+            continue
+        for i in members:
+            g = grids[i][step % 3]
+            batched[i].set_measurement_grid(**g)
+            single[i].set_measurement_grid(**g)
+            single[i].step(0.1)
+        batch.step([0.1] * len(members))
+        for i in members:
+            a, b = _snapshot(batched[i]), _snapshot(single[i])
+            for k in a:
+                va, vb = np.asarray(a[k]), np.asarray(b[k])
+                if va.dtype.kind == "f":
+                    va, vb = va.astype(np.float32).view(np.uint32), vb.astype(np.float32).view(np.uint32)
+                assert np.array_equal(va, vb), f"step {step}, filter {i}: {k} differs"
+    assert batched[2].sort_config()["passes"] == 2
+    one.close()
+    two.close()
+
+
+def test_batch_limits():
+    import torch
+
+    from paper_1605_02406_b300 import native as N
+    from paper_1605_02406_b300.filter import DogBatch, DogFilter
+    s = torch.cuda.Stream()
+    f = DogFilter(CASES[2], stream=s)
+    with pytest.raises(N.DogError) as e:
+        DogBatch([f, f])  # a filter listed twice
+    assert e.value.code == -1
+    with pytest.raises(N.DogError) as e:
+        N.dog_batch_create([f.h] * 129)
+    assert e.value.code in (-1, -7)
+
+
+def test_batch_autotune_steps_real_frames():
+    """dog_batch_autotune times groupings on real frames: afterwards every filter equals the
+    same filter stepped alone as many times, and later batched frames stay equal."""
+    import torch
+
+    from paper_1605_02406_b300.filter import DogBatch, DogFilter
+    shared = torch.cuda.Stream()
+    batched = [DogFilter(p, stream=shared) for p in CASES]
+    single = [DogFilter(p) for p in CASES]
+    g_b = _setup(batched, 9)
+    _setup(single, 9)
+    for i in range(len(CASES)):
+        batched[i].set_measurement_grid(**g_b[i][0][0])
+        single[i].set_measurement_grid(**g_b[i][0][0])
+    batch = DogBatch(batched)
+    before = batched[0].get_state()["frame"]
+    choice = batch.autotune(0.1, frames=1)
+    assert choice["groups"] >= 1
+    frames = batched[0].get_state()["frame"] - before
+    assert frames >= 2  # at least one capture frame and one timed frame per grouping tried
+    for i in range(len(CASES)):
+        for _ in range(frames):
+            single[i].step(0.1)
+    batch.step(0.1)
+    for i in range(len(CASES)):
+        single[i].step(0.1)
+        a, b = _snapshot(batched[i]), _snapshot(single[i])
+        for k in a:
+            va, vb = np.asarray(a[k]), np.asarray(b[k])
+            if va.dtype.kind == "f":
+                va, vb = va.astype(np.float32).view(np.uint32), vb.astype(np.float32).view(np.uint32)
+            assert np.array_equal(va, vb), f"filter {i}: {k} differs"
+    batch.close()
