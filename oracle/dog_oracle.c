@@ -85,6 +85,14 @@ typedef struct {
   /* ego motion to apply at the start of the next step (oracle_set_ego_motion) */
   int ego_on;
   real ego_c, ego_s, ego_dx, ego_dy;
+  uint8_t *inflag;                  /* [nu] 1 = the predicted particle lies inside the grid */
+  /* decisions taken from another run for the next step only (oracle_force_decisions):
+   * each particle's cell and in-grid flag, each newborn slot's cell and set, whether any
+   * newborn mass existed, whether the frame resampled, and each resampled source */
+  int forced;
+  uint32_t *fkey, *fbcell, *frsrc;
+  uint8_t *fin, *fbassoc;
+  int fbirth_mass, fresampled;
 } oracle;
 
 /* ------------------------------------------------------------------------------------
@@ -273,6 +281,8 @@ oracle *oracle_create(const or_params *p) {
   AR(bx, nb); AR(by, nb); AR(bvx, nb); AR(bvy, nb); AR(bw, nb); AR(bcell, nb); AR(bassoc, nb);
   AR(rsrc, nu);
   AR(bz, C); AR(bptp, C); AR(bpfp, C); AR(bpa, C); AR(bpc, C); AR(rbp, C); AR(fcell, C);
+  AR(inflag, nu);
+  AR(fkey, nu); AR(fin, nu); AR(fbcell, nb); AR(fbassoc, nb); AR(frsrc, nu);
 #undef AR
   for (int64_t c = 0; c < C; ++c) o->sgv[c] = 1;
   /* reading: initial state -- particles uniform over the grid, birth-distribution
@@ -301,7 +311,8 @@ void oracle_destroy(oracle *o) {
                   o->cov, o->mpred, o->muA, o->muU, o->px, o->py, o->pvx, o->pvy, o->pw,
                   o->key, o->perm, o->cstart, o->cend, o->S, o->A, o->wn, o->bx, o->by,
                   o->bvx, o->bvy, o->bw, o->bcell, o->bassoc, o->rsrc, o->bz, o->bptp,
-                  o->bpfp, o->bpa, o->bpc, o->rbp, o->fcell};
+                  o->bpfp, o->bpa, o->bpc, o->rbp, o->fcell, o->inflag, o->fkey, o->fin,
+                  o->fbcell, o->fbassoc, o->frsrc};
   for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); ++k) free(ptrs[k]);
   free(o);
 }
@@ -546,9 +557,15 @@ int oracle_step(oracle *o, float dt_f) {
     int in = (fx >= 0 && fx < (real)W && fy >= 0 && fy < (real)H);
     int col = !(fx >= 0) ? 0 : (!(fx < (real)W) ? W - 1 : (int)fx);
     int row = !(fy >= 0) ? 0 : (!(fy < (real)H) ? H - 1 : (int)fy);
+    uint32_t key = (uint32_t)row * (uint32_t)W + (uint32_t)col;
+    if (o->forced) { /* the other run's decision */
+      in = o->fin[i];
+      key = o->fkey[i];
+    }
     if (!in) w = 0;
     o->px[i] = x; o->py[i] = y; o->pvx[i] = vx; o->pvy[i] = vy; o->pw[i] = w;
-    o->key[i] = (uint32_t)row * (uint32_t)W + (uint32_t)col;
+    o->key[i] = key;
+    o->inflag[i] = (uint8_t)in;
   }
 
   /* ---- a2: sort particles by cell index (stable: ties keep array order) and assign
@@ -715,7 +732,32 @@ int oracle_step(oracle *o, float dt_f) {
   for (int64_t c = 0; c < C; ++c) RC += q40(bmass[c]);
   o->RC = RC;
   const real sB = (real)p->sigma_birth_vel;
-  if (RC == 0) {
+  if (o->forced) {
+    /* the other run's newborn slots: the same cells and sets, weights from this run's
+     * newborn masses with those counts (Eq. weights_associated / unassociated) */
+    uint32_t *cnt = (uint32_t *)calloc((size_t)C, sizeof(uint32_t));
+    uint32_t *cntA = (uint32_t *)calloc((size_t)C, sizeof(uint32_t));
+    for (uint32_t b = 0; b < nb; ++b) {
+      cnt[o->fbcell[b]] += 1;
+      cntA[o->fbcell[b]] += o->fbassoc[b];
+    }
+    for (uint32_t b = 0; b < nb; ++b) {
+      uint32_t c = o->fbcell[b];
+      o->bcell[b] = c;
+      o->bassoc[b] = o->fbassoc[b];
+      real rb = bmass[c], pA = o->pA[c], wb;
+      uint32_t n = cnt[c], nA = cntA[c], nUA = n - nA;
+      if (!o->fbirth_mass) wb = 0;
+      else if (full) { real a = rb / (real)n; wb = o->fcell[c] * a; }
+      else if (nA > 0 && nUA > 0) {
+        if (o->fbassoc[b]) { real a = pA * rb; wb = a / (real)nA; }
+        else { real q = R(1.0) - pA; real bb = q * rb; wb = bb / (real)nUA; }
+      } else wb = rb / (real)n;
+      o->bw[b] = wb;
+    }
+    free(cnt);
+    free(cntA);
+  } else if (RC == 0) {
     /* reading: no birth mass anywhere -- slots get weight 0 and cell (slot mod C) */
     for (uint32_t b = 0; b < nb; ++b) {
       o->bcell[b] = (uint32_t)(b % (uint64_t)C);
@@ -818,7 +860,8 @@ int oracle_step(oracle *o, float dt_f) {
   real *nx = (real *)malloc(sizeof(real) * nu), *ny = (real *)malloc(sizeof(real) * nu);
   real *nvx = (real *)malloc(sizeof(real) * nu), *nvy = (real *)malloc(sizeof(real) * nu);
   real *nw = (real *)malloc(sizeof(real) * nu);
-  if ((p->flags & OR_NO_RESAMPLE) || Wq == 0) {
+  const int resample = o->forced ? o->fresampled : !((p->flags & OR_NO_RESAMPLE) || Wq == 0);
+  if (!resample) {
     /* reading: with no weight left (or resampling switched off) the persistent particles
      * carry over in sorted order with their own normalised weights */
     for (uint32_t i = 0; i < nu; ++i) {
@@ -843,11 +886,15 @@ int oracle_step(oracle *o, float dt_f) {
     const uint32_t ntot = nu + nb;
     Q = q40(o->wn[0]);
     for (uint32_t i = 0; i < nu; ++i) {
-      uint64_t P = (uint64_t)(((u128)i * Wq + u) / nu);
-      while (!(Q > P)) {
-        ++j;
-        if (j >= ntot) return -9; /* cannot happen: P < Wq */
-        Q += (j < nu) ? q40(o->wn[j]) : q40(o->bw[j - nu]);
+      if (o->forced) {
+        j = o->frsrc[i];  /* the other run's source */
+      } else {
+        uint64_t P = (uint64_t)(((u128)i * Wq + u) / nu);
+        while (!(Q > P)) {
+          ++j;
+          if (j >= ntot) return -9; /* cannot happen: P < Wq */
+          Q += (j < nu) ? q40(o->wn[j]) : q40(o->bw[j - nu]);
+        }
       }
       o->rsrc[i] = j;
       if (j < nu) {
@@ -864,7 +911,25 @@ int oracle_step(oracle *o, float dt_f) {
   memcpy(o->vx, nvx, sizeof(real) * nu); memcpy(o->vy, nvy, sizeof(real) * nu);
   memcpy(o->w, nw, sizeof(real) * nu);
   free(nx); free(ny); free(nvx); free(nvy); free(nw);
+  o->forced = 0;
   return 0;
+}
+
+/* Decisions for the next step taken from another run of the same filter (for measuring the
+ * arithmetic error of one precision against another on the same Monte Carlo run): each
+ * predicted particle's cell index and in-grid flag [nu], each newborn slot's cell and set
+ * [nu_b], whether any newborn mass existed, whether the frame resampled and each posterior
+ * particle's joint source [nu].  Every real-valued quantity is still computed here. */
+void oracle_force_decisions(oracle *o, const uint32_t *key, const uint8_t *in, const uint32_t *bcell,
+                            const uint8_t *bassoc, int birth_mass, int resampled, const uint32_t *rsrc) {
+  memcpy(o->fkey, key, 4 * (size_t)o->p.nu);
+  memcpy(o->fin, in, (size_t)o->p.nu);
+  memcpy(o->fbcell, bcell, 4 * (size_t)o->p.nu_b);
+  memcpy(o->fbassoc, bassoc, (size_t)o->p.nu_b);
+  memcpy(o->frsrc, rsrc, 4 * (size_t)o->p.nu);
+  o->fbirth_mass = birth_mass;
+  o->fresampled = resampled;
+  o->forced = 1;
 }
 
 /* ---- accessors (binary64 in and out for both modes; exact for the FP32 mirror) ------- */
@@ -907,7 +972,7 @@ int oracle_get_particle_array(const oracle *o, int which, double *out) {
 }
 
 /* which: 0 key [nu] 1 perm [nu] 2 cell_start [C] 3 cell_end [C] 4 newborn cell [nu_b]
- * 5 newborn associated flag [nu_b] 6 resample source [nu] */
+ * 5 newborn associated flag [nu_b] 6 resample source [nu] 7 in-grid flag [nu] */
 int oracle_get_index_array(const oracle *o, int which, uint32_t *out) {
   switch (which) {
     case 0: memcpy(out, o->key, 4 * (size_t)o->p.nu); break;
@@ -917,6 +982,7 @@ int oracle_get_index_array(const oracle *o, int which, uint32_t *out) {
     case 4: memcpy(out, o->bcell, 4 * (size_t)o->p.nu_b); break;
     case 5: for (uint32_t b = 0; b < o->p.nu_b; ++b) out[b] = o->bassoc[b]; break;
     case 6: memcpy(out, o->rsrc, 4 * (size_t)o->p.nu); break;
+    case 7: for (uint32_t i = 0; i < o->p.nu; ++i) out[i] = o->inflag[i]; break;
     default: return -1;
   }
   return 0;

@@ -47,6 +47,9 @@ def _lib(mode: str):
         lib.oracle_cell_update.argtypes = [C.c_double] * 6 + [C.POINTER(C.c_double)]
         lib.oracle_box_muller.argtypes = [C.c_uint32, C.c_uint32, fp]
         lib.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        u8p = C.POINTER(C.c_uint8)
+        lib.oracle_force_decisions.argtypes = [C.c_void_p, u32p, u8p, u32p, u8p, C.c_int, C.c_int, u32p]
+        lib.oracle_force_decisions.restype = None
         lib.oracle_radar_likelihood.restype = C.c_double
         lib.oracle_radar_likelihood.argtypes = [C.c_double] * 8
         if mode == "f32":
@@ -86,7 +89,7 @@ CELL_FIELDS = ["m_occ", "m_free", "rho_p", "rho_b", "p_occ", "mean_vx", "mean_vy
 PARTICLE_FIELDS = ["pred_x", "pred_y", "pred_vx", "pred_vy", "pred_w", "w_norm",
                    "birth_x", "birth_y", "birth_vx", "birth_vy", "birth_w"]
 INDEX_FIELDS = ["key", "perm", "cell_start", "cell_end", "birth_cell", "birth_assoc",
-                "resample_src"]
+                "resample_src", "in_grid"]
 
 
 class OracleFilter:
@@ -158,7 +161,7 @@ class OracleFilter:
             a = np.empty(n, np.float64)
             self.lib.oracle_get_particle_array(self._h, k, _d(a))
             out[name] = a.astype(self._out_dtype())
-        sizes = [self.nu, self.nu, self.C, self.C, self.nu_b, self.nu_b, self.nu]
+        sizes = [self.nu, self.nu, self.C, self.C, self.nu_b, self.nu_b, self.nu, self.nu]
         for k, name in enumerate(INDEX_FIELDS):
             a = np.empty(sizes[k], np.uint32)
             self.lib.oracle_get_index_array(self._h, k, _u32(a))
@@ -171,6 +174,28 @@ class OracleFilter:
         self.lib.oracle_get_scalars(self._h, _u64(sc))
         out["frame"], out["W_total"], out["R_total"], out["u_offset"] = (int(v) for v in sc)
         return out
+
+    def decisions(self) -> dict:
+        """The integer decisions of the last step (see force_decisions)."""
+        im = self.intermediates()
+        return {"key": im["key"], "in_grid": im["in_grid"].astype(np.uint8),
+                "birth_cell": im["birth_cell"], "birth_assoc": im["birth_assoc"].astype(np.uint8),
+                "birth_mass": int(im["R_total"] > 0),
+                # resampling ran unless switched off or no weight was left (Alg. 7 reading)
+                "resampled": int(im["W_total"] > 0 and not (self.params.get("flags", 0) & 0x2)),
+                "resample_src": im["resample_src"]}
+
+    def force_decisions(self, d: dict):
+        """Take the next step's integer decisions (cells, in-grid flags, newborn slots,
+        resampling) from another run, e.g. the binary32 mirror's, so that the difference
+        between the two runs is arithmetic only."""
+        arr = {k: np.ascontiguousarray(d[k], dtype=np.uint8 if k in ("in_grid", "birth_assoc") else np.uint32)
+               for k in ("key", "in_grid", "birth_cell", "birth_assoc", "resample_src")}
+        u8 = lambda a: a.ctypes.data_as(C.POINTER(C.c_uint8))
+        self.lib.oracle_force_decisions(self._h, _u32(arr["key"]), u8(arr["in_grid"]), _u32(arr["birth_cell"]),
+                                        u8(arr["birth_assoc"]), int(d["birth_mass"]), int(d["resampled"]),
+                                        _u32(arr["resample_src"]))
+        self._forced = arr  # kept alive until the step has copied them (it copies at once)
 
     def get_state(self) -> dict:
         st = {k: np.empty(self.nu, np.float64) for k in ("x", "y", "vx", "vy", "w")}

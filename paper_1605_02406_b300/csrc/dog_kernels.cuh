@@ -1852,6 +1852,7 @@ __global__ void __launch_bounds__(BIRTH_BLOCK) k_birth(KParams P, DevBufs B) {
 //   and the tile sum of q40 of the joint weights for the resampling CDF.
 // ====================================================================================
 constexpr int NORM_BLOCK = 256, NORM_ITEMS = 8, NORM_TILE = NORM_BLOCK * NORM_ITEMS;
+static_assert(NORM_BLOCK == SEG_BLOCK, "k_normalise shares the segment pass's block scan");
 
 // shared-memory index of a thread's item, padded by one element per NORM_ITEMS so that a
 // warp reading its threads' item k hits distinct banks
