@@ -173,6 +173,9 @@ struct dog_filter {
   float ego_c = 1.0f, ego_s = 0.0f, ego_dx = 0.0f, ego_dy = 0.0f;
   // host I/O overlapped with compute: grid uploads and cell read-backs on their own streams
   cudaStream_t h2d = nullptr, d2h = nullptr;
+  // the second branch of a frame (normalisation beside the newborn chain)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_h2d = nullptr, ev_stage_free = nullptr, ev_snap = nullptr, ev_d2h = nullptr;
   bool d2h_pending = false;
   uint32_t *d2h_err = nullptr;  // pinned host word: error bits of the frame being read back
@@ -199,7 +202,24 @@ int cuda_fail(cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_fail(e_); \
   } while (0)
 
-// the kernels of one frame, in order; ev (optional) are recorded around each kernel
+// the normalisation of the persistent sources (Alg. 4) and, for the radar filter, the
+// velocity moments (Alg. 6), on stream st
+int enqueue_normalise(dog_filter *f, bool radar, cudaStream_t st) {
+  const KParams &K = f->K;
+  const DevBufs &B = f->B;
+  const uint32_t tiles = (K.nu + NORM_TILE - 1) / NORM_TILE;
+  if (radar) {
+    k_normalise<true><<<tiles, NORM_BLOCK, 0, st>>>(K, B);
+    k_moments<<<(K.C + 255) / 256 < 2368u ? (K.C + 255) / 256 : 2368u, 256, 0, st>>>(K, B);
+  } else {
+    k_normalise_lidar<<<tiles, NORM_BLOCK, 0, st>>>(K, B);
+  }
+  return cuda_fail(cudaGetLastError());
+}
+
+// the kernels of one frame, in order; ev (optional, profiling) are recorded around each
+// kernel, which are then issued one after the other on the filter's stream; otherwise the
+// normalisation runs on a second branch beside the newborn chain
 int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
   const KParams &K = f->K;
   const DevBufs &B = f->B;
@@ -209,7 +229,7 @@ int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
     if (ev) cudaEventRecord(ev[k], st);
   };
   mark();
-  k_tick<<<1, 256, 0, st>>>(B, 2048 * K.passes);
+  k_tick<<<1, 256, 0, st>>>(B, 2048 * K.passes, K.tiles_norm);
   if (K.flags & DOG_EGO) k_ego_warp<<<592, 256, 0, st>>>(K, B);  // timed with k_tick
   ++k; mark();
   const uint32_t pred_grid = (K.nu + PRED_TILE - 1) / PRED_TILE;
@@ -247,6 +267,15 @@ int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
   if (radar) k_cell<true><<<K.tiles_cell, CELL_BLOCK, 0, st>>>(K, B);
   else k_cell<false><<<K.tiles_cell, CELL_BLOCK, 0, st>>>(K, B);
   ++k; mark();
+  // the persistent sources' normalisation (and the radar moments) do not depend on the
+  // newborn chain: outside profiling they run on a second branch from here on
+  if (!ev) {
+    DOG_CUDA(cudaEventRecord(f->ev_fork, st));
+    DOG_CUDA(cudaStreamWaitEvent(f->aux, f->ev_fork, 0));
+    const int rc = enqueue_normalise(f, radar, f->aux);
+    if (rc) return rc;
+    DOG_CUDA(cudaEventRecord(f->ev_join, f->aux));
+  }
   k_scan_tiles<false><<<1, SCAN_BLOCK, 0, st>>>(B.tile_q, B.tile_n, K.tiles_cell, B.tile_qin, B.tile_nin,
                                                  &B.ctl->R_total, &B.ctl->n_birth_cells, K, B.ctl);
   ++k; mark();
@@ -256,11 +285,11 @@ int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
   if (radar) k_birth<true><<<f->birth_grid, BIRTH_BLOCK, 0, st>>>(K, B);
   else k_birth<false><<<f->birth_grid, BIRTH_BLOCK, 0, st>>>(K, B);
   ++k; mark();
-  if (radar) {
-    k_normalise<true><<<K.tiles_norm, NORM_BLOCK, 0, st>>>(K, B);
-    k_moments<<<(K.C + 255) / 256 < 2368u ? (K.C + 255) / 256 : 2368u, 256, 0, st>>>(K, B);  // timed with it
+  if (!ev) {  // the normalisation ran on the second branch; the CDF scan waits for both
+    DOG_CUDA(cudaStreamWaitEvent(st, f->ev_join, 0));
   } else {
-    k_normalise_lidar<<<K.tiles_norm, NORM_BLOCK, 0, st>>>(K, B);
+    const int rc = enqueue_normalise(f, radar, st);
+    if (rc) return rc;
   }
   ++k; mark();
   k_scan_tiles<true><<<1, SCAN_BLOCK, 0, st>>>(B.cdf_tile, nullptr, K.tiles_norm, B.cdf_incl, nullptr,
@@ -473,8 +502,9 @@ int dog_create(const dog_params *params, void *d_workspace, size_t workspace_byt
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&f->h2d, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&f->d2h, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&f->aux, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMallocHost(&f->d2h_err, 64);  // pinned: the copy stays asynchronous
-  cudaEvent_t *evs[] = {&f->ev_h2d, &f->ev_stage_free, &f->ev_snap, &f->ev_d2h};
+  cudaEvent_t *evs[] = {&f->ev_h2d, &f->ev_stage_free, &f->ev_snap, &f->ev_d2h, &f->ev_fork, &f->ev_join};
   for (auto q : evs)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(q, cudaEventDisableTiming);
   if (e == cudaSuccess && f->profile) {
@@ -629,6 +659,7 @@ int enqueue_group_frame(const std::vector<dog_filter *> &fs, cudaStream_t st) {
   auto seg = [](const dog_filter *f) { return f->K.tiles_seg; };
   auto cell = [](const dog_filter *f) { return f->K.tiles_cell; };
   auto norm = [](const dog_filter *f) { return f->K.tiles_norm; };
+  auto pers = [](const dog_filter *f) { return (f->K.nu + NORM_TILE - 1) / NORM_TILE; };
   auto births = [](const dog_filter *f) { return (uint32_t)f->birth_grid; };
   if (batch_args(bf, A, lidar, seg)) kb_segsum_lidar<<<A.first[A.n], SEG_BLOCK, 0, st>>>(A);
   if (batch_args(bf, A, radar, seg)) kb_segsum<true><<<A.first[A.n], SEG_BLOCK, 0, st>>>(A);
@@ -639,8 +670,8 @@ int enqueue_group_frame(const std::vector<dog_filter *> &fs, cudaStream_t st) {
   if (batch_args(bf, A, radar, cell)) kb_birth_prep<true><<<A.first[A.n], CELL_BLOCK, 0, st>>>(A);
   if (batch_args(bf, A, lidar, births)) kb_birth<false><<<A.first[A.n], BIRTH_BLOCK, 0, st>>>(A);
   if (batch_args(bf, A, radar, births)) kb_birth<true><<<A.first[A.n], BIRTH_BLOCK, 0, st>>>(A);
-  if (batch_args(bf, A, lidar, norm)) kb_normalise_lidar<<<A.first[A.n], NORM_BLOCK, 0, st>>>(A);
-  if (batch_args(bf, A, radar, norm)) kb_normalise_radar<<<A.first[A.n], NORM_BLOCK, 0, st>>>(A);
+  if (batch_args(bf, A, lidar, pers)) kb_normalise_lidar<<<A.first[A.n], NORM_BLOCK, 0, st>>>(A);
+  if (batch_args(bf, A, radar, pers)) kb_normalise_radar<<<A.first[A.n], NORM_BLOCK, 0, st>>>(A);
   if (batch_args(bf, A, radar, [](const dog_filter *f) { return std::min((f->K.C + 255) / 256, 2368u); }))
     kb_moments<<<A.first[A.n], 256, 0, st>>>(A);
   if (batch_args(bf, A, all, one)) kb_scan_tiles<true><<<A.first[A.n], SCAN_BLOCK, 0, st>>>(A);
@@ -810,12 +841,12 @@ void dog_batch_destroy(dog_batch *b) {
 void dog_destroy(dog_filter *f) {
   if (!f) return;
   if (f->st) cudaStreamSynchronize(f->st);
-  for (auto x : {f->h2d, f->d2h})
+  for (auto x : {f->h2d, f->d2h, f->aux})
     if (x) {
       cudaStreamSynchronize(x);
       cudaStreamDestroy(x);
     }
-  for (auto x : {f->ev_h2d, f->ev_stage_free, f->ev_snap, f->ev_d2h})
+  for (auto x : {f->ev_h2d, f->ev_stage_free, f->ev_snap, f->ev_d2h, f->ev_fork, f->ev_join})
     if (x) cudaEventDestroy(x);
   if (f->d2h_err) cudaFreeHost(f->d2h_err);
   for (auto &g : f->gexec)
@@ -1311,7 +1342,7 @@ extern "C" int dog_assign_cells_noalloc(const uint32_t *d_keys, uint32_t n, uint
   // every array of the scratch is rewritten before it is read: the histogram by k_tick, the
   // clamped keys and the per-tile digit counts by k_na_hist (first pass) and k_sort_count
   // (later passes)
-  k_tick<<<1, 256, 0, st>>>(B, 2048 * K.passes);
+  k_tick<<<1, 256, 0, st>>>(B, 2048 * K.passes, 0u);
   k_na_hist<<<K.tiles_sort, 256, 4u * K.passes * K.radix, st>>>(d_keys, num_cells, key_c, K, B);
   const size_t ssm = sort_smem_bytes(K.radix);
   int sms = 148;

@@ -28,11 +28,14 @@ namespace dog {
 // ====================================================================================
 // k_tick: begin a frame
 // ====================================================================================
-__device__ __forceinline__ void tick_body(const DevBufs &B, int n_hist) {
+__device__ __forceinline__ void tick_body(const DevBufs &B, int n_hist, uint32_t n_cdf) {
   for (int i = threadIdx.x; i < n_hist; i += blockDim.x) B.hist[i] = 0u;
+  // the joint-weight sums of the resampling tiles, which the normalisation (persistent
+  // sources) and the newborn kernel (newborn slots) add into
+  for (uint32_t i = threadIdx.x; i < n_cdf; i += blockDim.x) B.cdf_tile[i] = 0ull;
   if (threadIdx.x == 0) B.ctl->frame += 1u;
 }
-__global__ void k_tick(DevBufs B, int n_hist) { tick_body(B, n_hist); }
+__global__ void k_tick(DevBufs B, int n_hist, uint32_t n_cdf) { tick_body(B, n_hist, n_cdf); }
 
 // ====================================================================================
 // k_init: initial state -- particles uniform over the grid, birth-distribution
@@ -1756,6 +1759,37 @@ __global__ void __launch_bounds__(CELL_BLOCK) k_birth_prep(KParams P, DevBufs B)
   birth_prep_body<RADAR>(P, B, blockIdx.x);
 }
 
+constexpr int NORM_TILE_ = 2048;  // the resampling tile (NORM_TILE, defined with k_normalise)
+static_assert(BIRTH_SLOTS <= NORM_TILE_, "a newborn block spans at most two resampling tiles");
+
+// add a block's newborn weight sums q0 (tile t0) and q1 (tile t1 = t0 + 1, if any) to the
+// resampling tiles' joint-weight sums (exact 64-bit atomics: the order of the additions does
+// not matter)
+__device__ __forceinline__ void birth_tile_sums(const DevBufs &B, unsigned long long q0, unsigned long long q1,
+                                                uint32_t t0, uint32_t t1) {
+  __shared__ unsigned long long s_q[2][BIRTH_BLOCK / 32];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    q0 += __shfl_xor_sync(FULL, q0, o);
+    q1 += __shfl_xor_sync(FULL, q1, o);
+  }
+  if (lane == 0) {
+    s_q[0][warp] = q0;
+    s_q[1][warp] = q1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long a = 0ull, b = 0ull;
+    for (int w = 0; w < BIRTH_BLOCK / 32; ++w) {
+      a += s_q[0][w];
+      b += s_q[1][w];
+    }
+    if (a) atomicAdd(B.cdf_tile + t0, a);
+    if (t1 != t0 && b) atomicAdd(B.cdf_tile + t1, b);
+  }
+}
+
 // k_birth: a block makes the newborns of BIRTH_SLOTS consecutive slots.  Its slots belong to
 // the entries from the one owning its first slot to the one owning the next block's first
 // slot; it caches those entries' first slots in shared memory (at most BIRTH_CACHE of them),
@@ -1833,6 +1867,18 @@ __device__ __forceinline__ void birth_body(const KParams &P, const DevBufs &B, u
     const uint32_t s = s0 + r * BIRTH_BLOCK + threadIdx.x;
     if (s < s1) birth_init(P, B, s, cell[r], assoc[r], wb[r], zv[r], sg[r], frame, record);
   }
+  // the newborn part of the resampling tiles' joint-weight sums: slot s is joint source
+  // nu + s; this block's slots lie in at most two tiles (BIRTH_SLOTS <= NORM_TILE)
+  const uint32_t t_first = (P.nu + s0) / NORM_TILE_;
+  unsigned long long q0 = 0ull, q1 = 0ull;
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const uint32_t s = s0 + r * BIRTH_BLOCK + threadIdx.x;
+    if (s >= s1) continue;
+    const unsigned long long q = q40(wb[r]);
+    if ((P.nu + s) / NORM_TILE_ == t_first) q0 += q; else q1 += q;
+  }
+  birth_tile_sums(B, q0, q1, t_first, (P.nu + s1 - 1u) / NORM_TILE_);
 }
 template <bool RADAR>
 __global__ void __launch_bounds__(BIRTH_BLOCK) k_birth(KParams P, DevBufs B) {
@@ -1849,9 +1895,11 @@ __global__ void __launch_bounds__(BIRTH_BLOCK) k_birth(KParams P, DevBufs B) {
 //   its sums in its moment record; a cell spread over several tiles adds its pieces,
 //   divided by rho_p, in exact 2^-40 fixed point with integer atomics; k_moments finishes
 //   both;
-//   and the tile sum of q40 of the joint weights for the resampling CDF.
+//   and the persistent part of the tile sums of q40 of the joint weights for the resampling
+//   CDF (k_birth adds the newborn part).  The grid covers the persistent sources only.
 // ====================================================================================
 constexpr int NORM_BLOCK = 256, NORM_ITEMS = 8, NORM_TILE = NORM_BLOCK * NORM_ITEMS;
+static_assert(NORM_TILE == NORM_TILE_, "the newborn kernel's resampling tile");
 static_assert(NORM_BLOCK == SEG_BLOCK, "k_normalise shares the segment pass's block scan");
 
 // shared-memory index of a thread's item, padded by one element per NORM_ITEMS so that a
@@ -1865,7 +1913,6 @@ __device__ __forceinline__ void normalise_body(const KParams &P, const DevBufs &
   __shared__ unsigned long long s_red[NORM_BLOCK / 32];
   __shared__ float s_t[3][NORM_PADDED];  // w', vx, vy of the tile's items, for the tail pass
   const uint32_t tile = blk;
-  const uint32_t ntot = P.nu + P.nu_b;
   const uint32_t j0 = tile * NORM_TILE + threadIdx.x * NORM_ITEMS;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned long long qsum = 0ull;
@@ -1933,13 +1980,8 @@ __device__ __forceinline__ void normalise_body(const KParams &P, const DevBufs &
     }
     store_run<NORM_ITEMS>(B.wn, j0, P.nu, wnv);
   }
-  // newborn sources of this tile
-#pragma unroll
-  for (int it = 0; it < NORM_ITEMS; ++it) {
-    const uint32_t j = j0 + it;
-    if (j >= P.nu && j < ntot) qsum += q40(__ldg(B.bw + (j - P.nu)));
-  }
-  // tile sum of the joint quantised weights (k_scan_tiles turns them into the CDF)
+  // this tile's persistent part of the joint quantised weights (k_birth adds the newborn
+  // part; k_scan_tiles turns the tile sums into the CDF)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) qsum += __shfl_xor_sync(FULL, qsum, o);
   if (lane == 0) s_red[warp] = qsum;
@@ -1947,7 +1989,7 @@ __device__ __forceinline__ void normalise_body(const KParams &P, const DevBufs &
   if (threadIdx.x == 0) {
     unsigned long long tsum = 0ull;
     for (int w = 0; w < NORM_BLOCK / 32; ++w) tsum += s_red[w];
-    B.cdf_tile[tile] = tsum;
+    atomicAdd(B.cdf_tile + tile, tsum);
   }
   if (!has_pers) return;  // block-uniform
   // segmented compensated moment sums within the tile
@@ -2025,12 +2067,11 @@ __device__ __forceinline__ void moments_body(const KParams &P, const DevBufs &B,
 __global__ void __launch_bounds__(256) k_moments(KParams P, DevBufs B) { moments_body(P, B, blockIdx.x, gridDim.x); }
 
 // k_normalise_lidar: the lidar filter's normalisation (Eq. DSnormalization with g == 1:
-// w' = mu_UA w, Alg. 4) and the tile sums of the joint quantised weights; its moments
-// were summed in k_segsum_lidar.
+// w' = mu_UA w, Alg. 4) over the persistent sources and their part of the tile sums of the
+// joint quantised weights; its moments were summed in k_segsum_lidar.
 __device__ __forceinline__ void normalise_lidar_body(const KParams &P, const DevBufs &B, uint32_t blk) {
   __shared__ unsigned long long s_red[NORM_BLOCK / 32];
   const uint32_t tile = blk;
-  const uint32_t ntot = P.nu + P.nu_b;
   const uint32_t j0 = tile * NORM_TILE + threadIdx.x * NORM_ITEMS;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned long long qsum = 0ull;
@@ -2051,18 +2092,13 @@ __device__ __forceinline__ void normalise_lidar_body(const KParams &P, const Dev
     store_run<NORM_ITEMS>(B.wn, j0, P.nu, wn);
   }
 #pragma unroll
-  for (int it = 0; it < NORM_ITEMS; ++it) {
-    const uint32_t j = j0 + it;
-    if (j >= P.nu && j < ntot) qsum += q40(__ldg(B.bw + (j - P.nu)));
-  }
-#pragma unroll
   for (int o = 16; o > 0; o >>= 1) qsum += __shfl_xor_sync(FULL, qsum, o);
   if (lane == 0) s_red[warp] = qsum;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long tsum = 0ull;
     for (int w = 0; w < NORM_BLOCK / 32; ++w) tsum += s_red[w];
-    B.cdf_tile[tile] = tsum;
+    atomicAdd(B.cdf_tile + tile, tsum);  // the newborn part of a mixed tile comes from k_birth
   }
 }
 __global__ void __launch_bounds__(NORM_BLOCK) k_normalise_lidar(KParams P, DevBufs B) {
