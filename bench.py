@@ -49,7 +49,7 @@ ALG_BYTES = {
     # fields 24 (m_O, m_F, rho_b, rho_p, p_occ, mu_UA) and the 5 velocity moments 20
     "k_cell": (0, 0, 88),
     "k_birth": (0, 20, 0),        # write newborn state 16 + weight 4
-    "k_normalise": (12, 4, 0),    # lidar: read key 4, w 4, write w' 4; newborn w 4
+    "k_normalise": (12, 0, 0),    # lidar, persistent sources: read key 4, w 4, write w' 4
     "k_resample": (8, 4, 0),      # read w' 4; write the source index 4; newborn w 4
     "k_tick": (0, 0, 0),
 }
