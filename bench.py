@@ -17,6 +17,7 @@ Under torchrun each rank runs an independent replica (the filter does not shard)
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -65,6 +66,76 @@ def csrc_hash() -> str:
         with open(os.path.join(d, n), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
+
+
+def _ncu_rows(path: str) -> list:
+    """The rows of an ``ncu --csv --log-file`` log (the profiler's own lines skipped)."""
+    import csv
+    import io
+    lines = open(path).read().splitlines()
+    start = next(k for k, line in enumerate(lines) if line.startswith('"ID"'))
+    return list(csv.DictReader(io.StringIO("\n".join(lines[start:]))))
+
+
+def _ncu_kernel(full: str) -> str:
+    """'void k_segsum<0>(dog::KParams, ...)' -> 'k_segsum'"""
+    n = full.split("(")[0].replace("void ", "").replace("<unnamed>::", "").strip()
+    return n.split("<")[0].split("::")[-1]
+
+
+# per-launch labels, in launch order within one frame, of the kernels a frame runs more than
+# once or under another name than bench.py's per-kernel times (2-pass sort)
+NCU_LABELS = {"k_sort_pass": ["k_sort_pass0", "k_sort_pass1"],
+              "k_sort_offsets": ["k_sort_offsets0", "k_sort_offsets1"],
+              "k_sort_count": ["k_sort_count1"], "k_scan_tiles": ["k_scan_births", "k_scan_cdf"],
+              "k_segsum_lidar": ["k_segsum"], "k_normalise_lidar": ["k_normalise"]}
+
+
+def write_ncu_traffic(paths: list, out: str) -> dict:
+    """DRAM bytes per launch (``--metrics dram__bytes_read.sum,dram__bytes_write.sum``, one
+    frame's launches of each kernel) into ``out``, tagged with the hash of the CUDA sources."""
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    launches = {}
+    for j, p in enumerate(paths):
+        for r in _ncu_rows(p):
+            if r["Metric Name"] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+                d = launches.setdefault((j, int(r["ID"])), {"kernel": _ncu_kernel(r["Kernel Name"])})
+                d[r["Metric Name"].split(".")[0].rsplit("_", 1)[1]] = \
+                    float(r["Metric Value"].replace(",", "")) * scale.get(r["Metric Unit"], 1)
+    by_kernel = {}
+    for i in sorted(launches):
+        by_kernel.setdefault(launches[i]["kernel"], []).append(launches[i])
+    rw = {}
+    for k, ls in by_kernel.items():
+        labels = NCU_LABELS.get(k, [k])
+        if len(ls) != len(labels):
+            raise SystemExit(f"{k}: {len(ls)} launches captured, one frame has {len(labels)}")
+        for lab, d in zip(labels, ls):
+            rw[lab] = {"read": d["read"], "write": d["write"]}
+    js = {"csrc_hash": csrc_hash(), "unit": "bytes per launch (dram read + write)",
+          "kernels": {k: v["read"] + v["write"] for k, v in rw.items()}, "read_write": rw}
+    with open(out, "w") as fh:
+        json.dump(js, fh, indent=1)
+    return js
+
+
+def ncu_launch_table(path: str) -> str:
+    """Per kernel: launches, total and mean device time and share, from a
+    ``--metrics gpu__time_duration.sum --csv`` log (markdown)."""
+    scale = {"ns": 1e-3, "nsecond": 1e-3, "us": 1.0, "usecond": 1.0, "ms": 1e3, "msecond": 1e3}
+    tot = {}
+    for r in _ncu_rows(path):
+        if r["Metric Name"] == "gpu__time_duration.sum":
+            k = _ncu_kernel(r["Kernel Name"])
+            us = float(r["Metric Value"].replace(",", "")) * scale.get(r["Metric Unit"], 1.0)
+            n, t = tot.get(k, (0, 0.0))
+            tot[k] = (n + 1, t + us)
+    allt = sum(t for _, t in tot.values())
+    lines = ["| kernel | launches | total µs | µs / launch | share |", "|---|---|---|---|---|"]
+    for k, (n, t) in sorted(tot.items(), key=lambda kv: -kv[1][1]):
+        lines.append(f"| {k} | {n} | {t:.1f} | {t / n:.1f} | {100 * t / allt:.1f} % |")
+    lines.append(f"| **all** | {sum(n for n, _ in tot.values())} | {allt:.1f} | | 100 % |")
+    return "\n".join(lines)
 
 
 def peaks() -> tuple:
@@ -505,7 +576,18 @@ def main() -> None:
     ap.add_argument("--no-ego", action="store_true", help="skip the ego-motion workload")
     ap.add_argument("--no-phdmib", action="store_true", help="skip the PHD/MIB filter workload")
     ap.add_argument("--cpu-plan", action="store_true", help="only the full CPU baseline plan (slow)")
+    ap.add_argument("--ncu-traffic", nargs="+", metavar="CSV",
+                    help="write profiles/ncu_traffic.json from ncu DRAM-byte logs and exit")
+    ap.add_argument("--ncu-launches", metavar="CSV", help="print the per-kernel launch table of an ncu log and exit")
     args = ap.parse_args()
+    if args.ncu_traffic:
+        js = write_ncu_traffic(args.ncu_traffic, os.path.join(ROOT, "profiles", "ncu_traffic.json"))
+        for k, v in js["read_write"].items():
+            print(f"{k:18s} read {v['read'] / 1e6:8.1f} MB  write {v['write'] / 1e6:8.1f} MB")
+        return
+    if args.ncu_launches:
+        print(ncu_launch_table(args.ncu_launches))
+        return
     if args.cpu_plan:
         print(json.dumps(cpu_plan()), flush=True)
         return
@@ -554,7 +636,6 @@ def main() -> None:
     # the GPU from the first step on
     f.stream.wait_stream(torch.cuda.current_stream())
     grid_ptrs = [{k: v.data_ptr() for k, v in g.items()} for g in dev_grids]
-    import gc
     gc.collect()
     gc.disable()
     clk = Clocks(local)
@@ -607,13 +688,18 @@ def main() -> None:
     N.dog_wait_cells(fe.h)
     torch.cuda.synchronize()
     barrier()
-    ke = min(args.steps, 100)
+    # 100 steps whatever --steps is (about 35 ms): the last frame's read-back, which nothing
+    # overlaps, and the host's jitter then weigh what they weigh in a stream of frames
+    ke = 100
+    gc.collect()
+    gc.disable()
     t0 = time.perf_counter()
     for k in range(ke):
         e2e_step(args.warmup + k)
     N.dog_wait_cells(fe.h)  # the last frame's cells are on the host
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    gc.enable()
     e2e_value = replicas.job_throughput(params["nu"] * ke, e2e_s, "cuda")
     fe.close()
 
@@ -701,7 +787,7 @@ def main() -> None:
         "config": bench_config(cfg, params, world),
         "launch": "CUDA graph per step",
         "sort": dict(sort_cfg, chosen_by="dog_autotune"),
-        "e2e": {"value": e2e_value, "unit": "particle-updates/s",
+        "e2e": {"value": e2e_value, "unit": "particle-updates/s", "steps": ke,
                 "h2d_bytes_per_step": 2 * 4 * C, "d2h_bytes_per_step": 3 * 4 * C},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
