@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import argparse
 import collections
+import gc
 import json
 import queue
 import threading
@@ -123,26 +124,37 @@ def run(n_streams: int = 256, seconds: float = 3.0, budget_gb: float = 120.0, se
             arrivals.append((t, k))
             t += rng.exponential(1.0 / c["rate_hz"])
     arrivals.sort()
-    start = torch.cuda.Event(enable_timing=True)
-    start.record()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    done = []  # (arrival, stream, event)
-    i = 0
-    while i < len(arrivals):
-        now = time.perf_counter() - t0
-        if arrivals[i][0] > now:
-            time.sleep(min(arrivals[i][0] - now, 0.0005))
-            continue
-        while i < len(arrivals) and arrivals[i][0] <= now:
-            a, k = arrivals[i]
-            f = filters[k]
-            f.step(0.1)
-            ev = torch.cuda.Event(enable_timing=True)
-            ev.record(f.stream)
-            done.append((a, k, ev))
-            i += 1
-    torch.cuda.synchronize()
+    # the collector is paused while requests are issued: a collection pass over the loop's
+    # objects can hold the host thread for tens of milliseconds, and every request arriving
+    # meanwhile would count that wait in its latency.  (Before the start event: the GPU and
+    # host clocks of the latencies start together.)
+    gc.collect()
+    gc.disable()
+    try:
+        start = torch.cuda.Event(enable_timing=True)
+        start.record()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done = []  # (arrival, stream, event)
+        lag = []
+        i = 0
+        while i < len(arrivals):
+            now = time.perf_counter() - t0
+            if arrivals[i][0] > now:
+                time.sleep(min(arrivals[i][0] - now, 0.0005))
+                continue
+            while i < len(arrivals) and arrivals[i][0] <= now:
+                a, k = arrivals[i]
+                f = filters[k]
+                lag.append(time.perf_counter() - t0 - a)  # host: arrival to issue
+                f.step(0.1)
+                ev = torch.cuda.Event(enable_timing=True)
+                ev.record(f.stream)
+                done.append((a, k, ev))
+                i += 1
+        torch.cuda.synchronize()
+    finally:
+        gc.enable()
     wall = time.perf_counter() - t0
     lat = np.array([start.elapsed_time(ev) * 1e-3 - a for a, _, ev in done])
     updates = sum(int(admitted[k]["nu"]) for _, k, _ in done)
@@ -161,6 +173,7 @@ def run(n_streams: int = 256, seconds: float = 3.0, budget_gb: float = 120.0, se
         "updates": updates, "last_completion_s": last,
         "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
                        "max": float(lat.max() * 1e3)},
+        "issue_lag_ms": {"p99": float(np.percentile(lag, 99) * 1e3), "max": float(max(lag) * 1e3)},
         "wall_s": wall,
     }
 
@@ -230,65 +243,70 @@ def run_sessions(n_streams: int = 256, seconds: float = 3.0, budget_gb: float = 
     live, served, waits, done, first = {}, {}, [], [], []
     pending = 0  # admitted, not yet opened or not yet closed
     open_s, n_open, max_live = 0.0, 0, 0
-    start = torch.cuda.Event(enable_timing=True)
-    start.record()
-    torch.cuda.synchronize()
-    th.start()
-    t0 = time.perf_counter()
-    ci = 0
-    while True:
-        if not failed.empty():
-            raise RuntimeError("serving worker failed while opening or closing a filter") from failed.get()
-        if not th.is_alive():
-            raise RuntimeError("serving worker exited unexpectedly")
-        now = time.perf_counter() - t0
-        while ci < n and connect[ci] <= now:
-            adm.request(ci, need[ci])
-            ci += 1
-        while not closed.empty():
-            adm.release(closed.get())
-            pending -= 1
-        if now < seconds:
-            for k in adm.admit():
-                waits.append(now - connect[k])
-                todo.put(("open", k, now))
-                pending += 1
-        while not opened.empty():  # first frame issued by the worker at admission time
-            k, f, raw, g, ev, t_req, dt = opened.get()
-            pending -= 1
-            open_s += dt
-            n_open += 1
-            nu = int(cfgs[k]["nu"])
-            first.append((t_req, ev))
-            done.append((t_req, nu, ev))
-            live[k] = dict(f=f, raw=raw, grid_host=g if keep else None, t_end=min(t_req + life[k], seconds),
-                           next=time.perf_counter() - t0 + rng.exponential(1.0 / cfgs[k]["rate_hz"]),
-                           last=ev, frames=1, rate=cfgs[k]["rate_hz"], nu=nu)
-        max_live = max(max_live, len(live))
-        issued = False
-        for k in list(live):
-            s = live[k]
+    gc.collect()
+    gc.disable()  # as in run(): no collection pass while requests are issued
+    try:
+        start = torch.cuda.Event(enable_timing=True)
+        start.record()
+        torch.cuda.synchronize()
+        th.start()
+        t0 = time.perf_counter()
+        ci = 0
+        while True:
+            if not failed.empty():
+                raise RuntimeError("serving worker failed while opening or closing a filter") from failed.get()
+            if not th.is_alive():
+                raise RuntimeError("serving worker exited unexpectedly")
             now = time.perf_counter() - t0
-            while s["next"] <= now and s["next"] < s["t_end"]:  # requests due
-                s["f"].step(0.1)
-                ev = torch.cuda.Event(enable_timing=True)
-                ev.record(s["f"].stream)
-                done.append((s["next"], s["nu"], ev))
-                s["last"] = ev
-                s["frames"] += 1
-                s["next"] += rng.exponential(1.0 / s["rate"])
-                issued = True
-            if now >= s["t_end"] and s["last"].query():  # session over, last frame finished
-                served[k] = dict(frames=s["frames"])
-                if keep:
-                    served[k].update(grid=s["grid_host"], cells=s["f"].cells(["m_occ", "m_free", "p_occ"]))
-                todo.put(("close", k, (s["f"], s["raw"])))
-                pending += 1
-                del live[k]
-        if now >= seconds and not live and pending == 0:
-            break
-        if not issued:
-            time.sleep(0.0002)
+            while ci < n and connect[ci] <= now:
+                adm.request(ci, need[ci])
+                ci += 1
+            while not closed.empty():
+                adm.release(closed.get())
+                pending -= 1
+            if now < seconds:
+                for k in adm.admit():
+                    waits.append(now - connect[k])
+                    todo.put(("open", k, now))
+                    pending += 1
+            while not opened.empty():  # first frame issued by the worker at admission time
+                k, f, raw, g, ev, t_req, dt = opened.get()
+                pending -= 1
+                open_s += dt
+                n_open += 1
+                nu = int(cfgs[k]["nu"])
+                first.append((t_req, ev))
+                done.append((t_req, nu, ev))
+                live[k] = dict(f=f, raw=raw, grid_host=g if keep else None, t_end=min(t_req + life[k], seconds),
+                               next=time.perf_counter() - t0 + rng.exponential(1.0 / cfgs[k]["rate_hz"]),
+                               last=ev, frames=1, rate=cfgs[k]["rate_hz"], nu=nu)
+            max_live = max(max_live, len(live))
+            issued = False
+            for k in list(live):
+                s = live[k]
+                now = time.perf_counter() - t0
+                while s["next"] <= now and s["next"] < s["t_end"]:  # requests due
+                    s["f"].step(0.1)
+                    ev = torch.cuda.Event(enable_timing=True)
+                    ev.record(s["f"].stream)
+                    done.append((s["next"], s["nu"], ev))
+                    s["last"] = ev
+                    s["frames"] += 1
+                    s["next"] += rng.exponential(1.0 / s["rate"])
+                    issued = True
+                if now >= s["t_end"] and s["last"].query():  # session over, last frame finished
+                    served[k] = dict(frames=s["frames"])
+                    if keep:
+                        served[k].update(grid=s["grid_host"], cells=s["f"].cells(["m_occ", "m_free", "p_occ"]))
+                    todo.put(("close", k, (s["f"], s["raw"])))
+                    pending += 1
+                    del live[k]
+            if now >= seconds and not live and pending == 0:
+                break
+            if not issued:
+                time.sleep(0.0002)
+    finally:
+        gc.enable()
     todo.put(None)
     th.join()
     torch.cuda.synchronize()
