@@ -196,6 +196,15 @@ int cuda_fail(cudaError_t e) {
   return DOG_ERR_CUDA;
 }
 
+// k_sort_offsets of pass p with the register run that covers the sort tiles
+void launch_offsets(const KParams &K, const DevBufs &B, int p, cudaStream_t st) {
+  switch (offsets_per(K.tiles_sort)) {
+    case 4: k_sort_offsets<4><<<K.radix, OFF_BLOCK, 0, st>>>(K, B, p); break;
+    case 8: k_sort_offsets<8><<<K.radix, OFF_BLOCK, 0, st>>>(K, B, p); break;
+    default: k_sort_offsets<16><<<K.radix, OFF_BLOCK, 0, st>>>(K, B, p); break;
+  }
+}
+
 #define DOG_CUDA(x)                              \
   do {                                           \
     const cudaError_t e_ = (x);                  \
@@ -254,7 +263,7 @@ int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
                      count_smem_bytes(K.radix, f->count_ct), st>>>(K, B, kin, p, f->count_ct);
       ++k; mark();
     }
-    k_sort_offsets<<<K.radix, OFF_BLOCK, 0, st>>>(K, B, p);
+    launch_offsets(K, B, p, st);
     ++k; mark();
     k_sort_pass<<<K.tiles_sort, SORT_BLOCK, ssm, st>>>(K, B, kin, vin, kout, vout, p);
     kin = kout;
@@ -650,8 +659,14 @@ int enqueue_group_frame(const std::vector<dog_filter *> &fs, cudaStream_t st) {
       kb_sort_count<<<A.first[A.n], COUNT_BLOCK,
                       batch_smem(bf, has, [](const dog_filter *f) { return count_smem_bytes(f->K.radix, f->count_ct); }),
                       st>>>(A, p);
-    if (batch_args(bf, A, has, [](const dog_filter *f) { return f->K.radix; }))
-      kb_sort_offsets<<<A.first[A.n], OFF_BLOCK, 0, st>>>(A, p);
+    if (batch_args(bf, A, has, [](const dog_filter *f) { return f->K.radix; })) {
+      int per = 4;  // the register run that covers every filter's sort tiles
+      for (const dog_filter *f : bf)
+        if (has(f)) per = std::max(per, offsets_per(f->K.tiles_sort));
+      if (per == 4) kb_sort_offsets<4><<<A.first[A.n], OFF_BLOCK, 0, st>>>(A, p);
+      else if (per == 8) kb_sort_offsets<8><<<A.first[A.n], OFF_BLOCK, 0, st>>>(A, p);
+      else kb_sort_offsets<16><<<A.first[A.n], OFF_BLOCK, 0, st>>>(A, p);
+    }
     if (batch_args(bf, A, has, [](const dog_filter *f) { return f->K.tiles_sort; }))
       kb_sort_pass<<<A.first[A.n], SORT_BLOCK,
                      batch_smem(bf, has, [](const dog_filter *f) { return sort_smem_bytes(f->K.radix); }), st>>>(A, p);
@@ -1359,7 +1374,7 @@ extern "C" int dog_assign_cells_noalloc(const uint32_t *d_keys, uint32_t n, uint
     if (p > 0)
       k_sort_count<<<(K.tiles_sort + ct - 1) / ct, COUNT_BLOCK, count_smem_bytes(K.radix, ct), st>>>(K, B, kin,
                                                                                                        p, ct);
-    k_sort_offsets<<<K.radix, OFF_BLOCK, 0, st>>>(K, B, p);
+    launch_offsets(K, B, p, st);
     k_sort_pass<<<K.tiles_sort, SORT_BLOCK, ssm, st>>>(K, B, kin, vin, kout, vout, p);
     kin = kout;
     vin = vout;
@@ -1440,7 +1455,7 @@ int enqueue_sort(dog_filter *f, int passes, uint32_t ct, cudaEvent_t e0, cudaEve
     if (p > 0)
       k_sort_count<<<(K.tiles_sort + ct - 1) / ct, COUNT_BLOCK, count_smem_bytes(K.radix, ct), st>>>(K, B, kin,
                                                                                                       p, ct);
-    k_sort_offsets<<<K.radix, OFF_BLOCK, 0, st>>>(K, B, p);
+    launch_offsets(K, B, p, st);
     k_sort_pass<<<K.tiles_sort, SORT_BLOCK, ssm, st>>>(K, B, kin, vin, kout, vout, p);
     kin = kout;
     vin = vout;

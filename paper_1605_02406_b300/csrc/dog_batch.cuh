@@ -94,9 +94,11 @@ __global__ void __launch_bounds__(COUNT_BLOCK) kb_sort_count(const __grid_consta
   sort_count_body(P, B, sort_io(P, B, pass).kin, pass, s_bf.count_ct, bb.blk);
 }
 
-__global__ void __launch_bounds__(OFF_BLOCK) kb_sort_offsets(const __grid_constant__ BatchArgs A, int pass) {
+template <int OFF_PER>
+__global__ void __launch_bounds__(OFF_BLOCK, OFF_PER <= 4 ? 8 : 1) kb_sort_offsets(const __grid_constant__ BatchArgs A,
+                                                                                   int pass) {
   DOG_BATCH_PROLOGUE;
-  sort_offsets_body(P, B, pass, bb.blk);
+  sort_offsets_body<OFF_PER>(P, B, pass, bb.blk);
 }
 
 __global__ void __launch_bounds__(SORT_BLOCK, 2) kb_sort_pass(const __grid_constant__ BatchArgs A, int pass) {
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(NORM_BLOCK, 4) kb_normalise_radar(const __grid
   normalise_body<true>(P, B, bb.blk);
 }
 
-__global__ void __launch_bounds__(NORM_BLOCK) kb_normalise_lidar(const __grid_constant__ BatchArgs A) {
+__global__ void __launch_bounds__(NORM_BLOCK, 8) kb_normalise_lidar(const __grid_constant__ BatchArgs A) {
   DOG_BATCH_PROLOGUE;
   normalise_lidar_body(P, B, bb.blk);
 }

@@ -534,9 +534,17 @@ __global__ void __launch_bounds__(COUNT_BLOCK) k_sort_count(KParams P, DevBufs B
 // k_sort_offsets: for one pass, counts[d][t] -> (sum of the histogram below digit d) +
 // sum_{t' < t} counts[d][t'], in place.  One block per digit; thread k owns a contiguous run
 // of tiles, held in registers (read once, 16-byte loads where the row allows), and the
-// block scans the runs' totals.
-constexpr int OFF_BLOCK = 256, OFF_WARPS = OFF_BLOCK / 32, OFF_PER = 16;
+// block scans the runs' totals.  OFF_PER, the most tiles a thread holds, is the smallest of
+// 4, 8 and 16 that covers the filter's tiles (fewer registers: more blocks per SM).
+constexpr int OFF_BLOCK = 256, OFF_WARPS = OFF_BLOCK / 32;
 
+// the register run length for T sort tiles (T > 16 OFF_BLOCK takes the run from memory)
+inline int offsets_per(uint32_t T) {
+  const uint32_t per = (T + OFF_BLOCK - 1) / OFF_BLOCK;
+  return per <= 4u ? 4 : (per <= 8u ? 8 : 16);
+}
+
+template <int OFF_PER>
 __device__ __forceinline__ void sort_offsets_body(const KParams &P, const DevBufs &B, int pass, uint32_t blk) {
   __shared__ uint32_t s_h[OFF_WARPS], s_t[OFF_WARPS];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -625,8 +633,9 @@ __device__ __forceinline__ void sort_offsets_body(const KParams &P, const DevBuf
     }
   }
 }
-__global__ void __launch_bounds__(OFF_BLOCK) k_sort_offsets(KParams P, DevBufs B, int pass) {
-  sort_offsets_body(P, B, pass, blockIdx.x);
+template <int OFF_PER>
+__global__ void __launch_bounds__(OFF_BLOCK, OFF_PER <= 4 ? 8 : 1) k_sort_offsets(KParams P, DevBufs B, int pass) {
+  sort_offsets_body<OFF_PER>(P, B, pass, blockIdx.x);
 }
 
 __device__ __forceinline__ void sort_pass_body(const KParams &P, const DevBufs &B, const uint32_t *__restrict__ keys_in,
@@ -1398,20 +1407,28 @@ __device__ __forceinline__ void scan_tiles_body(const unsigned long long *__rest
     s_n[warp] = in;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long rq = 0ull;
-    uint32_t rn = 0u;
-    for (int w = 0; w < SCAN_BLOCK / 32; ++w) {
-      const unsigned long long tq = s_q[w];
-      const uint32_t tn = s_n[w];
-      s_q[w] = rq;
-      s_n[w] = rn;
-      rq += tq;
-      rn += tn;
+  static_assert(SCAN_BLOCK / 32 == 32, "one warp scans the warp totals");
+  if (warp == 0) {  // exclusive scan of the 32 warp totals by one warp
+    const unsigned long long vq = s_q[lane];
+    const uint32_t vn = s_n[lane];
+    unsigned long long xq = vq;
+    uint32_t xn = vn;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long tq = __shfl_up_sync(FULL, xq, o);
+      const uint32_t tn = __shfl_up_sync(FULL, xn, o);
+      if (lane >= (uint32_t)o) {
+        xq += tq;
+        xn += tn;
+      }
     }
-    *q_total = rq;
-    if (n_total) *n_total = rn;
-    if constexpr (SETUP) resample_setup(P, ctl, rq);
+    s_q[lane] = xq - vq;
+    s_n[lane] = xn - vn;
+    if (lane == 31) {
+      *q_total = xq;
+      if (n_total) *n_total = xn;
+      if constexpr (SETUP) resample_setup(P, ctl, xq);
+    }
   }
   __syncthreads();
   unsigned long long rq = s_q[warp] + iq - lq;
@@ -2101,7 +2118,7 @@ __device__ __forceinline__ void normalise_lidar_body(const KParams &P, const Dev
     atomicAdd(B.cdf_tile + tile, tsum);  // the newborn part of a mixed tile comes from k_birth
   }
 }
-__global__ void __launch_bounds__(NORM_BLOCK) k_normalise_lidar(KParams P, DevBufs B) {
+__global__ void __launch_bounds__(NORM_BLOCK, 8) k_normalise_lidar(KParams P, DevBufs B) {
   normalise_lidar_body(P, B, blockIdx.x);
 }
 
@@ -2250,7 +2267,7 @@ __device__ __forceinline__ void resample_body(const KParams &P, const DevBufs &B
     }
   }
 }
-__global__ void __launch_bounds__(RES_BLOCK, 3) k_resample(KParams P, DevBufs B) {
+__global__ void __launch_bounds__(RES_BLOCK, 4) k_resample(KParams P, DevBufs B) {
   resample_body(P, B, blockIdx.x);
 }
 
