@@ -238,7 +238,7 @@ int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
     if (ev) cudaEventRecord(ev[k], st);
   };
   mark();
-  k_tick<<<1, 256, 0, st>>>(B, 2048 * K.passes, K.tiles_norm);
+  k_tick<<<1, 1024, 0, st>>>(B, 2048 * K.passes, K.tiles_norm);
   if (K.flags & DOG_EGO) k_ego_warp<<<592, 256, 0, st>>>(K, B);  // timed with k_tick
   ++k; mark();
   const uint32_t pred_grid = (K.nu + PRED_TILE - 1) / PRED_TILE;
@@ -288,8 +288,8 @@ int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
   k_scan_tiles<false><<<1, SCAN_BLOCK, 0, st>>>(B.tile_q, B.tile_n, K.tiles_cell, B.tile_qin, B.tile_nin,
                                                  &B.ctl->R_total, &B.ctl->n_birth_cells, K, B.ctl);
   ++k; mark();
-  if (radar) k_birth_prep<true><<<K.tiles_cell, CELL_BLOCK, 0, st>>>(K, B);
-  else k_birth_prep<false><<<K.tiles_cell, CELL_BLOCK, 0, st>>>(K, B);
+  if (radar) k_birth_prep<true><<<K.tiles_cell, BPREP_BLOCK, 0, st>>>(K, B);
+  else k_birth_prep<false><<<K.tiles_cell, BPREP_BLOCK, 0, st>>>(K, B);
   ++k; mark();
   if (radar) k_birth<true><<<f->birth_grid, BIRTH_BLOCK, 0, st>>>(K, B);
   else k_birth<false><<<f->birth_grid, BIRTH_BLOCK, 0, st>>>(K, B);
@@ -681,8 +681,8 @@ int enqueue_group_frame(const std::vector<dog_filter *> &fs, cudaStream_t st) {
   if (batch_args(bf, A, lidar, cell)) kb_cell<false><<<A.first[A.n], CELL_BLOCK, 0, st>>>(A);
   if (batch_args(bf, A, radar, cell)) kb_cell<true><<<A.first[A.n], CELL_BLOCK, 0, st>>>(A);
   if (batch_args(bf, A, all, one)) kb_scan_tiles<false><<<A.first[A.n], SCAN_BLOCK, 0, st>>>(A);
-  if (batch_args(bf, A, lidar, cell)) kb_birth_prep<false><<<A.first[A.n], CELL_BLOCK, 0, st>>>(A);
-  if (batch_args(bf, A, radar, cell)) kb_birth_prep<true><<<A.first[A.n], CELL_BLOCK, 0, st>>>(A);
+  if (batch_args(bf, A, lidar, cell)) kb_birth_prep<false><<<A.first[A.n], BPREP_BLOCK, 0, st>>>(A);
+  if (batch_args(bf, A, radar, cell)) kb_birth_prep<true><<<A.first[A.n], BPREP_BLOCK, 0, st>>>(A);
   if (batch_args(bf, A, lidar, births)) kb_birth<false><<<A.first[A.n], BIRTH_BLOCK, 0, st>>>(A);
   if (batch_args(bf, A, radar, births)) kb_birth<true><<<A.first[A.n], BIRTH_BLOCK, 0, st>>>(A);
   if (batch_args(bf, A, lidar, pers)) kb_normalise_lidar<<<A.first[A.n], NORM_BLOCK, 0, st>>>(A);

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(SCAN_BLOCK) kb_scan_tiles(const __grid_constan
 }
 
 template <bool RADAR>
-__global__ void __launch_bounds__(CELL_BLOCK) kb_birth_prep(const __grid_constant__ BatchArgs A) {
+__global__ void __launch_bounds__(BPREP_BLOCK) kb_birth_prep(const __grid_constant__ BatchArgs A) {
   DOG_BATCH_PROLOGUE;
   birth_prep_body<RADAR>(P, B, bb.blk);
 }
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(256) kb_moments(const __grid_constant__ BatchA
   moments_body(P, B, bb.blk, bb.nblk);
 }
 
-__global__ void __launch_bounds__(RES_BLOCK, 3) kb_resample(const __grid_constant__ BatchArgs A) {
+__global__ void __launch_bounds__(RES_BLOCK, 5) kb_resample(const __grid_constant__ BatchArgs A) {
   DOG_BATCH_PROLOGUE;
   resample_body(P, B, bb.blk);
 }

@@ -1458,7 +1458,7 @@ __global__ void __launch_bounds__(SCAN_BLOCK)
 // order, its cells with newborn mass together with the tile-local inclusive prefix of the
 // fixed-point newborn masses; k_scan_tiles then scans the tile totals.
 // ====================================================================================
-constexpr int CELL_BLOCK = 256, CELL_ITEMS = 4, CELL_TILE = CELL_BLOCK * CELL_ITEMS;
+constexpr int CELL_BLOCK = 256, CELL_ITEMS = 2, CELL_TILE = CELL_BLOCK * CELL_ITEMS;
 
 __device__ __forceinline__ void cell_update(const KParams &P, float mp, float mFprev, float zO, float zF,
                                             float &mO, float &mF, float &rb) {
@@ -1728,6 +1728,7 @@ __device__ __forceinline__ void birth_init(const KParams &P, const DevBufs &B, u
 // block of BIRTH_SLOTS slots, the entry that owns the block's first slot.  One block per
 // cell tile.
 constexpr int BIRTH_SLOTS = 512, BIRTH_CACHE = 2048;
+constexpr int BPREP_BLOCK = 128;  // a cell tile's list holds a few birth cells on average
 
 template <bool RADAR>
 __device__ __forceinline__ void birth_prep_body(const KParams &P, const DevBufs &B, uint32_t blk) {
@@ -1738,7 +1739,7 @@ __device__ __forceinline__ void birth_prep_body(const KParams &P, const DevBufs 
   const uint32_t G0 = T > 0u ? B.tile_nin[T - 1u] : 0u;
   if (T == P.tiles_cell - 1u && threadIdx.x == 0) B.bl_first[B.tile_nin[T]] = P.nu_b;  // sentinel
   const uint32_t cnt = B.tile_n[T];
-  for (uint32_t e = threadIdx.x; e < cnt; e += CELL_BLOCK) {
+  for (uint32_t e = threadIdx.x; e < cnt; e += BPREP_BLOCK) {
     const size_t pos = (size_t)T * CELL_TILE + e;
     const uint32_t c = B.bl_cell[pos];
     const unsigned long long Rin = Tex + B.bl_R[pos];
@@ -1772,7 +1773,7 @@ __device__ __forceinline__ void birth_prep_body(const KParams &P, const DevBufs 
   }
 }
 template <bool RADAR>
-__global__ void __launch_bounds__(CELL_BLOCK) k_birth_prep(KParams P, DevBufs B) {
+__global__ void __launch_bounds__(BPREP_BLOCK) k_birth_prep(KParams P, DevBufs B) {
   birth_prep_body<RADAR>(P, B, blockIdx.x);
 }
 
@@ -2134,7 +2135,7 @@ __global__ void __launch_bounds__(NORM_BLOCK, 8) k_normalise_lidar(KParams P, De
 // Bsrc[i] with the equal weight W 2^-40 / nu (Eq. resampledParticleWeights), which the next
 // prediction reads through the index.
 // ====================================================================================
-constexpr int RES_BLOCK = 512, RES_ITEMS = NORM_TILE / RES_BLOCK;  // sources per thread
+constexpr int RES_BLOCK = 256, RES_ITEMS = NORM_TILE / RES_BLOCK;  // sources per thread
 constexpr int RES_RUN = 4;  // consecutive outputs per thread
 
 // count_theta_below by a warp: the 32 indices around the binary32 estimate are tested at
@@ -2267,7 +2268,7 @@ __device__ __forceinline__ void resample_body(const KParams &P, const DevBufs &B
     }
   }
 }
-__global__ void __launch_bounds__(RES_BLOCK, 4) k_resample(KParams P, DevBufs B) {
+__global__ void __launch_bounds__(RES_BLOCK, 6) k_resample(KParams P, DevBufs B) {
   resample_body(P, B, blockIdx.x);
 }
 
