@@ -891,7 +891,7 @@ int take_grid(dog_filter *f, const float *const src[5], int nfield, int kind, in
     for (int k = 0; k < nfield; ++k) gs.f[k] = f->B.g_stage + k * C;
   }
   // copy into place and validate in one pass
-  k_take_grid<<<592, 256, 0, f->st>>>(f->K, f->B, gs, kind);
+  k_take_grid<<<1184, 256, 0, f->st>>>(f->K, f->B, gs, kind);
   DOG_CUDA(cudaGetLastError());
   if (mem_kind != DOG_DEVICE) DOG_CUDA(cudaEventRecord(f->ev_stage_free, f->st));
   f->radar = radar;
@@ -1001,7 +1001,7 @@ int dog_get_cells_async(dog_filter *f, const dog_cells *out) {
   uint32_t *err_snap = reinterpret_cast<uint32_t *>(f->B.c_stage + 10 * C);
   CellSnap snap{};
   for (int k = 0; k < 10; ++k) snap.f[k] = dst[k] ? src[k] : nullptr;
-  k_snapshot<<<592, 256, 0, f->st>>>(snap, f->B.c_stage, (uint32_t)C, &f->B.ctl->err, err_snap);
+  k_snapshot<<<1184, 256, 0, f->st>>>(snap, f->B.c_stage, (uint32_t)C, &f->B.ctl->err, err_snap);
   DOG_CUDA(cudaGetLastError());
   DOG_CUDA(cudaEventRecord(f->ev_snap, f->st));
   DOG_CUDA(cudaStreamWaitEvent(f->d2h, f->ev_snap, 0));
