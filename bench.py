@@ -52,7 +52,6 @@ ALG_BYTES = {
     "k_birth": (0, 20, 0),        # write newborn state 16 + weight 4
     "k_normalise": (12, 0, 0),    # lidar, persistent sources: read key 4, w 4, write w' 4
     "k_resample": (8, 4, 0),      # read w' 4; write the source index 4; newborn w 4
-    "k_tick": (0, 0, 0),
 }
 
 

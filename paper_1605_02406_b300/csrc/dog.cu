@@ -139,7 +139,7 @@ size_t carve(const dog_params &p, const Derived &d, char *base, DevBufs *B) {
   return (off + 255) & ~(size_t)255;
 }
 
-const char *KNAMES[MAX_KERNELS] = {"k_tick", "k_predict", "k_sort_offsets0", "k_sort_pass0",
+const char *KNAMES[MAX_KERNELS] = {"k_ego_warp", "k_predict", "k_sort_offsets0", "k_sort_pass0",
                                    "k_sort_count1", "k_sort_offsets1", "k_sort_pass1",
                                    "k_sort_count2", "k_sort_offsets2", "k_sort_pass2",
                                    "k_segsum", "k_cell", "k_scan_births", "k_birth_prep", "k_birth",
@@ -238,9 +238,11 @@ int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
     if (ev) cudaEventRecord(ev[k], st);
   };
   mark();
-  k_tick<<<1, 1024, 0, st>>>(B, 2048 * K.passes, K.tiles_norm);
-  if (K.flags & DOG_EGO) k_ego_warp<<<592, 256, 0, st>>>(K, B);  // timed with k_tick
-  ++k; mark();
+  // no frame tick: the sort passes and the CDF scan reset what the frame accumulates into
+  if (K.flags & DOG_EGO) {
+    k_ego_warp<<<592, 256, 0, st>>>(K, B);
+    ++k; mark();
+  }
   const uint32_t pred_grid = (K.nu + PRED_TILE - 1) / PRED_TILE;
   k_predict<<<pred_grid, PRED_BLOCK, 4u * K.passes * K.radix, st>>>(K, B);
   ++k; mark();
@@ -488,7 +490,7 @@ int dog_create(const dog_params *params, void *d_workspace, size_t workspace_byt
   K.tiles_seg = d.tiles_seg;
   K.tiles_cell = d.tiles_cell;
   K.tiles_norm = d.tiles_norm;
-  f->nk = 9 + 3 * d.passes;
+  f->nk = 8 + 3 * d.passes;
   f->profile = (params->flags & DOG_PROFILE) != 0;
   f->use_graph = !(params->flags & DOG_NO_GRAPH) && f->st != nullptr && !f->profile;
   int dev = 0, sms = 148;
@@ -641,7 +643,6 @@ int enqueue_group_frame(const std::vector<dog_filter *> &fs, cudaStream_t st) {
   auto lidar = [](const dog_filter *f) { return !f->radar; };
   auto radar = [](const dog_filter *f) { return f->radar; };
   auto one = [](const dog_filter *) { return 1u; };
-  if (batch_args(bf, A, all, one)) kb_tick<<<A.first[A.n], 256, 0, st>>>(A);
   auto ego = [](const dog_filter *f) { return (f->K.flags & DOG_EGO) != 0; };
   if (batch_args(bf, A, ego, [](const dog_filter *f) { return std::min((f->K.C + 255) / 256, 592u); }))
     kb_ego_warp<<<A.first[A.n], 256, 0, st>>>(A);
@@ -1162,11 +1163,11 @@ int dog_profile_read(dog_filter *f, float *ms, const char **names, int max, int 
   if (!f || !ms || max <= 0) return DOG_ERR_INVALID_ARG;
   if (!f->profile) return DOG_ERR_BAD_STATE;
   DOG_CUDA(cudaStreamSynchronize(f->st));
-  // kernel slots in launch order: tick, predict, sort passes, segsum, cell, birth scan, birth
-  // prep, birth, normalise, CDF scan, resample
+  // kernel slots in launch order: ego-motion warp (DOG_EGO), predict, sort passes, segsum,
+  // cell, birth scan, birth prep, birth, normalise, CDF scan, resample
   int slot_kind[MAX_KERNELS];
   int nk = 0;
-  slot_kind[nk++] = 0;
+  if (f->p.flags & DOG_EGO) slot_kind[nk++] = 0;
   slot_kind[nk++] = 1;
   slot_kind[nk++] = 2;
   slot_kind[nk++] = 3;
@@ -1426,7 +1427,7 @@ void set_sort_cfg(dog_filter *f, int passes, uint32_t ct) {
   f->K.dbits = dbits;
   f->K.radix = 1u << dbits;
   f->count_ct = ct;
-  f->nk = 9 + 3 * passes;
+  f->nk = 8 + 3 * passes;
   f->cfg_version += 1;  // batches holding the filter capture again
   for (auto &g : f->gexec)  // the next step captures the frame again
     if (g) {

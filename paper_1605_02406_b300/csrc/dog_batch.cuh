@@ -58,12 +58,6 @@ __device__ __forceinline__ void batch_copy(BatchFilter &dst, const BatchFilter *
   const KParams &P = s_bf.P;        \
   const DevBufs &B = s_bf.B
 
-__global__ void kb_tick(const __grid_constant__ BatchArgs A) {
-  DOG_BATCH_PROLOGUE;
-  (void)bb;
-  tick_body(B, 2048 * P.passes, P.tiles_norm);
-}
-
 __global__ void kb_ego_warp(const __grid_constant__ BatchArgs A) {
   DOG_BATCH_PROLOGUE;
   ego_warp_body(P, B, bb.blk, bb.nblk);

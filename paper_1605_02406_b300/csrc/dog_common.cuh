@@ -12,7 +12,7 @@ constexpr uint32_t FULL = 0xffffffffu;
 enum : uint32_t { ERR_INPUT = 16u, ERR_INTERNAL = 32u };
 
 struct DevCtl {
-  uint32_t frame;          // incremented by k_tick at the start of every step
+  uint32_t frame;          // the last completed frame (advanced by the CDF scan, see this_frame)
   float dt;
   uint32_t err;
   uint32_t n_birth_cells;  // written by the newborn-mass tile scan
@@ -133,6 +133,13 @@ __device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) {
 __device__ __forceinline__ void st_volatile(uint32_t *p, uint32_t v) {
   *reinterpret_cast<volatile uint32_t *>(p) = v;
 }
+
+// The number of the frame being computed.  The control block holds the last completed
+// frame: the joint-weight CDF scan advances it once it has drawn the frame's resampling
+// offset, the last use of the number in a frame (every other kernel that reads it runs
+// before the scan: the newborn chain on the same stream, the normalisation branch joined
+// in before it).  Between frames it is the frame whose results the buffers hold.
+__device__ __forceinline__ uint32_t this_frame(const DevCtl *ctl) { return ctl->frame + 1u; }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;

@@ -1,7 +1,6 @@
 // dog_kernels.cuh -- the per-frame kernels of the DS-PHD/MIB filter (Sect. VII, Alg. 1-7).
 //
 // Frame data flow (nu persistent particles, nu_b newborn slots, C cells):
-//   k_tick        frame counter, reset of per-frame counters and digit histograms
 //   k_predict     Alg. 1  B -> A: constant-velocity prediction with Philox process noise,
 //                          persistence weight, cell index; digit histograms for the sort
 //   k_sort_count / k_sort_offsets / k_sort_pass
@@ -15,8 +14,11 @@
 //   k_normalise   Alg. 4/6 normalised persistent weights, velocity moment sums, tile sums
 //                          of the joint weights
 //   k_moments     Alg. 6  (radar filter) the cells' velocity moments from those sums
-//   k_scan_tiles          CDF of the joint weights over tiles
+//   k_scan_tiles          CDF of the joint weights over tiles; the frame counter advanced
 //   k_resample    Alg. 7  systematic resampling A + newborns -> B
+// What a frame accumulates into is cleared by its last reader within the frame (each sort
+// pass its digit histogram, the CDF scan the joint-weight tile sums), so a frame needs no
+// separate start-of-frame kernel.
 // No block waits for another block of the same launch: every cross-block dependency is a
 // kernel boundary.
 #pragma once
@@ -26,7 +28,10 @@
 namespace dog {
 
 // ====================================================================================
-// k_tick: begin a frame
+// k_tick: reset of the digit histograms and the joint-weight tile sums, and the frame
+// counter advanced.  A filter's frames need no tick: each sort pass clears its digit
+// histogram once the offsets are taken from it, and the CDF scan clears the tile sums it
+// reads and advances the counter (this_frame).  The allocation-free sort starts with one.
 // ====================================================================================
 __device__ __forceinline__ void tick_body(const DevBufs &B, int n_hist, uint32_t n_cdf) {
   for (int i = threadIdx.x; i < n_hist; i += blockDim.x) B.hist[i] = 0u;
@@ -293,7 +298,7 @@ __device__ __forceinline__ void predict_body(const KParams &P, const DevBufs &B,
   const uint32_t nh = (uint32_t)P.passes * P.radix;
   for (uint32_t k = threadIdx.x; k < nh; k += PRED_BLOCK) sh_hist[k] = 0u;
   __syncthreads();
-  const uint32_t frame = B.ctl->frame;
+  const uint32_t frame = this_frame(B.ctl);
   const float T = B.ctl->dt;
   const uint32_t mode = B.ctl->post_mode;
   const float w_res = B.ctl->w_new;
@@ -664,6 +669,10 @@ __device__ __forceinline__ void sort_pass_body(const KParams &P, const DevBufs &
     const uint32_t d = tid + j * SORT_BLOCK;
     offr[j] = d < radix ? __ldg(off + (size_t)d * P.tiles_sort) : 0u;
   }
+  // the pass's digit histogram was read by k_sort_offsets: cleared here for the next
+  // frame's prediction, which adds into it
+  if (tile == 0u)
+    for (uint32_t d = tid; d < radix; d += SORT_BLOCK) B.hist[pass * 2048u + d] = 0u;
   // warp counters cleared with 16-byte stores (SORT_WARPS * radix * 2 bytes, a multiple of 16)
   for (uint32_t k = tid; k < SORT_WARPS * radix / 8; k += SORT_BLOCK)
     reinterpret_cast<uint4 *>(s_whist)[k] = make_uint4(0u, 0u, 0u, 0u);
@@ -1028,7 +1037,7 @@ __device__ __forceinline__ void segsum_body(const KParams &P, const DevBufs &B, 
   constexpr int N = RADAR ? 2 : 1;
   __shared__ Seg<N> s_w[SEG_BLOCK / 32 + 1];
   __shared__ unsigned long long s_q[N][SEG_PADDED];
-  const uint32_t tile = blk, frame = B.ctl->frame;
+  const uint32_t tile = blk, frame = this_frame(B.ctl);
   const uint32_t base = tile * SEG_TILE;
   const uint32_t last_valid = min(base + SEG_TILE, P.nu) - 1u;
   // gather phase, warp-striped: position base + it*256 + threadIdx.x.  All permutation
@@ -1161,7 +1170,7 @@ __global__ void __launch_bounds__(SEG_BLOCK) k_segsum(KParams P, DevBufs B) {
 __device__ __forceinline__ void segsum_lidar_body(const KParams &P, const DevBufs &B, uint32_t blk) {
   __shared__ SegQM s_wqm[SEG_BLOCK / 32 + 1];
   __shared__ float s_x[3][SEG_PADDED];  // w, vx, vy in tile order (padded)
-  const uint32_t tile = blk, frame = B.ctl->frame;
+  const uint32_t tile = blk, frame = this_frame(B.ctl);
   const uint32_t base = tile * SEG_TILE;
   const uint32_t last_valid = min(base + SEG_TILE, P.nu) - 1u;
   // gather phase, warp-striped, all loads in flight before the stores.  After a resampled
@@ -1304,7 +1313,7 @@ __device__ void resample_setup(const KParams &P, DevCtl *ctl, unsigned long long
     return;
   }
   ctl->post_mode = POST_RESAMPLED;
-  const U4 r = philox(0u, ctl->frame, TAG_RESAMPLE, P.seed_lo, P.seed_hi);
+  const U4 r = philox(0u, this_frame(ctl), TAG_RESAMPLE, P.seed_lo, P.seed_hi);
   const unsigned long long r64 = ((unsigned long long)r.a << 32) | r.b;
   const unsigned long long u = __umul64hi(r64, Wt);
   ctl->u_offset = u;
@@ -1374,8 +1383,10 @@ __device__ __forceinline__ uint32_t count_theta_below(const Theta &T, unsigned l
   return i;
 }
 
+// SETUP (the joint-weight CDF): the per-frame resampling constants, the tile sums q cleared
+// for the next frame once read, and the frame counter advanced (this_frame)
 template <bool SETUP>
-__device__ __forceinline__ void scan_tiles_body(const unsigned long long *__restrict__ q, const uint32_t *__restrict__ n,
+__device__ __forceinline__ void scan_tiles_body(unsigned long long *q, const uint32_t *__restrict__ n,
                                                 uint32_t count, unsigned long long *q_incl, uint32_t *n_incl,
                                                 unsigned long long *q_total, uint32_t *n_total, const KParams &P,
                                                 DevCtl *ctl) {
@@ -1427,7 +1438,10 @@ __device__ __forceinline__ void scan_tiles_body(const unsigned long long *__rest
     if (lane == 31) {
       *q_total = xq;
       if (n_total) *n_total = xn;
-      if constexpr (SETUP) resample_setup(P, ctl, xq);
+      if constexpr (SETUP) {
+        resample_setup(P, ctl, xq);
+        ctl->frame += 1u;  // the frame's last reader of its number is done
+      }
     }
   }
   __syncthreads();
@@ -1436,6 +1450,7 @@ __device__ __forceinline__ void scan_tiles_body(const unsigned long long *__rest
   for (uint32_t k = 0; k < per; ++k)
     if (b + k < count) {
       rq += q[b + k];
+      if constexpr (SETUP) q[b + k] = 0ull;  // for the next frame's atomics
       q_incl[b + k] = rq;
       if (n) {
         rn += n[b + k];
@@ -1445,7 +1460,7 @@ __device__ __forceinline__ void scan_tiles_body(const unsigned long long *__rest
 }
 template <bool SETUP>
 __global__ void __launch_bounds__(SCAN_BLOCK)
-    k_scan_tiles(const unsigned long long *__restrict__ q, const uint32_t *__restrict__ n, uint32_t count,
+    k_scan_tiles(unsigned long long *q, const uint32_t *__restrict__ n, uint32_t count,
                  unsigned long long *q_incl, uint32_t *n_incl, unsigned long long *q_total,
                  uint32_t *n_total, KParams P, DevCtl *ctl) {
   scan_tiles_body<SETUP>(q, n, count, q_incl, n_incl, q_total, n_total, P, ctl);
@@ -1489,7 +1504,7 @@ template <bool RADAR>
 __device__ __forceinline__ void cell_body(const KParams &P, const DevBufs &B, uint32_t blk) {
   __shared__ unsigned long long s_wq[CELL_BLOCK / 32 + 1];
   __shared__ uint32_t s_wn[CELL_BLOCK / 32 + 1];
-  const uint32_t tile = blk, frame = B.ctl->frame;
+  const uint32_t tile = blk, frame = this_frame(B.ctl);
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned long long qin[CELL_ITEMS];
   uint32_t nex[CELL_ITEMS];
@@ -1816,7 +1831,7 @@ __device__ __forceinline__ void birth_tile_sums(const DevBufs &B, unsigned long 
 template <bool RADAR>
 __device__ __forceinline__ void birth_body(const KParams &P, const DevBufs &B, uint32_t blk) {
   __shared__ uint32_t s_first[BIRTH_CACHE + 1];
-  const uint32_t frame = B.ctl->frame;
+  const uint32_t frame = this_frame(B.ctl);
   const unsigned long long R = B.ctl->R_total;
   const bool record = (P.flags & 0x4u) != 0u;
   const uint32_t s0 = blk * BIRTH_SLOTS;
@@ -2058,7 +2073,7 @@ __global__ void __launch_bounds__(NORM_BLOCK, 4) k_normalise(KParams P, DevBufs 
 // inside one normalisation tile) or from its exact fixed-point pieces (a cell spread over
 // several; read and cleared for the next frame); 0 where rho_p = 0.
 __device__ __forceinline__ void moments_body(const KParams &P, const DevBufs &B, uint32_t blk, uint32_t nblk) {
-  const uint32_t frame = B.ctl->frame;
+  const uint32_t frame = this_frame(B.ctl);
   const size_t Cs = P.C;
   for (uint32_t c = blk * blockDim.x + threadIdx.x; c < P.C; c += nblk * blockDim.x) {
     const uint32_t tag = B.csum[c].tag;
@@ -2136,7 +2151,7 @@ __global__ void __launch_bounds__(NORM_BLOCK, 8) k_normalise_lidar(KParams P, De
 // prediction reads through the index.
 // ====================================================================================
 constexpr int RES_BLOCK = 256, RES_ITEMS = NORM_TILE / RES_BLOCK;  // sources per thread
-constexpr int RES_RUN = 4;  // consecutive outputs per thread
+constexpr int RES_RUN = 3;  // consecutive outputs per thread
 
 // count_theta_below by a warp: the 32 indices around the binary32 estimate are tested at
 // once (theta is non-decreasing, so the lanes below the count form a prefix); outside that
