@@ -187,7 +187,7 @@ def test_config1_scene_from_initial_state():
 
 
 @pytest.mark.parametrize("case", ["tiny", "no_births", "empty_grid", "no_resample", "single_cell",
-                                  "one_particle", "three_sort_passes"])
+                                  "one_particle", "three_sort_passes", "offset_run_of_eight"])
 def test_edge_cases(case):
     rng = np.random.default_rng(13)
     if case == "tiny":
@@ -202,6 +202,10 @@ def test_edge_cases(case):
         p = small(1, 1, nu=700, nu_b=30)
     elif case == "one_particle":
         p = small(8, 8, nu=1, nu_b=3)
+    elif case == "offset_run_of_eight":
+        # 1,465 sort tiles: the digit-offset kernel holds runs of up to eight tiles a thread
+        # (1,024 tiles and fewer take four, up to 4,096 sixteen, more go through memory)
+        p = small(512, 512, nu=6_000_000, nu_b=60_000)
     else:  # 2^23 cells need a third 8-bit digit pass
         p = small(4096, 2048, nu=9000, nu_b=500, cell_size=0.05)
     W, H = p["width"], p["height"]
