@@ -175,7 +175,7 @@ struct dog_filter {
   cudaStream_t h2d = nullptr, d2h = nullptr;
   // the second branch of a frame (normalisation beside the newborn chain)
   cudaStream_t aux = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_mjoin = nullptr;
   cudaEvent_t ev_h2d = nullptr, ev_stage_free = nullptr, ev_snap = nullptr, ev_d2h = nullptr;
   bool d2h_pending = false;
   uint32_t *d2h_err = nullptr;  // pinned host word: error bits of the frame being read back
@@ -211,24 +211,31 @@ void launch_offsets(const KParams &K, const DevBufs &B, int p, cudaStream_t st) 
     if (e_ != cudaSuccess) return cuda_fail(e_); \
   } while (0)
 
-// the normalisation of the persistent sources (Alg. 4) and, for the radar filter, the
-// velocity moments (Alg. 6), on stream st
+// the normalisation of the persistent sources (Alg. 4), on stream st
 int enqueue_normalise(dog_filter *f, bool radar, cudaStream_t st) {
   const KParams &K = f->K;
   const DevBufs &B = f->B;
   const uint32_t tiles = (K.nu + NORM_TILE - 1) / NORM_TILE;
-  if (radar) {
-    k_normalise<true><<<tiles, NORM_BLOCK, 0, st>>>(K, B);
-    k_moments<<<(K.C + 255) / 256 < 2368u ? (K.C + 255) / 256 : 2368u, 256, 0, st>>>(K, B);
-  } else {
-    k_normalise_lidar<<<tiles, NORM_BLOCK, 0, st>>>(K, B);
-  }
+  if (radar) k_normalise<true><<<tiles, NORM_BLOCK, 0, st>>>(K, B);
+  else k_normalise_lidar<<<tiles, NORM_BLOCK, 0, st>>>(K, B);
+  return cuda_fail(cudaGetLastError());
+}
+
+// the radar filter's velocity moments (Alg. 6) from the normalised weights, on stream st
+int enqueue_radar_moments(dog_filter *f, cudaStream_t st) {
+  const KParams &K = f->K;
+  const DevBufs &B = f->B;
+  const uint32_t tiles = (K.nu + NORM_TILE - 1) / NORM_TILE;
+  k_rmsum<<<tiles, NORM_BLOCK, 0, st>>>(K, B);
+  k_moments<<<(K.C + 255) / 256 < 2368u ? (K.C + 255) / 256 : 2368u, 256, 0, st>>>(K, B);
   return cuda_fail(cudaGetLastError());
 }
 
 // the kernels of one frame, in order; ev (optional, profiling) are recorded around each
 // kernel, which are then issued one after the other on the filter's stream; otherwise the
-// normalisation runs on a second branch beside the newborn chain
+// normalisation runs on a second branch beside the newborn chain, and the radar filter's
+// velocity moments continue that branch beside the CDF scan and the resampling, joined at
+// the end of the frame
 int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
   const KParams &K = f->K;
   const DevBufs &B = f->B;
@@ -283,9 +290,14 @@ int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
   if (!ev) {
     DOG_CUDA(cudaEventRecord(f->ev_fork, st));
     DOG_CUDA(cudaStreamWaitEvent(f->aux, f->ev_fork, 0));
-    const int rc = enqueue_normalise(f, radar, f->aux);
+    int rc = enqueue_normalise(f, radar, f->aux);
     if (rc) return rc;
     DOG_CUDA(cudaEventRecord(f->ev_join, f->aux));
+    if (radar) {
+      rc = enqueue_radar_moments(f, f->aux);
+      if (rc) return rc;
+      DOG_CUDA(cudaEventRecord(f->ev_mjoin, f->aux));
+    }
   }
   k_scan_tiles<false><<<1, SCAN_BLOCK, 0, st>>>(B.tile_q, B.tile_n, K.tiles_cell, B.tile_qin, B.tile_nin,
                                                  &B.ctl->R_total, &B.ctl->n_birth_cells, K, B.ctl);
@@ -299,7 +311,8 @@ int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
   if (!ev) {  // the normalisation ran on the second branch; the CDF scan waits for both
     DOG_CUDA(cudaStreamWaitEvent(st, f->ev_join, 0));
   } else {
-    const int rc = enqueue_normalise(f, radar, st);
+    int rc = enqueue_normalise(f, radar, st);
+    if (rc == DOG_OK && radar) rc = enqueue_radar_moments(f, st);  // timed with the normalisation
     if (rc) return rc;
   }
   ++k; mark();
@@ -308,6 +321,7 @@ int enqueue_frame(dog_filter *f, bool radar, cudaEvent_t *ev) {
   ++k; mark();
   k_resample<<<K.tiles_norm, RES_BLOCK, 0, st>>>(K, B);
   ++k; mark();
+  if (!ev && radar) DOG_CUDA(cudaStreamWaitEvent(st, f->ev_mjoin, 0));  // the moments' branch
   return cuda_fail(cudaGetLastError());
 }
 
@@ -413,8 +427,8 @@ int dog_workspace_bytes(const dog_params *params, size_t *out_bytes) {
 
 int dog_kernels_per_step(const dog_filter *f) {
   if (!f) return 0;
-  // + the radar filter's moment kernel, + the ego-motion setting and warp
-  return f->nk + (f->radar ? 1 : 0) + ((f->p.flags & DOG_EGO) ? 2 : 0);
+  // + the radar filter's two moment kernels, + the ego-motion setting and warp
+  return f->nk + (f->radar ? 2 : 0) + ((f->p.flags & DOG_EGO) ? 2 : 0);
 }
 
 static_assert(FLAG_EGO == DOG_EGO, "the kernels' ego flag is the ABI's");
@@ -515,7 +529,7 @@ int dog_create(const dog_params *params, void *d_workspace, size_t workspace_byt
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&f->d2h, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&f->aux, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMallocHost(&f->d2h_err, 64);  // pinned: the copy stays asynchronous
-  cudaEvent_t *evs[] = {&f->ev_h2d, &f->ev_stage_free, &f->ev_snap, &f->ev_d2h, &f->ev_fork, &f->ev_join};
+  cudaEvent_t *evs[] = {&f->ev_h2d, &f->ev_stage_free, &f->ev_snap, &f->ev_d2h, &f->ev_fork, &f->ev_join, &f->ev_mjoin};
   for (auto q : evs)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(q, cudaEventDisableTiming);
   if (e == cudaSuccess && f->profile) {
@@ -688,6 +702,7 @@ int enqueue_group_frame(const std::vector<dog_filter *> &fs, cudaStream_t st) {
   if (batch_args(bf, A, radar, births)) kb_birth<true><<<A.first[A.n], BIRTH_BLOCK, 0, st>>>(A);
   if (batch_args(bf, A, lidar, pers)) kb_normalise_lidar<<<A.first[A.n], NORM_BLOCK, 0, st>>>(A);
   if (batch_args(bf, A, radar, pers)) kb_normalise_radar<<<A.first[A.n], NORM_BLOCK, 0, st>>>(A);
+  if (batch_args(bf, A, radar, pers)) kb_rmsum<<<A.first[A.n], NORM_BLOCK, 0, st>>>(A);
   if (batch_args(bf, A, radar, [](const dog_filter *f) { return std::min((f->K.C + 255) / 256, 2368u); }))
     kb_moments<<<A.first[A.n], 256, 0, st>>>(A);
   if (batch_args(bf, A, all, one)) kb_scan_tiles<true><<<A.first[A.n], SCAN_BLOCK, 0, st>>>(A);
@@ -862,7 +877,7 @@ void dog_destroy(dog_filter *f) {
       cudaStreamSynchronize(x);
       cudaStreamDestroy(x);
     }
-  for (auto x : {f->ev_h2d, f->ev_stage_free, f->ev_snap, f->ev_d2h, f->ev_fork, f->ev_join})
+  for (auto x : {f->ev_h2d, f->ev_stage_free, f->ev_snap, f->ev_d2h, f->ev_fork, f->ev_join, f->ev_mjoin})
     if (x) cudaEventDestroy(x);
   if (f->d2h_err) cudaFreeHost(f->d2h_err);
   for (auto &g : f->gexec)

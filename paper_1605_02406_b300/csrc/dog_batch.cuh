@@ -143,9 +143,14 @@ __global__ void __launch_bounds__(BIRTH_BLOCK) kb_birth(const __grid_constant__ 
   birth_body<RADAR>(P, B, bb.blk);
 }
 
-__global__ void __launch_bounds__(NORM_BLOCK, 4) kb_normalise_radar(const __grid_constant__ BatchArgs A) {
+__global__ void __launch_bounds__(NORM_BLOCK) kb_normalise_radar(const __grid_constant__ BatchArgs A) {
   DOG_BATCH_PROLOGUE;
   normalise_body<true>(P, B, bb.blk);
+}
+
+__global__ void __launch_bounds__(NORM_BLOCK, 4) kb_rmsum(const __grid_constant__ BatchArgs A) {
+  DOG_BATCH_PROLOGUE;
+  rmsum_body(P, B, bb.blk);
 }
 
 __global__ void __launch_bounds__(NORM_BLOCK, 8) kb_normalise_lidar(const __grid_constant__ BatchArgs A) {

@@ -31,6 +31,9 @@ struct DevCtl {
   // whose cosine and sine are ego_c, ego_s, about the sensor position; ego_on = 0: none
   uint32_t ego_on;
   float ego_c, ego_s, ego_dx, ego_dy;
+  // the frame whose radar velocity moments k_moments finishes: written by k_normalise,
+  // which runs before the CDF scan advances the frame counter (k_moments runs beside it)
+  uint32_t frame_mom;
 };
 
 // How the posterior particles are held between frames:
@@ -136,9 +139,10 @@ __device__ __forceinline__ void st_volatile(uint32_t *p, uint32_t v) {
 
 // The number of the frame being computed.  The control block holds the last completed
 // frame: the joint-weight CDF scan advances it once it has drawn the frame's resampling
-// offset, the last use of the number in a frame (every other kernel that reads it runs
-// before the scan: the newborn chain on the same stream, the normalisation branch joined
-// in before it).  Between frames it is the frame whose results the buffers hold.
+// offset.  Every other kernel that reads it runs before the scan (the newborn chain on the
+// same stream, the normalisation joined in before it), except the radar filter's k_moments
+// beside it, which reads the number that k_normalise kept (DevCtl::frame_mom).  Between
+// frames it is the frame whose results the buffers hold.
 __device__ __forceinline__ uint32_t this_frame(const DevCtl *ctl) { return ctl->frame + 1u; }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {

@@ -11,9 +11,9 @@
 //   k_scan_tiles          prefix of the tiles' newborn masses
 //   k_birth_prep  Alg. 5  slot range, associated share and weights of each birth cell
 //   k_birth       Alg. 5  newborn particles, slots proportional to the newborn mass
-//   k_normalise   Alg. 4/6 normalised persistent weights, velocity moment sums, tile sums
-//                          of the joint weights
-//   k_moments     Alg. 6  (radar filter) the cells' velocity moments from those sums
+//   k_normalise   Alg. 4  normalised persistent weights, tile sums of the joint weights
+//                          (the lidar filter's velocity moments were summed in k_segsum_lidar)
+//   k_rmsum / k_moments  Alg. 6  (radar filter) the cells' velocity moments from w'
 //   k_scan_tiles          CDF of the joint weights over tiles; the frame counter advanced
 //   k_resample    Alg. 7  systematic resampling A + newborns -> B
 // What a frame accumulates into is cleared by its last reader within the frame (each sort
@@ -1919,17 +1919,12 @@ __global__ void __launch_bounds__(BIRTH_BLOCK) k_birth(KParams P, DevBufs B) {
 }
 
 // ====================================================================================
-// k_normalise (Alg. 4 / Alg. 6): over the joint source index space (persistent particles
-// in sorted order, read contiguously from the sorted copy, then newborn slots):
+// k_normalise (Alg. 4): over the joint source index space (persistent particles in sorted
+// order, read contiguously from the sorted copy, then newborn slots):
 //   w' = p_A mu_A g w + (1 - p_A) mu_UA w   (Eq. DSnormalization; lidar cells: mu_UA w),
-//   velocity moments of the persistent particles per cell (Eq. mean_x, var_x, covar_xy):
-//   the terms w' v, w' v^2, w' vx vy are formed as exact double-float products and summed
-//   by the block's segmented scan with compensated additions; a cell inside the tile leaves
-//   its sums in its moment record; a cell spread over several tiles adds its pieces,
-//   divided by rho_p, in exact 2^-40 fixed point with integer atomics; k_moments finishes
-//   both;
 //   and the persistent part of the tile sums of q40 of the joint weights for the resampling
-//   CDF (k_birth adds the newborn part).  The grid covers the persistent sources only.
+//   CDF (k_birth adds the newborn part).  The grid covers the persistent sources only.  The
+//   radar filter's velocity moments (Alg. 6) follow in k_rmsum and k_moments.
 // ====================================================================================
 constexpr int NORM_BLOCK = 256, NORM_ITEMS = 8, NORM_TILE = NORM_BLOCK * NORM_ITEMS;
 static_assert(NORM_TILE == NORM_TILE_, "the newborn kernel's resampling tile");
@@ -1940,52 +1935,32 @@ static_assert(NORM_BLOCK == SEG_BLOCK, "k_normalise shares the segment pass's bl
 __device__ __forceinline__ uint32_t norm_pad(uint32_t m) { return m + m / NORM_ITEMS; }
 constexpr int NORM_PADDED = NORM_TILE + NORM_TILE / NORM_ITEMS;
 
+// the radar filter's normalisation: w' per persistent source and the tile's part of the
+// joint quantised weights (the velocity moments follow in k_rmsum)
 template <bool RADAR>
 __device__ __forceinline__ void normalise_body(const KParams &P, const DevBufs &B, uint32_t blk) {
-  __shared__ SegMom s_w[NORM_BLOCK / 32 + 1];
   __shared__ unsigned long long s_red[NORM_BLOCK / 32];
-  __shared__ float s_t[3][NORM_PADDED];  // w', vx, vy of the tile's items, for the tail pass
   const uint32_t tile = blk;
   const uint32_t j0 = tile * NORM_TILE + threadIdx.x * NORM_ITEMS;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned long long qsum = 0ull;
-  const bool has_pers = tile * NORM_TILE < P.nu;  // block-uniform
-  uint32_t key[NORM_ITEMS];
-  uint32_t head = 0, tail = 0;
-  SegMom agg;
-  agg = seg_zero(agg);
-  if (has_pers) {
+  if (tile * NORM_TILE < P.nu) {  // block-uniform
+    uint32_t key[NORM_ITEMS];
     float ws[NORM_ITEMS], gs[NORM_ITEMS];
     load_run<NORM_ITEMS>(B.key_sorted, j0, P.nu, key, 0xffffffffu);
     load_runf<NORM_ITEMS>(B.Ow, j0, P.nu, ws);
     // the radar likelihood g of each particle, left in wn by k_segsum (for every particle of
     // a cell with p_A > 0, which includes every cell with an effective p_A > 0)
     if (RADAR) load_runf<NORM_ITEMS>(B.wn, j0, P.nu, gs);
-    float mvx[NORM_ITEMS], mvy[NORM_ITEMS], wnv[NORM_ITEMS];
-#pragma unroll
-    for (int it = 0; it < NORM_ITEMS; ++it) {
-      const float4 st = j0 + it < P.nu ? __ldg(B.Os + j0 + it) : make_float4(0.f, 0.f, 0.f, 0.f);
-      mvx[it] = st.z;
-      mvy[it] = st.w;
-    }
-    const uint32_t kprev = (j0 > 0 && j0 <= P.nu) ? __ldg(B.key_sorted + j0 - 1) : 0xfffffffeu;
-    const uint32_t knext = (j0 + NORM_ITEMS < P.nu) ? __ldg(B.key_sorted + j0 + NORM_ITEMS) : 0xfffffffeu;
     // per-cell factors of all items before any arithmetic (independent loads in flight)
     float cmu[NORM_ITEMS];
 #pragma unroll
     for (int it = 0; it < NORM_ITEMS; ++it) cmu[it] = j0 + it < P.nu ? __ldg(B.muU + key[it]) : 0.0f;
+    float wnv[NORM_ITEMS];
 #pragma unroll
     for (int it = 0; it < NORM_ITEMS; ++it) {
-      const uint32_t j = j0 + it;
-      const bool ok = j < P.nu;
-      const uint32_t kp = it == 0 ? kprev : key[it - 1];
-      const uint32_t kn = it == NORM_ITEMS - 1 ? knext : key[it + 1];
-      const bool h = ok && (j == 0 || key[it] != kp);
-      const bool t = ok && (j == P.nu - 1 || key[it] != kn);
-      head |= (uint32_t)h << it;
-      tail |= (uint32_t)t << it;
       wnv[it] = 0.0f;
-      if (ok) {
+      if (j0 + it < P.nu) {
         const uint32_t c = key[it];
         const float w = ws[it];
         const float muU = cmu[it];
@@ -2002,14 +1977,6 @@ __device__ __forceinline__ void normalise_body(const KParams &P, const DevBufs &
         wnv[it] = wn;
         qsum += q40(wn);
       }
-      SegMom e;
-      e.f = h;
-      moment_terms(wnv[it], mvx[it], mvy[it], e.m);
-      agg = seg_combine(agg, e);
-      const uint32_t m = norm_pad(threadIdx.x * NORM_ITEMS + it);
-      s_t[0][m] = wnv[it];
-      s_t[1][m] = mvx[it];
-      s_t[2][m] = mvy[it];
     }
     store_run<NORM_ITEMS>(B.wn, j0, P.nu, wnv);
   }
@@ -2023,8 +1990,65 @@ __device__ __forceinline__ void normalise_body(const KParams &P, const DevBufs &
     unsigned long long tsum = 0ull;
     for (int w = 0; w < NORM_BLOCK / 32; ++w) tsum += s_red[w];
     atomicAdd(B.cdf_tile + tile, tsum);
+    if (tile == 0u) B.ctl->frame_mom = this_frame(B.ctl);  // for k_moments
   }
-  if (!has_pers) return;  // block-uniform
+}
+template <bool RADAR>
+__global__ void __launch_bounds__(NORM_BLOCK) k_normalise(KParams P, DevBufs B) {
+  normalise_body<RADAR>(P, B, blockIdx.x);
+}
+
+// k_rmsum (radar filter, after k_normalise, beside the CDF scan and the resampling: nothing
+// later in the frame reads the moments): the velocity moments of the persistent particles
+// per cell (Eq. mean_x, var_x, covar_xy) from the normalised weights w' the normalisation
+// left in wn.  The terms w' v, w' v^2, w' vx vy are formed as exact double-float products
+// and summed by the block's segmented scan with compensated additions; a cell inside the
+// tile leaves its sums in its moment record; a cell spread over several tiles adds its
+// pieces, divided by rho_p, in exact 2^-40 fixed point with integer atomics; k_moments
+// finishes both.
+__device__ __forceinline__ void rmsum_body(const KParams &P, const DevBufs &B, uint32_t blk) {
+  __shared__ SegMom s_w[NORM_BLOCK / 32 + 1];
+  __shared__ float s_t[3][NORM_PADDED];  // w', vx, vy of the tile's items, for the tail pass
+  const uint32_t tile = blk;
+  if (tile * NORM_TILE >= P.nu) return;  // block-uniform
+  const uint32_t j0 = tile * NORM_TILE + threadIdx.x * NORM_ITEMS;
+  uint32_t key[NORM_ITEMS];
+  uint32_t head = 0, tail = 0;
+  SegMom agg;
+  agg = seg_zero(agg);
+  {
+    float wnv[NORM_ITEMS];
+    load_run<NORM_ITEMS>(B.key_sorted, j0, P.nu, key, 0xffffffffu);
+    load_runf<NORM_ITEMS>(B.wn, j0, P.nu, wnv);
+    float mvx[NORM_ITEMS], mvy[NORM_ITEMS];
+#pragma unroll
+    for (int it = 0; it < NORM_ITEMS; ++it) {
+      const float4 st = j0 + it < P.nu ? __ldg(B.Os + j0 + it) : make_float4(0.f, 0.f, 0.f, 0.f);
+      mvx[it] = st.z;
+      mvy[it] = st.w;
+    }
+    const uint32_t kprev = (j0 > 0 && j0 <= P.nu) ? __ldg(B.key_sorted + j0 - 1) : 0xfffffffeu;
+    const uint32_t knext = (j0 + NORM_ITEMS < P.nu) ? __ldg(B.key_sorted + j0 + NORM_ITEMS) : 0xfffffffeu;
+#pragma unroll
+    for (int it = 0; it < NORM_ITEMS; ++it) {
+      const uint32_t j = j0 + it;
+      const bool ok = j < P.nu;
+      const uint32_t kp = it == 0 ? kprev : key[it - 1];
+      const uint32_t kn = it == NORM_ITEMS - 1 ? knext : key[it + 1];
+      const bool h = ok && (j == 0 || key[it] != kp);
+      const bool t = ok && (j == P.nu - 1 || key[it] != kn);
+      head |= (uint32_t)h << it;
+      tail |= (uint32_t)t << it;
+      SegMom e;
+      e.f = h;
+      moment_terms(wnv[it], mvx[it], mvy[it], e.m);
+      agg = seg_combine(agg, e);
+      const uint32_t m = norm_pad(threadIdx.x * NORM_ITEMS + it);
+      s_t[0][m] = wnv[it];
+      s_t[1][m] = mvx[it];
+      s_t[2][m] = mvy[it];
+    }
+  }
   // segmented compensated moment sums within the tile
   const SegMom ex = block_seg_excl(agg, s_w);
   const uint32_t last_valid = min(tile * NORM_TILE + NORM_TILE, P.nu) - 1u;
@@ -2063,17 +2087,14 @@ __device__ __forceinline__ void normalise_body(const KParams &P, const DevBufs &
     }
   }
 }
-template <bool RADAR>
-__global__ void __launch_bounds__(NORM_BLOCK, 4) k_normalise(KParams P, DevBufs B) {
-  normalise_body<RADAR>(P, B, blockIdx.x);
-}
+__global__ void __launch_bounds__(NORM_BLOCK, 4) k_rmsum(KParams P, DevBufs B) { rmsum_body(P, B, blockIdx.x); }
 
-// k_moments (radar filter, after k_normalise): the velocity moments of every cell with
+// k_moments (radar filter, after k_rmsum): the velocity moments of every cell with
 // particles this frame from its compensated sums of w' v, ... divided by rho_p (a cell
 // inside one normalisation tile) or from its exact fixed-point pieces (a cell spread over
 // several; read and cleared for the next frame); 0 where rho_p = 0.
 __device__ __forceinline__ void moments_body(const KParams &P, const DevBufs &B, uint32_t blk, uint32_t nblk) {
-  const uint32_t frame = this_frame(B.ctl);
+  const uint32_t frame = B.ctl->frame_mom;  // the counter itself may have advanced already
   const size_t Cs = P.C;
   for (uint32_t c = blk * blockDim.x + threadIdx.x; c < P.C; c += nblk * blockDim.x) {
     const uint32_t tag = B.csum[c].tag;
