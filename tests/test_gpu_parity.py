@@ -265,6 +265,26 @@ def test_ego_motion_frames(flags):
         compare_frame(g, o, what=f"frame {k}: ")
 
 
+def test_ego_motion_radar_frames():
+    """Ego motion with radar grids (the likelihood g of the moved particles, the radar
+    moments on their own graph branch) bit for bit against the oracle over four frames."""
+    p = small(48, 37, nu=3 * 4096 + 1234, nu_b=2 * 2048 + 77, flags=RECORD | EGO)
+    rng = np.random.default_rng(16)
+    st = scene.random_state(p, rng, occupied_frac=0.1)
+    grids = [scene.random_measurement_grid(48, 37, rng, radar=True) for _ in range(3)]
+    assert all(float(g["p_A"].max()) > 0 for g in grids)
+    g, o = _gpu(p), OracleFilter(p, "f32")
+    g.set_state(st)
+    o.set_state(st)
+    for k, m in enumerate([(0.4, -0.25, 0.05), None, (0.0, 0.0, -0.3), (1.1, 0.3, 0.0)]):
+        for f in (g, o):
+            f.set_measurement_grid(**grids[k % 3])
+            if m is not None:
+                f.set_ego_motion(*m)
+            f.step(0.1)
+        compare_frame(g, o, radar=True, what=f"frame {k}: ")
+
+
 def _bern_grid(rng, W, H):
     C = W * H
     return dict(z=(rng.uniform(0, 1, C) < 0.3).astype(np.float32),
